@@ -1,0 +1,921 @@
+/*
+ * Oracle: plain, slow, FP64 CPU reference for the integral-direct J/K build.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  The CUDA
+ * product path never links, calls or reads anything here, and this file shares
+ * no code, tables or constants with it.
+ *
+ * What it computes (paper: Wang et al., "Extending GPU-Accelerated Gaussian
+ * Integrals in the TeraChem Software Package to f Type Orbitals"):
+ *   - contracted Cartesian Gaussian basis functions, Eq. contracted_basis and
+ *     Eq. primtive_basis (Sec. 2.1), normalised per component;
+ *   - the Boys function, Eq. boys_function, by its power series / asymptote;
+ *   - electron repulsion integrals, Eq. eri_definition, by a method that is
+ *     deliberately NOT the paper's McMurchie-Davidson scheme: Obara-Saika
+ *     vertical recurrence with the electron-transfer term, then Head-Gordon-
+ *     Pople horizontal recurrence (the paper's refs for OS and HGP);
+ *   - the Cauchy-Schwarz bound Eq. cauchy_schwarz_bound and the significance
+ *     test of Eq. kernel_upperbound (density factor off);
+ *   - J and K by their definitions, Eq. j_definition and Eq. k_definition,
+ *     either over every ordered shell quartet or over canonical quartets with
+ *     the 8-fold symmetry of Eq. 8_fold_symmetry;
+ *   - E_J and E_K of SI Eq. si_E_J_K and their nuclear gradient with all four
+ *     centres differentiated (SI Sec. 1.4), NOT the bra-only shortcut of
+ *     SI Eq. si_dE_J / si_dE_K, so that the shortcut gets checked;
+ *   - one-electron overlap (Eq. overlap_definition) and point-charge attraction
+ *     (Eq. v1e_definition2), used only to pin the ERIs and normalisation.
+ *
+ * Readings where the paper is silent (all listed in the design doc as well):
+ *   - normalisation: every primitive component gets
+ *     N = (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2i-1)!!(2j-1)!!(2k-1)!!), then each
+ *     shell's coefficients are scaled once so the contracted (l,0,0) component
+ *     has unit self-overlap;
+ *   - Cartesian components in lexicographic order (xx,xy,xz,yy,yz,zz; ...);
+ *   - Schwarz Q_ab = sqrt(max_{mu in a, nu in b} |(mu nu|mu nu)|) computed in
+ *     FP64, rounded to float32 toward +infinity; a quartet is kept iff
+ *     (double)Q_ab * (double)Q_cd >= thresh.
+ *
+ * Parity status: every function here is pinned by tests/test_oracle_*.py
+ * (quadrature, closed forms, sum rules, invariances, finite differences).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_LMAX 3
+#define OR_PI_L 3.141592653589793238462643383279502884L
+#define OR_PI 3.141592653589793238462643383279502884
+
+/* ------------------------------------------------------------------------ */
+/* Cartesian component bookkeeping                                           */
+/* ------------------------------------------------------------------------ */
+
+static int ncart(int l) { return l < 0 ? 0 : (l + 1) * (l + 2) / 2; }
+/* number of exponent triples (x,y,z) with x+y+z <= n */
+static int ncart_cum(int n) { return n < 0 ? 0 : (n + 1) * (n + 2) * (n + 3) / 6; }
+/* position of (x,y,z) inside its shell, lexicographic order (x desc, y desc) */
+static int cart_in_shell(int x, int y, int z) {
+  int r = y + z;
+  (void)x;
+  return r * (r + 1) / 2 + z;
+}
+/* position of (x,y,z) among all triples with sum <= x+y+z, grouped by sum */
+static int cart_global(int x, int y, int z) {
+  return ncart_cum(x + y + z - 1) + cart_in_shell(x, y, z);
+}
+/* the k-th component of shell l */
+static void cart_comp(int l, int k, int c[3]) {
+  int idx = 0;
+  for (int x = l; x >= 0; --x)
+    for (int y = l - x; y >= 0; --y) {
+      if (idx == k) {
+        c[0] = x; c[1] = y; c[2] = l - x - y;
+        return;
+      }
+      ++idx;
+    }
+}
+/* the k-th triple in global order */
+static void cart_comp_global(int k, int c[3]) {
+  int n = 0;
+  while (ncart_cum(n) <= k) ++n;
+  cart_comp(n, k - ncart_cum(n - 1), c);
+}
+
+static double dfact(int n) { /* n!!, with (-1)!! = 1 */
+  double r = 1.0;
+  for (int k = n; k > 1; k -= 2) r *= k;
+  return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Boys function, Eq. boys_function: F_m(x) = int_0^1 t^(2m) exp(-x t^2) dt  */
+/* x < 30 : F_m(x) = exp(-x) sum_k (2x)^k / ((2m+1)(2m+3)...(2m+2k+1))        */
+/* x >= 30: F_0 = (1/2) sqrt(pi/x) erf(sqrt(x)), then                          */
+/*          F_{m+1} = ((2m+1) F_m - exp(-x)) / (2x)                            */
+/* ------------------------------------------------------------------------ */
+
+void or_boys(int mmax, double x, double* F) {
+  long double X = x;
+  if (x < 30.0) {
+    long double ex = expl(-X);
+    for (int m = 0; m <= mmax; ++m) {
+      long double term = 1.0L / (2 * m + 1), sum = term;
+      for (int k = 1; k < 4000; ++k) {
+        term *= 2.0L * X / (long double)(2 * m + 2 * k + 1);
+        sum += term;
+        if (term < 1e-24L * sum) break;
+      }
+      F[m] = (double)(ex * sum);
+    }
+  } else {
+    long double ex = expl(-X);
+    long double f = 0.5L * sqrtl(OR_PI_L / X) * erfl(sqrtl(X));
+    F[0] = (double)f;
+    for (int m = 0; m < mmax; ++m) {
+      f = ((2 * m + 1) * f - ex) / (2.0L * X);
+      F[m + 1] = (double)f;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Primitive integrals over unnormalised Cartesian Gaussians                  */
+/* G(r) = (x-Ax)^i (y-Ay)^j (z-Az)^k exp(-a |r-A|^2)                          */
+/* ------------------------------------------------------------------------ */
+
+/* Obara-Saika 1-D overlap table s[i][j], i<=la, j<=lb (row stride lb+1). */
+static void os_overlap_1d(int la, int lb, double a, double b, double A, double B, double* s) {
+  double p = a + b, P = (a * A + b * B) / p;
+  double PA = P - A, PB = P - B, o2p = 0.5 / p;
+  int w = lb + 1;
+  s[0] = sqrt(OR_PI / p) * exp(-a * b / p * (A - B) * (A - B));
+  for (int i = 0; i <= la; ++i)
+    for (int j = 0; j <= lb; ++j) {
+      if (i == 0 && j == 0) continue;
+      double v;
+      if (i > 0) {
+        v = PA * s[(i - 1) * w + j];
+        if (i > 1) v += o2p * (i - 1) * s[(i - 2) * w + j];
+        if (j > 0) v += o2p * j * s[(i - 1) * w + j - 1];
+      } else {
+        v = PB * s[i * w + j - 1];
+        if (j > 1) v += o2p * (j - 1) * s[i * w + j - 2];
+      }
+      s[i * w + j] = v;
+    }
+}
+
+/* primitive overlap block out[na][nb] */
+void or_prim_overlap(int la, int lb, double a, double b, const double* A, const double* B, double* out) {
+  double sx[64], sy[64], sz[64];
+  os_overlap_1d(la, lb, a, b, A[0], B[0], sx);
+  os_overlap_1d(la, lb, a, b, A[1], B[1], sy);
+  os_overlap_1d(la, lb, a, b, A[2], B[2], sz);
+  int na = ncart(la), nb = ncart(lb), w = lb + 1;
+  for (int ia = 0; ia < na; ++ia) {
+    int ca[3];
+    cart_comp(la, ia, ca);
+    for (int ib = 0; ib < nb; ++ib) {
+      int cb[3];
+      cart_comp(lb, ib, cb);
+      out[ia * nb + ib] = sx[ca[0] * w + cb[0]] * sy[ca[1] * w + cb[1]] * sz[ca[2] * w + cb[2]];
+    }
+  }
+}
+
+/*
+ * Head-Gordon-Pople horizontal recurrence
+ *   (a, b+1_i| = (a+1_i, b| + AB_i (a, b|
+ * in:  [nouter][ncart_cum(E)][ninner], indexed by global triple of a (|a|<=E)
+ * out: [nouter][ncart(la)][ncart(lb)][ninner], E = la+lb
+ */
+static void hrr(int la, int lb, const double AB[3], int nouter, int ninner, const double* in, double* out) {
+  int E = la + lb, nE = ncart_cum(E);
+  int na = ncart(la), nb = ncart(lb);
+  for (int o = 0; o < nouter; ++o) {
+    /* cur[a_glob][b_in_level][inner] for the current |b| */
+    double* cur = (double*)malloc(sizeof(double) * nE * 1 * ninner);
+    memcpy(cur, in + (size_t)o * nE * ninner, sizeof(double) * nE * ninner);
+    for (int nbv = 0; nbv < lb; ++nbv) {
+      int nbc = ncart(nbv), nbn = ncart(nbv + 1);
+      double* nxt = (double*)calloc((size_t)nE * nbn * ninner, sizeof(double));
+      for (int jb = 0; jb < nbn; ++jb) {
+        int b1[3];
+        cart_comp(nbv + 1, jb, b1);
+        int dir = b1[0] > 0 ? 0 : (b1[1] > 0 ? 1 : 2);
+        int b0[3] = {b1[0], b1[1], b1[2]};
+        b0[dir] -= 1;
+        int ib0 = cart_in_shell(b0[0], b0[1], b0[2]);
+        /* |a| runs over la .. E-(nbv+1) */
+        for (int ka = ncart_cum(la - 1); ka < ncart_cum(E - nbv - 1); ++ka) {
+          int a[3];
+          cart_comp_global(ka, a);
+          int ap[3] = {a[0], a[1], a[2]};
+          ap[dir] += 1;
+          int kap = cart_global(ap[0], ap[1], ap[2]);
+          for (int t = 0; t < ninner; ++t)
+            nxt[((size_t)ka * nbn + jb) * ninner + t] =
+                cur[((size_t)kap * nbc + ib0) * ninner + t] + AB[dir] * cur[((size_t)ka * nbc + ib0) * ninner + t];
+        }
+      }
+      free(cur);
+      cur = nxt;
+    }
+    /* cur now [a_glob][ncart(lb)][inner]; keep |a| == la */
+    for (int ia = 0; ia < na; ++ia) {
+      int a[3];
+      cart_comp(la, ia, a);
+      int ka = cart_global(a[0], a[1], a[2]);
+      for (int ib = 0; ib < nb; ++ib)
+        for (int t = 0; t < ninner; ++t)
+          out[(((size_t)o * na + ia) * nb + ib) * ninner + t] = cur[((size_t)ka * nb + ib) * ninner + t];
+    }
+    free(cur);
+  }
+}
+
+/*
+ * Primitive ERI block [ab|cd], out[na][nb][nc][nd], by Obara-Saika:
+ *   [00|00]^(m) = 2 pi^(5/2) / (p q sqrt(p+q)) K_AB K_CD F_m(rho |PQ|^2)
+ *   bra VRR  [e+1_i,0|00]^(m) = PA_i [e0|00]^(m) + WP_i [e0|00]^(m+1)
+ *                               + e_i/(2p) ([e-1_i,0|00]^(m) - rho/p [e-1_i,0|00]^(m+1))
+ *   ket VRR  [e0|f+1_i,0]^(m) = QC_i [e0|f0]^(m) + WQ_i [e0|f0]^(m+1)
+ *                               + f_i/(2q) ([e0|f-1_i,0]^(m) - rho/q [e0|f-1_i,0]^(m+1))
+ *                               + e_i/(2(p+q)) [e-1_i,0|f0]^(m+1)
+ * then HRR on the bra and on the ket.  The base case is Eq. eri_base_case.
+ */
+void or_prim_eri(int la, int lb, int lc, int ld, double a, double b, double c, double d, const double* A,
+                 const double* B, const double* C, const double* D, double* out) {
+  int E = la + lb, F = lc + ld, L = E + F;
+  double p = a + b, q = c + d, rho = p * q / (p + q);
+  double P[3], Q[3], W[3], PA[3], WP[3], QC[3], WQ[3], AB[3], CD[3];
+  double ab2 = 0, cd2 = 0, pq2 = 0;
+  for (int i = 0; i < 3; ++i) {
+    P[i] = (a * A[i] + b * B[i]) / p;
+    Q[i] = (c * C[i] + d * D[i]) / q;
+    W[i] = (p * P[i] + q * Q[i]) / (p + q);
+    PA[i] = P[i] - A[i];
+    WP[i] = W[i] - P[i];
+    QC[i] = Q[i] - C[i];
+    WQ[i] = W[i] - Q[i];
+    AB[i] = A[i] - B[i];
+    CD[i] = C[i] - D[i];
+    ab2 += AB[i] * AB[i];
+    cd2 += CD[i] * CD[i];
+    pq2 += (P[i] - Q[i]) * (P[i] - Q[i]);
+  }
+  double Fm[32];
+  or_boys(L, rho * pq2, Fm);
+  double pref = 2.0 * pow(OR_PI, 2.5) / (p * q * sqrt(p + q)) * exp(-a * b / p * ab2) * exp(-c * d / q * cd2);
+
+  int nE = ncart_cum(E), nF = ncart_cum(F), nm = L + 1;
+  double* V = (double*)calloc((size_t)nE * nF * nm, sizeof(double));
+#define VV(ie, jf, m) V[((size_t)(ie) * nF + (jf)) * nm + (m)]
+  for (int m = 0; m <= L; ++m) VV(0, 0, m) = pref * Fm[m];
+  /* bra VRR with f = 0 */
+  for (int ie = 1; ie < nE; ++ie) {
+    int e[3];
+    cart_comp_global(ie, e);
+    int ne = e[0] + e[1] + e[2];
+    int i = e[0] > 0 ? 0 : (e[1] > 0 ? 1 : 2);
+    int e1[3] = {e[0], e[1], e[2]};
+    e1[i] -= 1; /* e = e1 + 1_i */
+    int k1 = cart_global(e1[0], e1[1], e1[2]);
+    int k2 = -1;
+    if (e1[i] > 0) {
+      int e2[3] = {e1[0], e1[1], e1[2]};
+      e2[i] -= 1;
+      k2 = cart_global(e2[0], e2[1], e2[2]);
+    }
+    for (int m = 0; m <= L - ne; ++m) {
+      double v = PA[i] * VV(k1, 0, m) + WP[i] * VV(k1, 0, m + 1);
+      if (k2 >= 0) v += e1[i] / (2.0 * p) * (VV(k2, 0, m) - rho / p * VV(k2, 0, m + 1));
+      VV(ie, 0, m) = v;
+    }
+  }
+  /* ket VRR with the electron-transfer term */
+  for (int jf = 1; jf < nF; ++jf) {
+    int f[3];
+    cart_comp_global(jf, f);
+    int nf = f[0] + f[1] + f[2];
+    int i = f[0] > 0 ? 0 : (f[1] > 0 ? 1 : 2);
+    int f1[3] = {f[0], f[1], f[2]};
+    f1[i] -= 1;
+    int j1 = cart_global(f1[0], f1[1], f1[2]);
+    int j2 = -1;
+    if (f1[i] > 0) {
+      int f2[3] = {f1[0], f1[1], f1[2]};
+      f2[i] -= 1;
+      j2 = cart_global(f2[0], f2[1], f2[2]);
+    }
+    for (int ie = 0; ie < nE; ++ie) {
+      int e[3];
+      cart_comp_global(ie, e);
+      int ne = e[0] + e[1] + e[2];
+      int ke = -1;
+      if (e[i] > 0) {
+        int e1[3] = {e[0], e[1], e[2]};
+        e1[i] -= 1;
+        ke = cart_global(e1[0], e1[1], e1[2]);
+      }
+      for (int m = 0; m <= L - ne - nf; ++m) {
+        double v = QC[i] * VV(ie, j1, m) + WQ[i] * VV(ie, j1, m + 1);
+        if (j2 >= 0) v += f1[i] / (2.0 * q) * (VV(ie, j2, m) - rho / q * VV(ie, j2, m + 1));
+        if (ke >= 0) v += e[i] / (2.0 * (p + q)) * VV(ke, j1, m + 1);
+        VV(ie, jf, m) = v;
+      }
+    }
+  }
+  /* (e0|f0) at m = 0, laid out [ie][jf] */
+  double* T = (double*)malloc(sizeof(double) * nE * nF);
+  for (int ie = 0; ie < nE; ++ie)
+    for (int jf = 0; jf < nF; ++jf) T[(size_t)ie * nF + jf] = VV(ie, jf, 0);
+#undef VV
+  free(V);
+  int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
+  /* bra HRR: [ie][jf] -> [a][b][jf] */
+  double* U = (double*)malloc(sizeof(double) * na * nb * nF);
+  hrr(la, lb, AB, 1, nF, T, U);
+  free(T);
+  /* ket HRR: [ab][jf] -> [ab][c][d] */
+  hrr(lc, ld, CD, na * nb, 1, U, out);
+  free(U);
+}
+
+/*
+ * Primitive point-charge attraction (a| 1/|r-C| |b), out[na][nb], unit charge,
+ * Eq. v1e_definition2, by the Obara-Saika three-centre recurrence:
+ *   Theta^(m)_00 = (2 pi / p) K_AB F_m(p |PC|^2)       (Eq. v1e_base_case)
+ *   Theta^(m)_{e+1_i} = PA_i Theta^(m)_e - PC_i Theta^(m+1)_e
+ *                       + e_i/(2p) (Theta^(m)_{e-1_i} - Theta^(m+1)_{e-1_i})
+ * then HRR.
+ */
+void or_prim_nuclear(int la, int lb, double a, double b, const double* A, const double* B, const double* C,
+                     double* out) {
+  int E = la + lb;
+  double p = a + b, P[3], PA[3], PC[3], AB[3], ab2 = 0, pc2 = 0;
+  for (int i = 0; i < 3; ++i) {
+    P[i] = (a * A[i] + b * B[i]) / p;
+    PA[i] = P[i] - A[i];
+    PC[i] = P[i] - C[i];
+    AB[i] = A[i] - B[i];
+    ab2 += AB[i] * AB[i];
+    pc2 += PC[i] * PC[i];
+  }
+  double Fm[32];
+  or_boys(E, p * pc2, Fm);
+  double pref = 2.0 * OR_PI / p * exp(-a * b / p * ab2);
+  int nE = ncart_cum(E), nm = E + 1;
+  double* V = (double*)calloc((size_t)nE * nm, sizeof(double));
+  for (int m = 0; m <= E; ++m) V[m] = pref * Fm[m];
+  for (int ie = 1; ie < nE; ++ie) {
+    int e[3];
+    cart_comp_global(ie, e);
+    int ne = e[0] + e[1] + e[2];
+    int i = e[0] > 0 ? 0 : (e[1] > 0 ? 1 : 2);
+    int e1[3] = {e[0], e[1], e[2]};
+    e1[i] -= 1;
+    int k1 = cart_global(e1[0], e1[1], e1[2]);
+    int k2 = -1;
+    if (e1[i] > 0) {
+      int e2[3] = {e1[0], e1[1], e1[2]};
+      e2[i] -= 1;
+      k2 = cart_global(e2[0], e2[1], e2[2]);
+    }
+    for (int m = 0; m <= E - ne; ++m) {
+      double v = PA[i] * V[k1 * nm + m] - PC[i] * V[k1 * nm + m + 1];
+      if (k2 >= 0) v += e1[i] / (2.0 * p) * (V[k2 * nm + m] - V[k2 * nm + m + 1]);
+      V[ie * nm + m] = v;
+    }
+  }
+  double* T = (double*)malloc(sizeof(double) * nE);
+  for (int ie = 0; ie < nE; ++ie) T[ie] = V[ie * nm];
+  free(V);
+  hrr(la, lb, AB, 1, 1, T, out);
+  free(T);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Basis: shells, normalisation                                               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int nshell, natom, nbf;
+  int *atom, *l, *nprim, *poff, *aoff;
+  double* exps;
+  double* cn;     /* coefficient of the normalised (l,0,0) component, per primitive */
+  double* coords; /* natom*3 */
+} or_ctx;
+
+static double norm_l00(double alpha, int l) {
+  return pow(2.0 * alpha / OR_PI, 0.75) * pow(4.0 * alpha, 0.5 * l) / sqrt(dfact(2 * l - 1));
+}
+/* ratio between the norm of component (x,y,z) and of (l,0,0); exponent-free */
+static double comp_factor(int x, int y, int z) {
+  int l = x + y + z;
+  return sqrt(dfact(2 * l - 1) / (dfact(2 * x - 1) * dfact(2 * y - 1) * dfact(2 * z - 1)));
+}
+
+void* or_create(int nshell, int natom, const int32_t* atom, const int32_t* l, const int32_t* nprim,
+                const int32_t* poff, const double* exps, const double* coefs, const double* coords) {
+  or_ctx* c = (or_ctx*)calloc(1, sizeof(or_ctx));
+  c->nshell = nshell;
+  c->natom = natom;
+  c->atom = (int*)malloc(sizeof(int) * nshell);
+  c->l = (int*)malloc(sizeof(int) * nshell);
+  c->nprim = (int*)malloc(sizeof(int) * nshell);
+  c->poff = (int*)malloc(sizeof(int) * nshell);
+  c->aoff = (int*)malloc(sizeof(int) * (nshell + 1));
+  int ntot = 0, nbf = 0;
+  for (int s = 0; s < nshell; ++s) {
+    c->atom[s] = atom[s];
+    c->l[s] = l[s];
+    c->nprim[s] = nprim[s];
+    c->poff[s] = poff[s];
+    c->aoff[s] = nbf;
+    nbf += ncart(l[s]);
+    if (poff[s] + nprim[s] > ntot) ntot = poff[s] + nprim[s];
+  }
+  c->aoff[nshell] = nbf;
+  c->nbf = nbf;
+  c->exps = (double*)malloc(sizeof(double) * ntot);
+  c->cn = (double*)malloc(sizeof(double) * ntot);
+  memcpy(c->exps, exps, sizeof(double) * ntot);
+  c->coords = (double*)malloc(sizeof(double) * natom * 3);
+  memcpy(c->coords, coords, sizeof(double) * natom * 3);
+  /* per-primitive norm, then rescale so the contracted (l,0,0) has unit norm */
+  for (int s = 0; s < nshell; ++s) {
+    int L = l[s], o = poff[s], np = nprim[s];
+    for (int k = 0; k < np; ++k) c->cn[o + k] = coefs[o + k] * norm_l00(exps[o + k], L);
+    double zero[3] = {0, 0, 0}, S = 0.0;
+    double* blk = (double*)malloc(sizeof(double) * ncart(L) * ncart(L));
+    for (int k1 = 0; k1 < np; ++k1)
+      for (int k2 = 0; k2 < np; ++k2) {
+        or_prim_overlap(L, L, exps[o + k1], exps[o + k2], zero, zero, blk);
+        S += c->cn[o + k1] * c->cn[o + k2] * blk[0]; /* (l,0,0) with itself */
+      }
+    free(blk);
+    double sc = 1.0 / sqrt(S);
+    for (int k = 0; k < np; ++k) c->cn[o + k] *= sc;
+  }
+  return c;
+}
+
+void or_destroy(void* h) {
+  or_ctx* c = (or_ctx*)h;
+  if (!c) return;
+  free(c->atom); free(c->l); free(c->nprim); free(c->poff); free(c->aoff);
+  free(c->exps); free(c->cn); free(c->coords);
+  free(c);
+}
+
+void or_set_coords(void* h, const double* coords) {
+  or_ctx* c = (or_ctx*)h;
+  memcpy(c->coords, coords, sizeof(double) * c->natom * 3);
+}
+
+int or_nbf(void* h) { return ((or_ctx*)h)->nbf; }
+void or_ao_offsets(void* h, int32_t* out) {
+  or_ctx* c = (or_ctx*)h;
+  for (int s = 0; s <= c->nshell; ++s) out[s] = c->aoff[s];
+}
+void or_norm_coefs(void* h, double* out) {
+  or_ctx* c = (or_ctx*)h;
+  for (int s = 0; s < c->nshell; ++s)
+    for (int k = 0; k < c->nprim[s]; ++k) out[c->poff[s] + k] = c->cn[c->poff[s] + k];
+}
+
+static const double* ctr(const or_ctx* c, int s) { return c->coords + 3 * c->atom[s]; }
+
+/* contracted, normalised overlap block S[na][nb] (Eq. overlap_definition) */
+void or_overlap_block(void* h, int sa, int sb, double* out) {
+  or_ctx* c = (or_ctx*)h;
+  int la = c->l[sa], lb = c->l[sb], na = ncart(la), nb = ncart(lb);
+  double* blk = (double*)malloc(sizeof(double) * na * nb);
+  for (int i = 0; i < na * nb; ++i) out[i] = 0.0;
+  for (int ka = 0; ka < c->nprim[sa]; ++ka)
+    for (int kb = 0; kb < c->nprim[sb]; ++kb) {
+      int pa = c->poff[sa] + ka, pb = c->poff[sb] + kb;
+      or_prim_overlap(la, lb, c->exps[pa], c->exps[pb], ctr(c, sa), ctr(c, sb), blk);
+      double w = c->cn[pa] * c->cn[pb];
+      for (int i = 0; i < na * nb; ++i) out[i] += w * blk[i];
+    }
+  for (int ia = 0; ia < na; ++ia) {
+    int ca[3];
+    cart_comp(la, ia, ca);
+    for (int ib = 0; ib < nb; ++ib) {
+      int cb[3];
+      cart_comp(lb, ib, cb);
+      out[ia * nb + ib] *= comp_factor(ca[0], ca[1], ca[2]) * comp_factor(cb[0], cb[1], cb[2]);
+    }
+  }
+  free(blk);
+}
+
+/* contracted, normalised point-charge attraction block V[na][nb], charge at C */
+void or_nuclear_block(void* h, int sa, int sb, const double* C, double* out) {
+  or_ctx* c = (or_ctx*)h;
+  int la = c->l[sa], lb = c->l[sb], na = ncart(la), nb = ncart(lb);
+  double* blk = (double*)malloc(sizeof(double) * na * nb);
+  for (int i = 0; i < na * nb; ++i) out[i] = 0.0;
+  for (int ka = 0; ka < c->nprim[sa]; ++ka)
+    for (int kb = 0; kb < c->nprim[sb]; ++kb) {
+      int pa = c->poff[sa] + ka, pb = c->poff[sb] + kb;
+      or_prim_nuclear(la, lb, c->exps[pa], c->exps[pb], ctr(c, sa), ctr(c, sb), C, blk);
+      double w = c->cn[pa] * c->cn[pb];
+      for (int i = 0; i < na * nb; ++i) out[i] += w * blk[i];
+    }
+  for (int ia = 0; ia < na; ++ia) {
+    int ca[3];
+    cart_comp(la, ia, ca);
+    for (int ib = 0; ib < nb; ++ib) {
+      int cb[3];
+      cart_comp(lb, ib, cb);
+      out[ia * nb + ib] *= comp_factor(ca[0], ca[1], ca[2]) * comp_factor(cb[0], cb[1], cb[2]);
+    }
+  }
+  free(blk);
+}
+
+static void apply_comp_factors(int la, int lb, int lc, int ld, double* out) {
+  int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
+  for (int ia = 0; ia < na; ++ia) {
+    int ca[3];
+    cart_comp(la, ia, ca);
+    double fa = comp_factor(ca[0], ca[1], ca[2]);
+    for (int ib = 0; ib < nb; ++ib) {
+      int cb[3];
+      cart_comp(lb, ib, cb);
+      double fb = comp_factor(cb[0], cb[1], cb[2]);
+      for (int ic = 0; ic < nc; ++ic) {
+        int cc[3];
+        cart_comp(lc, ic, cc);
+        double fc = comp_factor(cc[0], cc[1], cc[2]);
+        for (int id = 0; id < nd; ++id) {
+          int cd[3];
+          cart_comp(ld, id, cd);
+          double fd = comp_factor(cd[0], cd[1], cd[2]);
+          out[((ia * nb + ib) * nc + ic) * nd + id] *= fa * fb * fc * fd;
+        }
+      }
+    }
+  }
+}
+
+/* contracted, normalised ERI block (ab|cd), out[na][nb][nc][nd] */
+void or_eri_block(void* h, int sa, int sb, int sc, int sd, double* out) {
+  or_ctx* c = (or_ctx*)h;
+  int la = c->l[sa], lb = c->l[sb], lc = c->l[sc], ld = c->l[sd];
+  int n = ncart(la) * ncart(lb) * ncart(lc) * ncart(ld);
+  double* blk = (double*)malloc(sizeof(double) * n);
+  for (int i = 0; i < n; ++i) out[i] = 0.0;
+  for (int ka = 0; ka < c->nprim[sa]; ++ka)
+    for (int kb = 0; kb < c->nprim[sb]; ++kb)
+      for (int kc = 0; kc < c->nprim[sc]; ++kc)
+        for (int kd = 0; kd < c->nprim[sd]; ++kd) {
+          int pa = c->poff[sa] + ka, pb = c->poff[sb] + kb, pc = c->poff[sc] + kc, pd = c->poff[sd] + kd;
+          or_prim_eri(la, lb, lc, ld, c->exps[pa], c->exps[pb], c->exps[pc], c->exps[pd], ctr(c, sa), ctr(c, sb),
+                      ctr(c, sc), ctr(c, sd), blk);
+          double w = c->cn[pa] * c->cn[pb] * c->cn[pc] * c->cn[pd];
+          for (int i = 0; i < n; ++i) out[i] += w * blk[i];
+        }
+  apply_comp_factors(la, lb, lc, ld, out);
+  free(blk);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Schwarz bounds and lists (Eq. cauchy_schwarz_bound, Eq. kernel_upperbound) */
+/* ------------------------------------------------------------------------ */
+
+static float round_up_f32(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = nextafterf(f, INFINITY);
+  return f;
+}
+static int pair_index(int a, int b) { return a >= b ? a * (a + 1) / 2 + b : b * (b + 1) / 2 + a; }
+static int pair_class(int la, int lb) {
+  int hi = la > lb ? la : lb, lo = la > lb ? lb : la;
+  return hi * (hi + 1) / 2 + lo;
+}
+
+/* Q[pair_index(a,b)] for all a >= b, float32 rounded toward +infinity */
+void or_schwarz(void* h, float* Q) {
+  or_ctx* c = (or_ctx*)h;
+  int ns = c->nshell;
+#pragma omp parallel for schedule(dynamic)
+  for (int a = 0; a < ns; ++a) {
+    for (int b = 0; b <= a; ++b) {
+      int na = ncart(c->l[a]), nb = ncart(c->l[b]);
+      double* blk = (double*)malloc(sizeof(double) * na * nb * na * nb);
+      or_eri_block(h, a, b, a, b, blk);
+      double mx = 0.0;
+      for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nb; ++j) {
+          double v = fabs(blk[((i * nb + j) * na + i) * nb + j]);
+          if (v > mx) mx = v;
+        }
+      free(blk);
+      Q[pair_index(a, b)] = round_up_f32(sqrt(mx));
+    }
+  }
+}
+
+/*
+ * Lists from float32 Q: sig[pair] = 1 iff (double)Q*(double)Qmax >= thresh;
+ * counts[pair*10 + cls] = number of pairs of class cls significant with it.
+ */
+void or_lists(void* h, double thresh, const float* Q, int32_t* sig, int32_t* counts) {
+  or_ctx* c = (or_ctx*)h;
+  int ns = c->nshell, np = ns * (ns + 1) / 2;
+  double qmax = 0.0;
+  for (int i = 0; i < np; ++i)
+    if ((double)Q[i] > qmax) qmax = (double)Q[i];
+  int* cls = (int*)malloc(sizeof(int) * np);
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b <= a; ++b) cls[pair_index(a, b)] = pair_class(c->l[a], c->l[b]);
+  for (int i = 0; i < np; ++i) sig[i] = ((double)Q[i] * qmax >= thresh) ? 1 : 0;
+  for (int i = 0; i < np; ++i) {
+    for (int k = 0; k < 10; ++k) counts[i * 10 + k] = 0;
+    if (!sig[i]) continue;
+    for (int j = 0; j < np; ++j)
+      if (sig[j] && (double)Q[i] * (double)Q[j] >= thresh) counts[i * 10 + cls[j]] += 1;
+  }
+  free(cls);
+}
+
+/* ------------------------------------------------------------------------ */
+/* J and K (Eq. j_definition, Eq. k_definition)                               */
+/* ------------------------------------------------------------------------ */
+
+static int quartet_kept(const float* Q, double thresh, int a, int b, int cc, int d) {
+  return (double)Q[pair_index(a, b)] * (double)Q[pair_index(cc, d)] >= thresh;
+}
+
+/*
+ * mode 0: every ordered shell quartet, J_mn += (mn|ls) D_ls, K_ml += (mn|ls) D_ns.
+ * mode 1: canonical quartets a>=b, c>=d, pair(ab)>=pair(cd), scaled by
+ *         w = 1/2^[a=b] 1/2^[c=d] 1/2^[ab=cd] and scattered into all eight index
+ *         permutations of Eq. 8_fold_symmetry.
+ * J or K may be NULL.  Q: float32 Schwarz bounds (or_schwarz layout).
+ */
+void or_jk(void* h, const double* Dm, double thresh, const float* Q, int mode, double* J, double* K) {
+  or_ctx* c = (or_ctx*)h;
+  int ns = c->nshell, n = c->nbf;
+  if (J) memset(J, 0, sizeof(double) * n * n);
+  if (K) memset(K, 0, sizeof(double) * n * n);
+#pragma omp parallel
+  {
+    double* Jt = (double*)calloc((size_t)n * n, sizeof(double));
+    double* Kt = (double*)calloc((size_t)n * n, sizeof(double));
+    double* X = (double*)malloc(sizeof(double) * 10000);
+#pragma omp for schedule(dynamic)
+    for (int a = 0; a < ns; ++a) {
+      for (int b = 0; b < ns; ++b) {
+        if (mode == 1 && b > a) continue;
+        for (int cc = 0; cc < ns; ++cc)
+          for (int d = 0; d < ns; ++d) {
+            if (mode == 1 && (d > cc || pair_index(cc, d) > pair_index(a, b))) continue;
+            if (!quartet_kept(Q, thresh, a, b, cc, d)) continue;
+            or_eri_block(h, a, b, cc, d, X);
+            int na = ncart(c->l[a]), nb = ncart(c->l[b]), nc = ncart(c->l[cc]), nd = ncart(c->l[d]);
+            int oa = c->aoff[a], ob = c->aoff[b], oc = c->aoff[cc], od = c->aoff[d];
+            double w = 1.0;
+            if (mode == 1) {
+              if (a == b) w *= 0.5;
+              if (cc == d) w *= 0.5;
+              if (pair_index(a, b) == pair_index(cc, d)) w *= 0.5;
+            }
+            for (int i = 0; i < na; ++i)
+              for (int j = 0; j < nb; ++j)
+                for (int k = 0; k < nc; ++k)
+                  for (int l = 0; l < nd; ++l) {
+                    double x = w * X[((i * nb + j) * nc + k) * nd + l];
+                    int m_ = oa + i, n_ = ob + j, l_ = oc + k, s_ = od + l;
+                    if (mode == 0) {
+                      Jt[(size_t)m_ * n + n_] += x * Dm[(size_t)l_ * n + s_];
+                      Kt[(size_t)m_ * n + l_] += x * Dm[(size_t)n_ * n + s_];
+                    } else {
+                      /* the eight permutations (mn|ls) (nm|ls) (mn|sl) (nm|sl)
+                         (ls|mn) (sl|mn) (ls|nm) (sl|nm) */
+                      Jt[(size_t)m_ * n + n_] += x * Dm[(size_t)l_ * n + s_];
+                      Jt[(size_t)n_ * n + m_] += x * Dm[(size_t)l_ * n + s_];
+                      Jt[(size_t)m_ * n + n_] += x * Dm[(size_t)s_ * n + l_];
+                      Jt[(size_t)n_ * n + m_] += x * Dm[(size_t)s_ * n + l_];
+                      Jt[(size_t)l_ * n + s_] += x * Dm[(size_t)m_ * n + n_];
+                      Jt[(size_t)s_ * n + l_] += x * Dm[(size_t)m_ * n + n_];
+                      Jt[(size_t)l_ * n + s_] += x * Dm[(size_t)n_ * n + m_];
+                      Jt[(size_t)s_ * n + l_] += x * Dm[(size_t)n_ * n + m_];
+                      Kt[(size_t)m_ * n + l_] += x * Dm[(size_t)n_ * n + s_];
+                      Kt[(size_t)n_ * n + l_] += x * Dm[(size_t)m_ * n + s_];
+                      Kt[(size_t)m_ * n + s_] += x * Dm[(size_t)n_ * n + l_];
+                      Kt[(size_t)n_ * n + s_] += x * Dm[(size_t)m_ * n + l_];
+                      Kt[(size_t)l_ * n + m_] += x * Dm[(size_t)s_ * n + n_];
+                      Kt[(size_t)s_ * n + m_] += x * Dm[(size_t)l_ * n + n_];
+                      Kt[(size_t)l_ * n + n_] += x * Dm[(size_t)s_ * n + m_];
+                      Kt[(size_t)s_ * n + n_] += x * Dm[(size_t)l_ * n + m_];
+                    }
+                  }
+          }
+      }
+    }
+#pragma omp critical
+    {
+      for (size_t i = 0; i < (size_t)n * n; ++i) {
+        if (J) J[i] += Jt[i];
+        if (K) K[i] += Kt[i];
+      }
+    }
+    free(Jt);
+    free(Kt);
+    free(X);
+  }
+}
+
+/* E_J = 1/2 sum D J, E_K = -1/4 sum D K (SI Eq. si_E_J_K), long double sums */
+void or_energy(int n, const double* Dm, const double* J, const double* K, double* EJ, double* EK) {
+  long double sj = 0.0L, sk = 0.0L;
+  for (size_t i = 0; i < (size_t)n * n; ++i) {
+    if (J) sj += (long double)Dm[i] * (long double)J[i];
+    if (K) sk += (long double)Dm[i] * (long double)K[i];
+  }
+  if (EJ) *EJ = (double)(0.5L * sj);
+  if (EK) *EK = (double)(-0.25L * sk);
+}
+
+/*
+ * Sampled blocks for large systems.
+ * J block (a,b): J_mn = sum over all ordered shells (c,d) of (ab|cd) D_cd.
+ * K block (a,c): K_ml = sum over all ordered shells (b,d) of (ab|cd) D_bd.
+ * Both with the quartet test on Q.
+ */
+void or_j_block(void* h, const double* Dm, double thresh, const float* Q, int a, int b, double* out) {
+  or_ctx* c = (or_ctx*)h;
+  int ns = c->nshell, n = c->nbf, na = ncart(c->l[a]), nb = ncart(c->l[b]);
+  for (int i = 0; i < na * nb; ++i) out[i] = 0.0;
+#pragma omp parallel
+  {
+    double* acc = (double*)calloc(na * nb, sizeof(double));
+    double* X = (double*)malloc(sizeof(double) * 10000);
+#pragma omp for schedule(dynamic)
+    for (int cc = 0; cc < ns; ++cc)
+      for (int d = 0; d < ns; ++d) {
+        if (!quartet_kept(Q, thresh, a, b, cc, d)) continue;
+        or_eri_block(h, a, b, cc, d, X);
+        int nc = ncart(c->l[cc]), nd = ncart(c->l[d]), oc = c->aoff[cc], od = c->aoff[d];
+        for (int i = 0; i < na; ++i)
+          for (int j = 0; j < nb; ++j)
+            for (int k = 0; k < nc; ++k)
+              for (int l = 0; l < nd; ++l)
+                acc[i * nb + j] += X[((i * nb + j) * nc + k) * nd + l] * Dm[(size_t)(oc + k) * n + od + l];
+      }
+#pragma omp critical
+    for (int i = 0; i < na * nb; ++i) out[i] += acc[i];
+    free(acc);
+    free(X);
+  }
+}
+
+void or_k_block(void* h, const double* Dm, double thresh, const float* Q, int a, int cc, double* out) {
+  or_ctx* c = (or_ctx*)h;
+  int ns = c->nshell, n = c->nbf, na = ncart(c->l[a]), nc = ncart(c->l[cc]);
+  for (int i = 0; i < na * nc; ++i) out[i] = 0.0;
+#pragma omp parallel
+  {
+    double* acc = (double*)calloc(na * nc, sizeof(double));
+    double* X = (double*)malloc(sizeof(double) * 10000);
+#pragma omp for schedule(dynamic)
+    for (int b = 0; b < ns; ++b)
+      for (int d = 0; d < ns; ++d) {
+        if (!quartet_kept(Q, thresh, a, b, cc, d)) continue;
+        or_eri_block(h, a, b, cc, d, X);
+        int nb = ncart(c->l[b]), nd = ncart(c->l[d]), ob = c->aoff[b], od = c->aoff[d];
+        for (int i = 0; i < na; ++i)
+          for (int j = 0; j < nb; ++j)
+            for (int k = 0; k < nc; ++k)
+              for (int l = 0; l < nd; ++l)
+                acc[i * nc + k] += X[((i * nb + j) * nc + k) * nd + l] * Dm[(size_t)(ob + j) * n + od + l];
+      }
+#pragma omp critical
+    for (int i = 0; i < na * nc; ++i) out[i] += acc[i];
+    free(acc);
+    free(X);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nuclear gradient of E = E_J + E_K with D held fixed (SI Sec. 1.4)          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * d(ab|cd)/dX_t for the centre X of shell `which` (0:a 1:b 2:c 3:d), t = x,y,z,
+ * from the raising/lowering rule at primitive level
+ *   d/dX_t G(i) = 2 alpha G(i + 1_t) - i_t G(i - 1_t),
+ * with each function keeping its own normalisation.  out[3][na nb nc nd].
+ */
+static void eri_deriv_block(or_ctx* c, int s[4], int which, double* out) {
+  int l[4], nn[4];
+  for (int k = 0; k < 4; ++k) {
+    l[k] = c->l[s[k]];
+    nn[k] = ncart(l[k]);
+  }
+  int n = nn[0] * nn[1] * nn[2] * nn[3];
+  for (int i = 0; i < 3 * n; ++i) out[i] = 0.0;
+  int lup[4] = {l[0], l[1], l[2], l[3]}, ldn[4] = {l[0], l[1], l[2], l[3]};
+  lup[which] += 1;
+  ldn[which] -= 1;
+  int nup[4], ndn[4];
+  for (int k = 0; k < 4; ++k) {
+    nup[k] = ncart(lup[k]);
+    ndn[k] = ncart(ldn[k]);
+  }
+  int Nup = nup[0] * nup[1] * nup[2] * nup[3], Ndn = ldn[which] >= 0 ? ndn[0] * ndn[1] * ndn[2] * ndn[3] : 0;
+  double* up = (double*)malloc(sizeof(double) * Nup);
+  double* dn = (double*)malloc(sizeof(double) * (Ndn > 0 ? Ndn : 1));
+  int k4[4];
+  for (k4[0] = 0; k4[0] < c->nprim[s[0]]; ++k4[0])
+    for (k4[1] = 0; k4[1] < c->nprim[s[1]]; ++k4[1])
+      for (k4[2] = 0; k4[2] < c->nprim[s[2]]; ++k4[2])
+        for (k4[3] = 0; k4[3] < c->nprim[s[3]]; ++k4[3]) {
+          int pp[4];
+          double ex[4];
+          const double* R[4];
+          double w = 1.0;
+          for (int k = 0; k < 4; ++k) {
+            pp[k] = c->poff[s[k]] + k4[k];
+            ex[k] = c->exps[pp[k]];
+            R[k] = ctr(c, s[k]);
+            w *= c->cn[pp[k]];
+          }
+          or_prim_eri(lup[0], lup[1], lup[2], lup[3], ex[0], ex[1], ex[2], ex[3], R[0], R[1], R[2], R[3], up);
+          if (Ndn > 0)
+            or_prim_eri(ldn[0], ldn[1], ldn[2], ldn[3], ex[0], ex[1], ex[2], ex[3], R[0], R[1], R[2], R[3], dn);
+          double alpha = ex[which];
+          int idx[4];
+          for (idx[0] = 0; idx[0] < nn[0]; ++idx[0])
+            for (idx[1] = 0; idx[1] < nn[1]; ++idx[1])
+              for (idx[2] = 0; idx[2] < nn[2]; ++idx[2])
+                for (idx[3] = 0; idx[3] < nn[3]; ++idx[3]) {
+                  int o = ((idx[0] * nn[1] + idx[1]) * nn[2] + idx[2]) * nn[3] + idx[3];
+                  int cw[3];
+                  cart_comp(l[which], idx[which], cw);
+                  for (int t = 0; t < 3; ++t) {
+                    int cu[3] = {cw[0], cw[1], cw[2]};
+                    cu[t] += 1;
+                    int iu[4] = {idx[0], idx[1], idx[2], idx[3]};
+                    iu[which] = cart_in_shell(cu[0], cu[1], cu[2]);
+                    double v = 2.0 * alpha * up[((iu[0] * nup[1] + iu[1]) * nup[2] + iu[2]) * nup[3] + iu[3]];
+                    if (cw[t] > 0) {
+                      int cdn[3] = {cw[0], cw[1], cw[2]};
+                      cdn[t] -= 1;
+                      int id[4] = {idx[0], idx[1], idx[2], idx[3]};
+                      id[which] = cart_in_shell(cdn[0], cdn[1], cdn[2]);
+                      v -= cw[t] * dn[((id[0] * ndn[1] + id[1]) * ndn[2] + id[2]) * ndn[3] + id[3]];
+                    }
+                    out[t * n + o] += w * v;
+                  }
+                }
+        }
+  for (int t = 0; t < 3; ++t) apply_comp_factors(l[0], l[1], l[2], l[3], out + t * n);
+  free(up);
+  free(dn);
+}
+
+/*
+ * grad[natom*3] = dE/dR with E = 1/2 sum D_mn D_ls (mn|ls) - 1/4 sum D_ml D_ns (mn|ls),
+ * i.e. sum over every ordered quartet of Gamma_mnls d(mn|ls)/dR with
+ * Gamma = 1/2 D_mn D_ls - 1/4 D_ml D_ns, all four centres differentiated.
+ * The quartet test uses the given (frozen) Q.  want_j / want_k select terms.
+ */
+void or_grad(void* h, const double* Dm, double thresh, const float* Q, int want_j, int want_k, double* grad) {
+  or_ctx* c = (or_ctx*)h;
+  int ns = c->nshell, n = c->nbf, nat = c->natom;
+  for (int i = 0; i < nat * 3; ++i) grad[i] = 0.0;
+#pragma omp parallel
+  {
+    double* g = (double*)calloc(nat * 3, sizeof(double));
+    double* dX = (double*)malloc(sizeof(double) * 3 * 10000);
+#pragma omp for schedule(dynamic)
+    for (int a = 0; a < ns; ++a)
+      for (int b = 0; b < ns; ++b)
+        for (int cc = 0; cc < ns; ++cc)
+          for (int d = 0; d < ns; ++d) {
+            if (!quartet_kept(Q, thresh, a, b, cc, d)) continue;
+            int s[4] = {a, b, cc, d};
+            int na = ncart(c->l[a]), nb = ncart(c->l[b]), nc = ncart(c->l[cc]), nd = ncart(c->l[d]);
+            int nq = na * nb * nc * nd;
+            for (int which = 0; which < 4; ++which) {
+              eri_deriv_block(c, s, which, dX);
+              int atom = c->atom[s[which]];
+              for (int i = 0; i < na; ++i)
+                for (int j = 0; j < nb; ++j)
+                  for (int k = 0; k < nc; ++k)
+                    for (int l = 0; l < nd; ++l) {
+                      int m_ = c->aoff[a] + i, n_ = c->aoff[b] + j, l_ = c->aoff[cc] + k, s_ = c->aoff[d] + l;
+                      double G = 0.0;
+                      if (want_j) G += 0.5 * Dm[(size_t)m_ * n + n_] * Dm[(size_t)l_ * n + s_];
+                      if (want_k) G -= 0.25 * Dm[(size_t)m_ * n + l_] * Dm[(size_t)n_ * n + s_];
+                      int o = ((i * nb + j) * nc + k) * nd + l;
+                      for (int t = 0; t < 3; ++t) g[atom * 3 + t] += G * dX[t * nq + o];
+                    }
+            }
+          }
+#pragma omp critical
+    for (int i = 0; i < nat * 3; ++i) grad[i] += g[i];
+    free(g);
+    free(dX);
+  }
+}
+
+int or_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
