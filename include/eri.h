@@ -1,0 +1,159 @@
+/*
+ * eri.h -- C ABI of the GB300 integral-direct Coulomb/exchange library.
+ *
+ * The operations follow Wang et al., "Extending GPU-Accelerated Gaussian
+ * Integrals in the TeraChem Software Package to f Type Orbitals":
+ *   basis functions      Sec. 2.1, Eq. contracted_basis, Eq. primtive_basis
+ *   ERIs                 Sec. 2.5, Eq. eri_definition, Eq. eri_formula
+ *   J and K              Eq. j_definition (J_mn = sum_ls (mn|ls) D_ls),
+ *                        Eq. k_definition (K_ml = sum_ns (mn|ls) D_ns)
+ *   screening            Eq. cauchy_schwarz_bound, Eq. kernel_upperbound
+ *   energies, gradient   SI Eq. si_E_J_K, SI Eq. si_dE_J, SI Eq. si_dE_K
+ *
+ * Conventions (all calls):
+ *   - units bohr / hartree; all floating-point arguments are FP64;
+ *   - matrices are nbf x nbf, row-major, AO order = user shell order, and
+ *     inside a shell the Cartesian components are lexicographic
+ *     (xx,xy,xz,yy,yz,zz; xxx,xxy,xxz,xyy,xyz,xzz,yyy,yyz,yzz,zzz);
+ *   - every function is normalised: each primitive component gets
+ *     (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2i-1)!!(2j-1)!!(2k-1)!!) and each
+ *     shell's coefficients are rescaled once so the contracted (l,0,0)
+ *     function has unit norm (the paper leaves the convention open, Sec. 2.1);
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     every call that takes a stream is ordered on it and returns before the
+ *     GPU work finishes, unless stated otherwise;
+ *   - D, J, K, dEdR and E pointers are DEVICE pointers on the plan's device,
+ *     owned by the caller; outputs are overwritten, not accumulated;
+ *   - D must be symmetric (8-fold symmetry, Eq. 8_fold_symmetry);
+ *   - return value 0 on success, else a negative ERI_E* code; no call aborts
+ *     the process.  eri_strerror() describes a code.
+ *   - a plan must not be used from two streams at the same time.
+ */
+#ifndef GB300_ERI_H
+#define GB300_ERI_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ERI_OK 0
+#define ERI_EINVAL (-1)       /* bad argument: NULL, l > 3, nprim <= 0, exponent <= 0, NaN ... */
+#define ERI_ENOMEM (-2)       /* device or host allocation failed */
+#define ERI_ECUDA (-3)        /* a CUDA runtime call failed */
+#define ERI_EUNSUPPORTED (-4) /* valid request this build cannot serve */
+#define ERI_ETIMEOUT (-5)     /* a bounded device wait gave up */
+#define ERI_EDEVICE (-6)      /* a device-side check failed (status word set) */
+
+#define ERI_FP64 0  /* every quartet in FP64 */
+#define ERI_MIXED 1 /* quartets with bound below mixed_tau in FP32, the rest FP64 */
+
+typedef struct eri_plan eri_plan_t;
+
+typedef struct {
+  int32_t atom;        /* index into coords */
+  int32_t l;           /* 0..3 (s, p, d, f), Cartesian */
+  int32_t nprim;       /* >= 1 */
+  int32_t prim_offset; /* first primitive in exps / coefs */
+} eri_shell_t;
+
+typedef struct {
+  int32_t nshell, natom;
+  const eri_shell_t* shells; /* host, nshell entries, user order */
+  const double* exps;        /* host, exponents (> 0) */
+  const double* coefs;       /* host, raw contraction coefficients */
+} eri_basis_t;
+
+typedef struct {
+  double thresh;      /* Schwarz quartet threshold THRECL (Eq. kernel_upperbound); default 1e-12 */
+  int32_t precision;  /* ERI_FP64 (default) or ERI_MIXED */
+  double mixed_tau;   /* FP64 tier: Q_ab Q_cd max|D| >= mixed_tau; default 1e-5 (paper Sec. 4.1) */
+  int32_t device;     /* CUDA device ordinal; default: current device */
+} eri_opts_t;
+
+typedef struct {
+  int32_t nbf, nshell, npair, nsig_pair;
+  int64_t quartets_k;      /* canonical significant shell quartets (unique, 8-fold) */
+  int64_t quartets_j;      /* ordered significant (bra, ket) shell-pair pairs of the J-engine */
+  int64_t prim_quartets_k; /* primitive quartets behind quartets_k */
+  int64_t quartets_k_fp32; /* of quartets_k, evaluated in FP32 by the last mixed build */
+  double flops_k, flops_j; /* algorithmic FLOPs of the last build (McMurchie-Davidson count) */
+  int32_t device_status;   /* device-side status word (0 = ok) */
+} eri_stats_t;
+
+/* Fill opts with the defaults listed above.  Host only. */
+int eri_default_opts(eri_opts_t* opts);
+
+/*
+ * Build a plan: copies the basis and coordinates (host, natom*3 doubles) to
+ * the device, normalises the basis, forms every shell pair's primitive-pair
+ * data, the Schwarz bounds Q_ab (Eq. cauchy_schwarz_bound, float32 rounded
+ * up) and the class-sorted significant pair and quartet lists for
+ * opts->thresh.  Synchronises the device.  *out owns all device memory it
+ * allocates until eri_plan_destroy.  opts may be NULL (defaults).
+ * Errors: ERI_EINVAL (bad basis or coords), ERI_ENOMEM, ERI_ECUDA.
+ */
+int eri_plan(const eri_basis_t* basis, const double* coords, const eri_opts_t* opts, eri_plan_t** out);
+
+/*
+ * Move the atoms: coords_dev is a DEVICE pointer to natom*3 doubles.  Pair
+ * data, Schwarz bounds and lists are rebuilt on `stream`, then the call waits
+ * for the new list sizes (a device->host copy).  Use for finite differences
+ * and for autograd.  If freeze_lists != 0 the lists and Q of the previous
+ * geometry are kept (so energies are smooth functions of the coordinates).
+ */
+int eri_plan_set_coords(eri_plan_t* plan, const double* coords_dev, int32_t freeze_lists, void* stream);
+
+/*
+ * J_mn = sum_ls (mn|ls) D_ls and K_ml = sum_ns (mn|ls) D_ns over the quartets
+ * whose Schwarz bound Q_ab Q_cd >= thresh (Eq. j_definition, Eq. k_definition,
+ * Eq. kernel_upperbound).  D, J, K: device, nbf*nbf.  J or K may be NULL to
+ * skip that matrix (J alone runs only the J-engine).  thresh < 0 keeps the
+ * plan's threshold; another value rebuilds the lists first (with a host wait).
+ * precision: ERI_FP64 or ERI_MIXED (tier split at the plan's mixed_tau).
+ */
+int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double* K, double thresh, int32_t precision,
+                 void* stream);
+
+/*
+ * E_J = 1/2 sum D_mn J_mn and E_K = -1/4 sum D_mn K_mn (SI Eq. si_E_J_K):
+ * E_out is a DEVICE pointer to 2 doubles {E_J, E_K}.  J or K may be NULL
+ * (its energy is written as 0).
+ */
+int eri_energy(eri_plan_t* plan, const double* D, const double* J, const double* K, double* E_out, void* stream);
+
+/*
+ * dE/dR for E = 1/2 tr(D J) - 1/4 tr(D K) with D held fixed (the terms in dD/dR
+ * are left out, SI Eq. si_dE_J_step1): dEdR is a DEVICE pointer to natom*3
+ * doubles.  Uses the bra-derivative form SI Eq. si_dE_J / si_dE_K with the
+ * derivative Hermite coefficients of SI Eq. si_dE_recursion.  Lists as for
+ * eri_build_jk at the plan's threshold.  want_j / want_k select the terms.
+ */
+int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int32_t want_j, int32_t want_k, void* stream);
+
+/*
+ * Copy the plan's lists to HOST buffers for inspection (each may be NULL):
+ *   Q      float32 [npair]        Schwarz bound per shell pair, pair index a(a+1)/2+b (a >= b)
+ *   sig    int32   [npair]        1 iff Q * Qmax >= thresh
+ *   counts int32   [npair * 10]   kets of each pair class significant with the pair
+ *   sorted int32   [npair]        significant pair indices, class by class (ss ps pp ds dp dd fs fp fd ff),
+ *                                 each class by Q descending then pair index ascending
+ *   class_count int32 [10]        length of each class in `sorted`
+ * Synchronises the device.
+ */
+int eri_get_lists(eri_plan_t* plan, float* Q, int32_t* sig, int32_t* counts, int32_t* sorted,
+                  int32_t* class_count);
+
+/* Statistics of the plan and of its last build (host copy; synchronises). */
+int eri_get_stats(eri_plan_t* plan, eri_stats_t* stats);
+
+/* Free every device and host resource of the plan (NULL is a no-op). */
+int eri_plan_destroy(eri_plan_t* plan);
+
+/* Static description of an error code. */
+const char* eri_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

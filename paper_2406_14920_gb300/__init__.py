@@ -1,0 +1,184 @@
+"""GB300-native integral-direct Coulomb (J) and exchange (K) library.
+
+Thin Python binding over the C ABI of include/eri.h (libgb300eri.so, built
+in-tree by ``paper_2406_14920_gb300.build.build()``).  This module only
+marshals arguments: every step of the J/K build runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  There is no CPU
+fallback: if the library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgb300eri.so")
+_lib = None
+
+ERI_FP64 = 0
+ERI_MIXED = 1
+
+
+class EriError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what} failed: {strerror(code)} ({code})")
+        self.code = code
+
+
+class ShellT(C.Structure):
+    _fields_ = [("atom", C.c_int32), ("l", C.c_int32), ("nprim", C.c_int32), ("prim_offset", C.c_int32)]
+
+
+class BasisT(C.Structure):
+    _fields_ = [("nshell", C.c_int32), ("natom", C.c_int32), ("shells", C.POINTER(ShellT)),
+                ("exps", C.POINTER(C.c_double)), ("coefs", C.POINTER(C.c_double))]
+
+
+class OptsT(C.Structure):
+    _fields_ = [("thresh", C.c_double), ("precision", C.c_int32), ("mixed_tau", C.c_double),
+                ("device", C.c_int32)]
+
+
+class StatsT(C.Structure):
+    _fields_ = [("nbf", C.c_int32), ("nshell", C.c_int32), ("npair", C.c_int32), ("nsig_pair", C.c_int32),
+                ("quartets_k", C.c_int64), ("quartets_j", C.c_int64), ("prim_quartets_k", C.c_int64),
+                ("quartets_k_fp32", C.c_int64), ("flops_k", C.c_double), ("flops_j", C.c_double),
+                ("device_status", C.c_int32)]
+
+
+def lib():
+    """Load libgb300eri.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2406_14920_gb300.build.build() first")
+        L = C.CDLL(LIB_PATH)
+        vp, d, i32 = C.c_void_p, C.POINTER(C.c_double), C.c_int32
+        L.eri_default_opts.argtypes = [C.POINTER(OptsT)]
+        L.eri_plan.argtypes = [C.POINTER(BasisT), d, C.POINTER(OptsT), C.POINTER(vp)]
+        L.eri_plan_set_coords.argtypes = [vp, vp, i32, vp]
+        L.eri_build_jk.argtypes = [vp, vp, vp, vp, C.c_double, i32, vp]
+        L.eri_energy.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.eri_jk_grad.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.eri_get_lists.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.eri_get_stats.argtypes = [vp, C.POINTER(StatsT)]
+        L.eri_plan_destroy.argtypes = [vp]
+        L.eri_strerror.argtypes = [C.c_int]
+        L.eri_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().eri_strerror(int(code)).decode()
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise EriError(rc, what)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """An eri_plan over one basis and geometry (see include/eri.h)."""
+
+    def __init__(self, basis, coords=None, thresh=1e-12, precision=ERI_FP64, mixed_tau=1e-5, device=None):
+        L = lib()
+        self.basis = basis
+        self.nbf = basis.nbf
+        self.natom = basis.natom
+        self.npair = basis.nshell * (basis.nshell + 1) // 2
+        shells = (ShellT * basis.nshell)()
+        for s in range(basis.nshell):
+            shells[s].atom = int(basis.shell_atom[s])
+            shells[s].l = int(basis.shell_l[s])
+            shells[s].nprim = int(basis.shell_nprim[s])
+            shells[s].prim_offset = int(basis.shell_prim_offset[s])
+        self._exps = np.ascontiguousarray(basis.exps, np.float64)
+        self._coefs = np.ascontiguousarray(basis.coefs, np.float64)
+        b = BasisT(basis.nshell, basis.natom, shells, self._exps.ctypes.data_as(C.POINTER(C.c_double)),
+                   self._coefs.ctypes.data_as(C.POINTER(C.c_double)))
+        self._shells = shells
+        crd = np.ascontiguousarray(basis.coords if coords is None else coords, np.float64)
+        o = OptsT()
+        L.eri_default_opts(C.byref(o))
+        o.thresh = float(thresh)
+        o.precision = int(precision)
+        o.mixed_tau = float(mixed_tau)
+        o.device = -1 if device is None else int(device)
+        h = C.c_void_p()
+        _check(L.eri_plan(C.byref(b), crd.ctypes.data_as(C.POINTER(C.c_double)), C.byref(o), C.byref(h)), "eri_plan")
+        self.h = h
+        self.precision = int(precision)
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().eri_plan_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_jk(self, D, J=None, K=None, want_j=True, want_k=True, thresh=-1.0, precision=None, stream=None):
+        """J, K (torch float64 CUDA tensors, nbf x nbf) for the density D."""
+        import torch
+        n = self.nbf
+        if want_j and J is None:
+            J = torch.empty((n, n), dtype=torch.float64, device=D.device)
+        if want_k and K is None:
+            K = torch.empty((n, n), dtype=torch.float64, device=D.device)
+        prec = self.precision if precision is None else int(precision)
+        _check(lib().eri_build_jk(self.h, _ptr(D), _ptr(J if want_j else None), _ptr(K if want_k else None),
+                                  float(thresh), prec, _stream_ptr(stream)), "eri_build_jk")
+        return (J if want_j else None), (K if want_k else None)
+
+    def energy(self, D, J, K, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(2, dtype=torch.float64, device=D.device)
+        _check(lib().eri_energy(self.h, _ptr(D), _ptr(J), _ptr(K), _ptr(out), _stream_ptr(stream)), "eri_energy")
+        return out
+
+    def set_coords(self, coords_dev, freeze_lists=False, stream=None):
+        _check(lib().eri_plan_set_coords(self.h, _ptr(coords_dev), int(bool(freeze_lists)), _stream_ptr(stream)),
+               "eri_plan_set_coords")
+
+    def grad(self, D, out=None, want_j=True, want_k=True, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.natom, 3), dtype=torch.float64, device=D.device)
+        _check(lib().eri_jk_grad(self.h, _ptr(D), _ptr(out), int(want_j), int(want_k), _stream_ptr(stream)),
+               "eri_jk_grad")
+        return out
+
+    def lists(self):
+        Q = np.zeros(self.npair, np.float32)
+        sig = np.zeros(self.npair, np.int32)
+        counts = np.zeros(self.npair * 10, np.int32)
+        srt = np.zeros(self.npair, np.int32)
+        cc = np.zeros(10, np.int32)
+        P = lambda a, t: a.ctypes.data_as(C.POINTER(t))
+        _check(lib().eri_get_lists(self.h, P(Q, C.c_float), P(sig, C.c_int32), P(counts, C.c_int32),
+                                   P(srt, C.c_int32), P(cc, C.c_int32)), "eri_get_lists")
+        return {"Q": Q, "sig": sig, "counts": counts.reshape(self.npair, 10), "sorted": srt[:int(cc.sum())],
+                "class_count": cc}
+
+    def stats(self):
+        s = StatsT()
+        _check(lib().eri_get_stats(self.h, C.byref(s)), "eri_get_stats")
+        return {k: getattr(s, k) for k, _ in StatsT._fields_}

@@ -1,0 +1,134 @@
+// Launch helpers for the class-specialised kernels.  Each bra class gets its own
+// translation unit (k_bra<X>.cu, j_lab<N>.cu) so that the build compiles them
+// in parallel.
+#pragma once
+#include <algorithm>
+#include "kernels.cuh"
+
+namespace eri {
+
+template <int X> struct ClassL;
+template <> struct ClassL<0> { static constexpr int l1 = 0, l2 = 0; };
+template <> struct ClassL<1> { static constexpr int l1 = 1, l2 = 0; };
+template <> struct ClassL<2> { static constexpr int l1 = 1, l2 = 1; };
+template <> struct ClassL<3> { static constexpr int l1 = 2, l2 = 0; };
+template <> struct ClassL<4> { static constexpr int l1 = 2, l2 = 1; };
+template <> struct ClassL<5> { static constexpr int l1 = 2, l2 = 2; };
+template <> struct ClassL<6> { static constexpr int l1 = 3, l2 = 0; };
+template <> struct ClassL<7> { static constexpr int l1 = 3, l2 = 1; };
+template <> struct ClassL<8> { static constexpr int l1 = 3, l2 = 2; };
+template <> struct ClassL<9> { static constexpr int l1 = 3, l2 = 3; };
+
+struct LaunchInfo {
+  int grid, block;
+  size_t smem;
+};
+
+template <typename Kern>
+inline cudaError_t launch_persistent(Kern kern, size_t smem, int64_t items, int warps_per_block, int nsm,
+                                     LaunchInfo* info) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * warps_per_block, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  int64_t need = (items + warps_per_block - 1) / warps_per_block;
+  int64_t grid = std::min<int64_t>(need, (int64_t)nsm * occ);
+  if (grid < 1) grid = 1;
+  info->grid = (int)grid;
+  info->block = 32 * warps_per_block;
+  info->smem = smem;
+  return cudaSuccess;
+}
+
+template <int LA, int LB, int LC, int LD, typename T>
+cudaError_t launch_k_t(const KArgs& a, cudaStream_t s, int nsm) {
+  if (a.wl.total <= 0) return cudaSuccess;
+  using S = KShape<LA, LB, LC, LD, T>;
+  constexpr int WPB = 4;
+  LaunchInfo li;
+  auto kern = k_warp_kernel<LA, LB, LC, LD, T>;
+  cudaError_t e = launch_persistent(kern, WPB * S::smem_per_warp(), a.wl.total, WPB, nsm, &li);
+  if (e != cudaSuccess) return e;
+  kern<<<li.grid, li.block, li.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int X, int Y>
+cudaError_t launch_k_xy(int prec, const KArgs& a, cudaStream_t s, int nsm) {
+  if constexpr (Y <= X) {
+    constexpr int LA = ClassL<X>::l1, LB = ClassL<X>::l2, LC = ClassL<Y>::l1, LD = ClassL<Y>::l2;
+    return prec ? launch_k_t<LA, LB, LC, LD, float>(a, s, nsm) : launch_k_t<LA, LB, LC, LD, double>(a, s, nsm);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+template <int X>
+cudaError_t launch_k_x(int Y, int prec, const KArgs& a, cudaStream_t s, int nsm) {
+  switch (Y) {
+    case 0: return launch_k_xy<X, 0>(prec, a, s, nsm);
+    case 1: return launch_k_xy<X, 1>(prec, a, s, nsm);
+    case 2: return launch_k_xy<X, 2>(prec, a, s, nsm);
+    case 3: return launch_k_xy<X, 3>(prec, a, s, nsm);
+    case 4: return launch_k_xy<X, 4>(prec, a, s, nsm);
+    case 5: return launch_k_xy<X, 5>(prec, a, s, nsm);
+    case 6: return launch_k_xy<X, 6>(prec, a, s, nsm);
+    case 7: return launch_k_xy<X, 7>(prec, a, s, nsm);
+    case 8: return launch_k_xy<X, 8>(prec, a, s, nsm);
+    case 9: return launch_k_xy<X, 9>(prec, a, s, nsm);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int LAB, int LCD, typename T>
+cudaError_t launch_j_t(const JArgs& a, cudaStream_t s, int nsm) {
+  if (a.wl.total <= 0) return cudaSuccess;
+  using S = JShape<LAB, LCD, T>;
+  constexpr int WPB = 4;
+  LaunchInfo li;
+  auto kern = j_warp_kernel<LAB, LCD, T>;
+  cudaError_t e = launch_persistent(kern, WPB * S::smem_per_warp(), a.wl.total, WPB, nsm, &li);
+  if (e != cudaSuccess) return e;
+  kern<<<li.grid, li.block, li.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LAB>
+cudaError_t launch_j_lab(int LCD, int prec, const JArgs& a, cudaStream_t s, int nsm) {
+#define ERI_JCASE(N) \
+  case N: return prec ? launch_j_t<LAB, N, float>(a, s, nsm) : launch_j_t<LAB, N, double>(a, s, nsm);
+  switch (LCD) {
+    ERI_JCASE(0)
+    ERI_JCASE(1)
+    ERI_JCASE(2)
+    ERI_JCASE(3)
+    ERI_JCASE(4)
+    ERI_JCASE(5)
+    ERI_JCASE(6)
+  }
+#undef ERI_JCASE
+  return cudaErrorInvalidValue;
+}
+
+// entry points defined in the per-class translation units
+cudaError_t launch_k_bra0(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_k_bra1(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_k_bra2(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_k_bra3(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_k_bra4(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_k_bra5(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_k_bra6(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_k_bra7(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_k_bra8(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_k_bra9(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_j_lab0(int, int, const JArgs&, cudaStream_t, int);
+cudaError_t launch_j_lab1(int, int, const JArgs&, cudaStream_t, int);
+cudaError_t launch_j_lab2(int, int, const JArgs&, cudaStream_t, int);
+cudaError_t launch_j_lab3(int, int, const JArgs&, cudaStream_t, int);
+cudaError_t launch_j_lab4(int, int, const JArgs&, cudaStream_t, int);
+cudaError_t launch_j_lab5(int, int, const JArgs&, cudaStream_t, int);
+cudaError_t launch_j_lab6(int, int, const JArgs&, cudaStream_t, int);
+
+}  // namespace eri

@@ -1,0 +1,7 @@
+// J-engine kernels with bra Hermite order 0 (all ket orders 0..6, FP64 and FP32).
+#include "dispatch.cuh"
+namespace eri {
+cudaError_t launch_j_lab0(int LCD, int prec, const JArgs& a, cudaStream_t s, int nsm) {
+  return launch_j_lab<0>(LCD, prec, a, s, nsm);
+}
+}  // namespace eri

@@ -1,0 +1,920 @@
+// Plan construction, preparation kernels and the C ABI (include/eri.h).
+//
+// Every numerical step of the path runs in a kernel of this library:
+//   normalisation (Sec. 2.1)            k_normalize, k_compfac
+//   Boys table (Eq. boys_function)      k_boys_table
+//   primitive pair data (Eq. pair_definition)   k_pairs
+//   Schwarz bounds (Eq. cauchy_schwarz_bound)   k_schwarz
+//   class-sorted lists (Sec. 3.2, Eq. kernel_upperbound)   k_sig, k_rank, k_counts, k_prefix
+//   Hermite density (Eq. j_formula, first sub-step)        k_hermite_density
+//   J-engine / exchange kernels (kernels.cuh)
+//   Hermite J -> Cartesian J (Eq. j_formula, last sub-step) k_post_j
+//   K symmetrisation (Eq. 8_fold_symmetry)                 k_post_k
+//   energies (SI Eq. si_E_J_K)                             k_energy
+// Host code only validates arguments, does integer bookkeeping (offsets,
+// launch sizes) and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/eri.h"
+#include "dispatch.cuh"
+#include "plan.cuh"
+
+using namespace eri;
+
+// ---------------------------------------------------------------------------
+// device kernels
+// ---------------------------------------------------------------------------
+
+// Per-primitive normalised coefficient of the (l,0,0) component:
+// c_k N_l(a_k) s, N_l(a) = (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2l-1)!!),
+// s chosen so the contracted (l,0,0) function has unit norm; for two
+// normalised (l,0,0) primitives on one centre <g_a|g_b> = (2 sqrt(ab)/(a+b))^(l+3/2).
+__global__ void k_normalize(int nshell, const int* __restrict__ l, const int* __restrict__ nprim,
+                            const int* __restrict__ poff, const double* __restrict__ ex,
+                            const double* __restrict__ co, double* __restrict__ cn) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nshell) return;
+  const int L = l[s], n = nprim[s], o = poff[s];
+  double df = 1.0;
+  for (int k = 2 * L - 1; k > 1; k -= 2) df *= k;
+  double S = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double ai = ex[o + i], aj = ex[o + j];
+      S += co[o + i] * co[o + j] * pow(2.0 * sqrt(ai * aj) / (ai + aj), L + 1.5);
+    }
+  const double sc = 1.0 / sqrt(S);
+  for (int i = 0; i < n; ++i) {
+    double a = ex[o + i];
+    cn[o + i] = co[o + i] * sc * pow(2.0 * a / 3.14159265358979323846, 0.75) * pow(4.0 * a, 0.5 * L) / sqrt(df);
+  }
+}
+
+// Component factor f(x,y,z) = sqrt((2l-1)!! / ((2x-1)!! (2y-1)!! (2z-1)!!)) per AO.
+__global__ void k_compfac(int nshell, const int* __restrict__ l, const int* __restrict__ ao, double* __restrict__ f) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nshell) return;
+  const int L = l[s];
+  auto df = [](int n) {
+    double r = 1.0;
+    for (int k = n; k > 1; k -= 2) r *= k;
+    return r;
+  };
+  for (int k = 0; k < ncart(L); ++k) {
+    int x, y, z;
+    cart_xyz(L, k, x, y, z);
+    f[ao[s] + k] = sqrt(df(2 * L - 1) / (df(2 * x - 1) * df(2 * y - 1) * df(2 * z - 1)));
+  }
+}
+
+// Boys table F_m(T_k), T_k = k h: series for a high order m_top,
+// F_m(T) = exp(-T) sum_i (2T)^i / ((2m+1)(2m+3)...(2m+2i+1)), then the stable
+// downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1).
+__global__ void k_boys_table(double* __restrict__ t64, float* __restrict__ t32) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= BOYS_NT) return;
+  const double T = k * BOYS_H;
+  const int mtop = BOYS_MDIM + 24;
+  double term = 1.0 / (2 * mtop + 1), sum = term;
+  for (int i = 1; i < 2000; ++i) {
+    term *= 2.0 * T / (2 * mtop + 2 * i + 1);
+    sum += term;
+    if (term < 1e-18 * sum) break;
+  }
+  const double e = exp(-T);
+  double f = e * sum;
+  for (int m = mtop - 1; m >= 0; --m) {
+    f = (2.0 * T * f + e) / (2 * m + 1);
+    if (m < BOYS_MDIM) {
+      t64[k * BOYS_MDIM + m] = f;
+      t32[k * BOYS_MDIM + m] = (float)f;
+    }
+  }
+}
+
+// Primitive-pair data for every shell pair (Eq. pair_definition):
+// p = a+b, P = (aA+bB)/p, PA = P-A, PB = P-B,
+// pref = c_a c_b exp(-ab/p |AB|^2) sqrt(2 pi^(5/2)) / p  (so that a quartet's
+// prefactor 2 pi^(5/2)/(pq sqrt(p+q)) K_AB K_CD c c c c = pref_ab pref_cd / sqrt(p+q)).
+__global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __restrict__ s2,
+                        const int* __restrict__ poff, const int* __restrict__ sh_atom, const int* __restrict__ sh_np,
+                        const int* __restrict__ sh_po, const double* __restrict__ ex, const double* __restrict__ cn,
+                        const double* __restrict__ coords, int nprimpair, double* p_, double* P_, double* PA_,
+                        double* PB_, double* pref_, float* pf, float* Pf, float* PAf, float* PBf, float* preff) {
+  int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= npair) return;
+  const int a = s1[ip], b = s2[ip];
+  const double* A = coords + 3 * sh_atom[a];
+  const double* Bc = coords + 3 * sh_atom[b];
+  double AB2 = 0.0;
+  for (int d = 0; d < 3; ++d) AB2 += (A[d] - Bc[d]) * (A[d] - Bc[d]);
+  int o = poff[ip];
+  const double s2pi52 = 5.9149671727956129;  // sqrt(2 pi^(5/2))
+  for (int i = 0; i < sh_np[a]; ++i)
+    for (int j = 0; j < sh_np[b]; ++j, ++o) {
+      const double ea = ex[sh_po[a] + i], eb = ex[sh_po[b] + j];
+      const double p = ea + eb;
+      const double pr = cn[sh_po[a] + i] * cn[sh_po[b] + j] * exp(-ea * eb / p * AB2) * s2pi52 / p;
+      p_[o] = p;
+      pref_[o] = pr;
+      pf[o] = (float)p;
+      preff[o] = (float)pr;
+      for (int d = 0; d < 3; ++d) {
+        const double P = (ea * A[d] + eb * Bc[d]) / p;
+        P_[d * nprimpair + o] = P;
+        PA_[d * nprimpair + o] = P - A[d];
+        PB_[d * nprimpair + o] = P - Bc[d];
+        Pf[d * nprimpair + o] = (float)P;
+        PAf[d * nprimpair + o] = (float)(P - A[d]);
+        PBf[d * nprimpair + o] = (float)(P - Bc[d]);
+      }
+    }
+}
+
+// runtime-l E^{ij}_t (Eq. E_recursion), E[(i*5+j)*9+t], i,j <= 4
+__device__ void md_e_rt(int li, int lj, double PA, double PB, double o2p, double* E) {
+  for (int x = 0; x < 225; ++x) E[x] = 0.0;
+  E[0] = 1.0;
+  for (int i = 0; i < li; ++i)
+    for (int t = 0; t <= i + 1; ++t) {
+      double v = PA * E[(i * 5) * 9 + t];
+      if (t > 0) v += o2p * E[(i * 5) * 9 + t - 1];
+      if (t + 1 <= i) v += (t + 1) * E[(i * 5) * 9 + t + 1];
+      E[((i + 1) * 5) * 9 + t] = v;
+    }
+  for (int i = 0; i <= li; ++i)
+    for (int j = 0; j < lj; ++j)
+      for (int t = 0; t <= i + j + 1; ++t) {
+        double v = PB * E[(i * 5 + j) * 9 + t];
+        if (t > 0) v += o2p * E[(i * 5 + j) * 9 + t - 1];
+        if (t + 1 <= i + j) v += (t + 1) * E[(i * 5 + j) * 9 + t + 1];
+        E[(i * 5 + j + 1) * 9 + t] = v;
+      }
+}
+
+// Schwarz bound per shell pair: Q = sqrt(max_{mu,nu} |(mu nu|mu nu)|) in FP64, rounded up to float32.
+__global__ void k_schwarz(int npair, const int* __restrict__ s1, const int* __restrict__ s2, const int* __restrict__ np,
+                          const int* __restrict__ poff, const int* __restrict__ sh_l, const int* __restrict__ ao,
+                          const double* __restrict__ f, PairData pd, const double* __restrict__ boys,
+                          const RStep* __restrict__ st, float* __restrict__ Q) {
+  int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= npair) return;
+  const int l1 = sh_l[s1[ip]], l2 = sh_l[s2[ip]], lp = l1 + l2, L = 2 * lp;
+  const int n1 = ncart(l1), n2 = ncart(l2);
+  double diag[100];
+  for (int x = 0; x < n1 * n2; ++x) diag[x] = 0.0;
+  double E1[3][225], E2[3][225], Ra[455], Rb[455], F[13];
+  for (int i = 0; i < np[ip]; ++i) {
+    const int pi = poff[ip] + i;
+    for (int d = 0; d < 3; ++d) md_e_rt(l1, l2, pd.PA[d * pd.n + pi], pd.PB[d * pd.n + pi], 0.5 / pd.p[pi], E1[d]);
+    for (int j = 0; j < np[ip]; ++j) {
+      const int pj = poff[ip] + j;
+      for (int d = 0; d < 3; ++d) md_e_rt(l1, l2, pd.PA[d * pd.n + pj], pd.PB[d * pd.n + pj], 0.5 / pd.p[pj], E2[d]);
+      const double p = pd.p[pi], q = pd.p[pj], rho = p * q / (p + q);
+      double X = pd.P[pi] - pd.P[pj], Y = pd.P[pd.n + pi] - pd.P[pd.n + pj], Z = pd.P[2 * pd.n + pi] - pd.P[2 * pd.n + pj];
+      const double T = rho * (X * X + Y * Y + Z * Z);
+      // generic Boys (runtime order): Taylor at the top order then downward
+      if (T < BOYS_TMAX) {
+        int k = __double2int_rn(T * BOYS_INV_H);
+        double dd = k * BOYS_H - T, acc = boys[k * BOYS_MDIM + L + BOYS_TAYLOR64 - 1];
+        for (int jj = BOYS_TAYLOR64 - 2; jj >= 0; --jj) acc = acc * dd / (jj + 1) + boys[k * BOYS_MDIM + L + jj];
+        F[L] = acc;
+        double e = exp(-T);
+        for (int m = L - 1; m >= 0; --m) F[m] = (2 * T * F[m + 1] + e) / (2 * m + 1);
+      } else {
+        double e = exp(-T);
+        F[0] = 0.5 * sqrt(3.14159265358979323846 / T);
+        for (int m = 0; m < L; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) / (2 * T);
+      }
+      const double pref = pd.pref[pi] * pd.pref[pj] / sqrt(p + q);
+      // R into Ra (ping-pong with Rb), result lands in Ra if L even else Rb
+      double* cur = Ra;
+      double* nxt = Rb;
+      cur[0] = pref * F[L];
+      for (int m = L - 1; m >= 0; --m) {
+        int ne = nherm(L - m);
+        for (int e = 0; e < ne; ++e) {
+          if (e == 0) { nxt[0] = pref * F[m]; continue; }
+          RStep s = st[e];
+          double pq = s.dir == 0 ? X : (s.dir == 1 ? Y : Z);
+          double v = pq * cur[s.dep1];
+          if (s.dep2 >= 0) v += s.k * cur[s.dep2];
+          nxt[e] = -2.0 * rho * v;
+        }
+        double* t = cur; cur = nxt; nxt = t;
+      }
+      const double* R = cur;
+      for (int mu = 0; mu < n1; ++mu) {
+        int ix, iy, iz;
+        cart_xyz(l1, mu, ix, iy, iz);
+        for (int nu = 0; nu < n2; ++nu) {
+          int jx, jy, jz;
+          cart_xyz(l2, nu, jx, jy, jz);
+          double v = 0.0;
+          for (int tx = 0; tx <= ix + jx; ++tx)
+            for (int ty = 0; ty <= iy + jy; ++ty)
+              for (int tz = 0; tz <= iz + jz; ++tz) {
+                const double ep = E1[0][(ix * 5 + jx) * 9 + tx] * E1[1][(iy * 5 + jy) * 9 + ty] * E1[2][(iz * 5 + jz) * 9 + tz];
+                for (int sx = 0; sx <= ix + jx; ++sx)
+                  for (int sy = 0; sy <= iy + jy; ++sy)
+                    for (int sz = 0; sz <= iz + jz; ++sz) {
+                      const double eq = E2[0][(ix * 5 + jx) * 9 + sx] * E2[1][(iy * 5 + jy) * 9 + sy] *
+                                        E2[2][(iz * 5 + jz) * 9 + sz];
+                      const double sg = ((sx + sy + sz) & 1) ? -1.0 : 1.0;
+                      v += ep * eq * sg * R[herm_index(tx + sx, ty + sy, tz + sz)];
+                    }
+              }
+          const double fn = f[ao[s1[ip]] + mu] * f[ao[s2[ip]] + nu];
+          diag[mu * n2 + nu] += v * fn * fn;
+        }
+      }
+    }
+  }
+  double mx = 0.0;
+  for (int x = 0; x < n1 * n2; ++x) mx = fmax(mx, fabs(diag[x]));
+  (void)lp;
+  Q[ip] = __double2float_ru(sqrt(mx));
+}
+
+__global__ void k_qmax(int n, const float* __restrict__ Q, unsigned int* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float v = i < n ? Q[i] : 0.0f;
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));  // Q >= 0: uint order = float order
+}
+
+// significance of each pair: (double)Q * (double)Qmax >= thresh; per-class counts
+__global__ void k_sig(int npair, const float* __restrict__ Q, const unsigned int* __restrict__ qmax_bits, double thresh,
+                      const int* __restrict__ cls, int* __restrict__ sig, int* __restrict__ ccount) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npair) return;
+  const double qmax = (double)__uint_as_float(*qmax_bits);
+  const int s = ((double)Q[i] * qmax >= thresh) ? 1 : 0;
+  sig[i] = s;
+  if (s) atomicAdd(ccount + cls[i], 1);
+}
+
+// rank of each significant pair inside its class: Q descending, pair index ascending
+__global__ void k_rank(int npair, const float* __restrict__ Q, const int* __restrict__ cls, const int* __restrict__ sig,
+                       const int* __restrict__ coff, int* __restrict__ sorted, int* __restrict__ pos) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npair || !sig[i]) return;
+  const float qi = Q[i];
+  const int ci = cls[i];
+  int r = 0;
+  for (int j = 0; j < npair; ++j) {
+    if (!sig[j] || cls[j] != ci) continue;
+    const float qj = Q[j];
+    if (qj > qi || (qj == qi && j < i)) ++r;
+  }
+  sorted[coff[ci] + r] = i;
+  pos[i] = r;
+}
+
+// counts[pair][Y] = number of kets of class Y with Q_i Q_k >= thresh (binary search on the Q-sorted list)
+__global__ void k_counts(int npair, const float* __restrict__ Q, const int* __restrict__ sig,
+                         const int* __restrict__ sorted, const int* __restrict__ coff, const int* __restrict__ ccount,
+                         double thresh, int* __restrict__ counts) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npair * NPAIRCLASS) return;
+  const int i = t / NPAIRCLASS, Y = t % NPAIRCLASS;
+  if (!sig[i]) { counts[t] = 0; return; }
+  const double qi = (double)Q[i];
+  const int* lst = sorted + coff[Y];
+  int lo = 0, hi = ccount[Y];  // first position with Q_i Q_k < thresh
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (qi * (double)Q[lst[mid]] >= thresh) lo = mid + 1; else hi = mid;
+  }
+  counts[t] = lo;
+}
+
+// prefix arrays of the K (canonical) and J (ordered) work lists, one thread per class pair
+__global__ void k_prefix(const int* __restrict__ sorted, const int* __restrict__ coff, const int* __restrict__ ccount,
+                         const int* __restrict__ counts, const int64_t* __restrict__ koff, const int64_t* __restrict__ joff,
+                         int64_t* __restrict__ kpre, int64_t* __restrict__ jpre, int64_t* __restrict__ ktot,
+                         int64_t* __restrict__ jtot, const int* __restrict__ np, int64_t* __restrict__ kprim) {
+  const int cp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cp >= NPAIRCLASS * NPAIRCLASS) return;
+  const int X = cp / NPAIRCLASS, Y = cp % NPAIRCLASS;
+  const int nb = ccount[X];
+  const int* bl = sorted + coff[X];
+  const int* kl = sorted + coff[Y];
+  int64_t accj = 0;
+  int64_t* jp = jpre + joff[cp];
+  for (int i = 0; i < nb; ++i) {
+    jp[i] = accj;
+    accj += counts[bl[i] * NPAIRCLASS + Y];
+  }
+  jp[nb] = accj;
+  jtot[cp] = accj;
+  if (Y <= X) {
+    int64_t acck = 0, accp = 0;
+    int64_t* kp = kpre + koff[cp];
+    for (int i = 0; i < nb; ++i) {
+      kp[i] = acck;
+      int c = counts[bl[i] * NPAIRCLASS + Y];
+      if (X == Y && c > i + 1) c = i + 1;
+      acck += c;
+      int64_t s = 0;
+      for (int k = 0; k < c; ++k) s += np[kl[k]];
+      accp += s * np[bl[i]];
+    }
+    kp[nb] = acck;
+    ktot[cp] = acck;
+    kprim[cp] = accp;
+  }
+}
+
+// D' = D f f (component norms folded in)
+__global__ void k_scale_d(int n, const double* __restrict__ D, const double* __restrict__ f, double* __restrict__ Dp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * n) return;
+  Dp[i] = D[i] * f[i / n] * f[i % n];
+}
+
+// Hermite density per primitive pair (Eq. j_formula, first sub-step):
+// D_Q = (-1)^|Q| s sum_{l in s1, s in s2} E_Q^{ls} D'_ls, s = 2 for s1 != s2
+// (the pair stands for both orders), 1 for a diagonal pair.
+__global__ void k_hermite_density(int npair, const int* __restrict__ s1, const int* __restrict__ s2,
+                                  const int* __restrict__ np, const int* __restrict__ poff, const int* __restrict__ hoff,
+                                  const int* __restrict__ sh_l, const int* __restrict__ ao, const int* __restrict__ sig,
+                                  PairData pd, const double* __restrict__ Dp, int nbf, double* __restrict__ Dh) {
+  int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= npair || !sig[ip]) return;
+  const int a = s1[ip], b = s2[ip], la = sh_l[a], lb = sh_l[b], H = nherm(la + lb);
+  const double sc = a == b ? 1.0 : 2.0;
+  double E[3][225];
+  for (int k = 0; k < np[ip]; ++k) {
+    const int pi = poff[ip] + k;
+    for (int d = 0; d < 3; ++d) md_e_rt(la, lb, pd.PA[d * pd.n + pi], pd.PB[d * pd.n + pi], 0.5 / pd.p[pi], E[d]);
+    double* out = Dh + hoff[ip] + (size_t)k * H;
+    for (int q = 0; q < H; ++q) out[q] = 0.0;
+    for (int mu = 0; mu < ncart(la); ++mu) {
+      int ix, iy, iz;
+      cart_xyz(la, mu, ix, iy, iz);
+      for (int nu = 0; nu < ncart(lb); ++nu) {
+        int jx, jy, jz;
+        cart_xyz(lb, nu, jx, jy, jz);
+        const double dv = sc * Dp[(size_t)(ao[a] + mu) * nbf + ao[b] + nu];
+        for (int tx = 0; tx <= ix + jx; ++tx)
+          for (int ty = 0; ty <= iy + jy; ++ty)
+            for (int tz = 0; tz <= iz + jz; ++tz) {
+              const double sg = ((tx + ty + tz) & 1) ? -1.0 : 1.0;
+              out[herm_index(tx, ty, tz)] +=
+                  sg * dv * E[0][(ix * 5 + jx) * 9 + tx] * E[1][(iy * 5 + jy) * 9 + ty] * E[2][(iz * 5 + jz) * 9 + tz];
+            }
+      }
+    }
+  }
+}
+
+// Cartesian J from Hermite J (Eq. j_formula, last sub-step): thread per (pair, mu, nu)
+__global__ void k_post_j(int npair, const int* __restrict__ s1, const int* __restrict__ s2, const int* __restrict__ np,
+                         const int* __restrict__ poff, const int* __restrict__ hoff, const int* __restrict__ sh_l,
+                         const int* __restrict__ ao, const int* __restrict__ sig, PairData pd,
+                         const double* __restrict__ Jh, const double* __restrict__ f, int nbf, double* __restrict__ J) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npair * 100) return;
+  const int ip = t / 100, c = t % 100;
+  if (!sig[ip]) return;
+  const int a = s1[ip], b = s2[ip], la = sh_l[a], lb = sh_l[b];
+  const int mu = c / 10, nu = c % 10;
+  if (mu >= ncart(la) || nu >= ncart(lb)) return;
+  int ix, iy, iz, jx, jy, jz;
+  cart_xyz(la, mu, ix, iy, iz);
+  cart_xyz(lb, nu, jx, jy, jz);
+  const int H = nherm(la + lb);
+  double E[3][225];
+  double v = 0.0;
+  for (int k = 0; k < np[ip]; ++k) {
+    const int pi = poff[ip] + k;
+    for (int d = 0; d < 3; ++d) md_e_rt(la, lb, pd.PA[d * pd.n + pi], pd.PB[d * pd.n + pi], 0.5 / pd.p[pi], E[d]);
+    const double* jh = Jh + hoff[ip] + (size_t)k * H;
+    for (int tx = 0; tx <= ix + jx; ++tx)
+      for (int ty = 0; ty <= iy + jy; ++ty)
+        for (int tz = 0; tz <= iz + jz; ++tz)
+          v += E[0][(ix * 5 + jx) * 9 + tx] * E[1][(iy * 5 + jy) * 9 + ty] * E[2][(iz * 5 + jz) * 9 + tz] *
+               jh[herm_index(tx, ty, tz)];
+  }
+  const int r = ao[a] + mu, cc = ao[b] + nu;
+  v *= f[r] * f[cc];
+  J[(size_t)r * nbf + cc] = v;
+  if (a != b) J[(size_t)cc * nbf + r] = v;
+}
+
+// K = (Kh + Kh^T) f f  (Eq. 8_fold_symmetry: the transposes carry permutations 5-8)
+__global__ void k_post_k(int n, const double* __restrict__ Kh, const double* __restrict__ f, double* __restrict__ K) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * n) return;
+  const int r = (int)(i / n), c = (int)(i % n);
+  K[i] = (Kh[i] + Kh[(size_t)c * n + r]) * f[r] * f[c];
+}
+
+// E_J = 1/2 sum D J, E_K = -1/4 sum D K; one block, fixed order (deterministic)
+__global__ void k_energy(int64_t nn, const double* __restrict__ D, const double* __restrict__ J,
+                         const double* __restrict__ K, double* __restrict__ E) {
+  __shared__ double sj[32], sk[32];
+  double aj = 0.0, ak = 0.0;
+  for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) {
+    if (J) aj += D[i] * J[i];
+    if (K) ak += D[i] * K[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    aj += __shfl_xor_sync(0xffffffffu, aj, o);
+    ak += __shfl_xor_sync(0xffffffffu, ak, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sj[threadIdx.x >> 5] = aj; sk[threadIdx.x >> 5] = ak; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tj = 0.0, tk = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tj += sj[w]; tk += sk[w]; }
+    E[0] = 0.5 * tj;
+    E[1] = -0.25 * tk;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return eri_fail(e_); \
+  } while (0)
+
+static int eri_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return ERI_ENOMEM;
+  return ERI_ECUDA;
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+static int grid1(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+static std::vector<RStep> make_rsteps() {
+  std::vector<RStep> st(nherm(LMAX_QUARTET));
+  for (int n = 0; n <= LMAX_QUARTET; ++n)
+    for (int r = 0; r <= n; ++r)
+      for (int v = 0; v <= r; ++v) {
+        int u = r - v, t = n - r;
+        int e = herm_index(t, u, v);
+        RStep s{};
+        s.t = (uint8_t)t; s.u = (uint8_t)u; s.v = (uint8_t)v;
+        s.dep1 = -1; s.dep2 = -1; s.k = 0; s.dir = 0;
+        int c[3] = {t, u, v};
+        if (n > 0) {
+          int d = t > 0 ? 0 : (u > 0 ? 1 : 2);
+          s.dir = (uint8_t)d;
+          int c1[3] = {c[0], c[1], c[2]};
+          c1[d] -= 1;
+          s.dep1 = (int16_t)herm_index(c1[0], c1[1], c1[2]);
+          if (c1[d] > 0) {
+            int c2[3] = {c1[0], c1[1], c1[2]};
+            c2[d] -= 1;
+            s.dep2 = (int16_t)herm_index(c2[0], c2[1], c2[2]);
+            s.k = (int16_t)c1[d];
+          }
+        }
+        st[e] = s;
+      }
+  return st;
+}
+
+int eri_plan_impl::alloc_pairs() {
+  CK(dalloc(&d_p, nprimpair)); CK(dalloc(&d_P, 3 * (size_t)nprimpair)); CK(dalloc(&d_PA, 3 * (size_t)nprimpair));
+  CK(dalloc(&d_PB, 3 * (size_t)nprimpair)); CK(dalloc(&d_pref, nprimpair));
+  CK(dalloc(&d_pf, nprimpair)); CK(dalloc(&d_Pf, 3 * (size_t)nprimpair)); CK(dalloc(&d_PAf, 3 * (size_t)nprimpair));
+  CK(dalloc(&d_PBf, 3 * (size_t)nprimpair)); CK(dalloc(&d_preff, nprimpair));
+  return ERI_OK;
+}
+
+PairData eri_plan_impl::pairdata() const {
+  PairData pd;
+  pd.p = d_p; pd.P = d_P; pd.PA = d_PA; pd.PB = d_PB; pd.pref = d_pref;
+  pd.pf = d_pf; pd.Pf = d_Pf; pd.PAf = d_PAf; pd.PBf = d_PBf; pd.preff = d_preff;
+  pd.n = nprimpair;
+  return pd;
+}
+
+ShellPairInfo eri_plan_impl::spinfo() const {
+  ShellPairInfo sp;
+  sp.s1 = d_ps1; sp.s2 = d_ps2; sp.np = d_pnp; sp.poff = d_ppoff; sp.ao1 = d_pao1; sp.ao2 = d_pao2; sp.hoff = d_phoff;
+  return sp;
+}
+
+// pair data + Schwarz + lists for the current device coordinates
+int eri_plan_impl::geometry(cudaStream_t s, bool rebuild_q) {
+  k_pairs<<<grid1(npair, 128), 128, 0, s>>>(npair, d_ps1, d_ps2, d_ppoff, d_sh_atom, d_sh_np, d_sh_po, d_exps, d_cn,
+                                        d_coords, nprimpair, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf, d_PBf,
+                                        d_preff);
+  CK(cudaGetLastError());
+  if (rebuild_q) {
+    k_schwarz<<<grid1(npair, 64), 64, 0, s>>>(npair, d_ps1, d_ps2, d_pnp, d_ppoff, d_sh_l, d_sh_ao, d_f, pairdata(), d_boys64,
+                                              d_rsteps, d_Q);
+    CK(cudaGetLastError());
+    return build_lists(thresh, s);
+  }
+  return ERI_OK;
+}
+
+int eri_plan_impl::build_lists(double th, cudaStream_t s) {
+  thresh = th;
+  CK(cudaMemsetAsync(d_qmax, 0, sizeof(unsigned int), s));
+  CK(cudaMemsetAsync(d_ccount, 0, sizeof(int) * NPAIRCLASS, s));
+  k_qmax<<<grid1(npair, 256), 256, 0, s>>>(npair, d_Q, d_qmax);
+  k_sig<<<grid1(npair, 256), 256, 0, s>>>(npair, d_Q, d_qmax, th, d_pcls, d_sig, d_ccount);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h_ccount, d_ccount, sizeof(int) * NPAIRCLASS, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int coff[NPAIRCLASS];
+  int acc = 0;
+  nsig = 0;
+  for (int X = 0; X < NPAIRCLASS; ++X) { coff[X] = acc; acc += h_ccount[X]; }
+  nsig = acc;
+  for (int X = 0; X < NPAIRCLASS; ++X) h_coff[X] = coff[X];
+  CK(cudaMemcpyAsync(d_coff, h_coff, sizeof(int) * NPAIRCLASS, cudaMemcpyHostToDevice, s));
+  k_rank<<<grid1(npair, 256), 256, 0, s>>>(npair, d_Q, d_pcls, d_sig, d_coff, d_sorted, d_pos);
+  k_counts<<<grid1((int64_t)npair * NPAIRCLASS, 256), 256, 0, s>>>(npair, d_Q, d_sig, d_sorted, d_coff, d_ccount, th,
+                                                               d_counts);
+  CK(cudaGetLastError());
+  int64_t ko = 0, jo = 0;
+  for (int X = 0; X < NPAIRCLASS; ++X)
+    for (int Y = 0; Y < NPAIRCLASS; ++Y) {
+      h_koff[X * NPAIRCLASS + Y] = ko;
+      h_joff[X * NPAIRCLASS + Y] = jo;
+      jo += h_ccount[X] + 1;
+      if (Y <= X) ko += h_ccount[X] + 1;
+    }
+  if (ko > kpre_cap) {
+    cudaFree(d_kpre);
+    CK(dalloc(&d_kpre, ko));
+    kpre_cap = ko;
+  }
+  if (jo > jpre_cap) {
+    cudaFree(d_jpre);
+    CK(dalloc(&d_jpre, jo));
+    jpre_cap = jo;
+  }
+  CK(cudaMemcpyAsync(d_koff, h_koff, sizeof(h_koff), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_joff, h_joff, sizeof(h_joff), cudaMemcpyHostToDevice, s));
+  k_prefix<<<1, 128, 0, s>>>(d_sorted, d_coff, d_ccount, d_counts, d_koff, d_joff, d_kpre, d_jpre, d_ktot, d_jtot,
+                             d_pnp, d_kprim);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h_ktot, d_ktot, sizeof(h_ktot), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h_jtot, d_jtot, sizeof(h_jtot), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h_kprim, d_kprim, sizeof(h_kprim), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return ERI_OK;
+}
+
+WorkList eri_plan_impl::klist(int X, int Y) const {
+  WorkList w;
+  w.bra = d_sorted + h_coff[X];
+  w.ket = d_sorted + h_coff[Y];
+  w.prefix = d_kpre + h_koff[X * NPAIRCLASS + Y];
+  w.nbra = h_ccount[X];
+  w.total = h_ktot[X * NPAIRCLASS + Y];
+  return w;
+}
+
+WorkList eri_plan_impl::jlist(int X, int Y) const {
+  WorkList w;
+  w.bra = d_sorted + h_coff[X];
+  w.ket = d_sorted + h_coff[Y];
+  w.prefix = d_jpre + h_joff[X * NPAIRCLASS + Y];
+  w.nbra = h_ccount[X];
+  w.total = h_jtot[X * NPAIRCLASS + Y];
+  return w;
+}
+
+void eri_plan_impl::release() {
+  void* ptrs[] = {d_sh_l, d_sh_atom, d_sh_np, d_sh_po, d_sh_ao, d_exps, d_coefs, d_cn, d_f, d_coords, d_ps1, d_ps2,
+                  d_pnp, d_ppoff, d_pao1, d_pao2, d_phoff, d_pcls, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf,
+                  d_PBf, d_preff, d_Q, d_qmax, d_sig, d_ccount, d_coff, d_sorted, d_pos, d_counts, d_koff, d_joff,
+                  d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Dherm,
+                  d_Jherm, d_status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+static const int kClassL1[NPAIRCLASS] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
+static const int kClassL2[NPAIRCLASS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+
+extern "C" int eri_default_opts(eri_opts_t* o) {
+  if (!o) return ERI_EINVAL;
+  o->thresh = 1e-12;
+  o->precision = ERI_FP64;
+  o->mixed_tau = 1e-5;
+  o->device = -1;
+  return ERI_OK;
+}
+
+extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const eri_opts_t* opts, eri_plan_t** out) {
+  if (!basis || !coords || !out || !basis->shells || !basis->exps || !basis->coefs) return ERI_EINVAL;
+  *out = nullptr;
+  const int ns = basis->nshell, na = basis->natom;
+  if (ns <= 0 || na <= 0 || ns > 100000) return ERI_EINVAL;
+  int nprim_tot = 0;
+  for (int s = 0; s < ns; ++s) {
+    const eri_shell_t& sh = basis->shells[s];
+    if (sh.l < 0 || sh.l > LMAX || sh.nprim <= 0 || sh.nprim > 64 || sh.atom < 0 || sh.atom >= na ||
+        sh.prim_offset < 0)
+      return sh.l > LMAX ? ERI_EUNSUPPORTED : ERI_EINVAL;
+    nprim_tot = std::max(nprim_tot, sh.prim_offset + sh.nprim);
+  }
+  for (int i = 0; i < nprim_tot; ++i)
+    if (!(basis->exps[i] > 0.0) || !std::isfinite(basis->exps[i]) || !std::isfinite(basis->coefs[i])) return ERI_EINVAL;
+  for (int i = 0; i < 3 * na; ++i)
+    if (!std::isfinite(coords[i])) return ERI_EINVAL;
+  eri_opts_t o;
+  eri_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.thresh >= 0.0) || !(o.mixed_tau >= 0.0) || (o.precision != ERI_FP64 && o.precision != ERI_MIXED))
+    return ERI_EINVAL;
+
+  eri_plan_impl* P = new (std::nothrow) eri_plan_impl();
+  if (!P) return ERI_ENOMEM;
+  P->opts = o;
+  if (o.device >= 0) {
+    if (cudaSetDevice(o.device) != cudaSuccess) { delete P; return ERI_ECUDA; }
+  }
+  cudaGetDevice(&P->device);
+  cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, P->device);
+  P->nshell = ns;
+  P->natom = na;
+  std::vector<int> l(ns), atom(ns), np(ns), po(ns), ao(ns + 1);
+  int nbf = 0;
+  for (int s = 0; s < ns; ++s) {
+    l[s] = basis->shells[s].l; atom[s] = basis->shells[s].atom; np[s] = basis->shells[s].nprim;
+    po[s] = basis->shells[s].prim_offset; ao[s] = nbf; nbf += ncart(l[s]);
+  }
+  ao[ns] = nbf;
+  P->nbf = nbf;
+  // shell pairs in pair-index order (a >= b), oriented so that s1 has the higher l
+  const int npair = ns * (ns + 1) / 2;
+  P->npair = npair;
+  std::vector<int> ps1(npair), ps2(npair), pnp(npair), ppoff(npair), pao1(npair), pao2(npair), phoff(npair), pcls(npair);
+  int64_t nprimpair = 0, nherm_tot = 0;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b <= a; ++b) {
+      int ip = a * (a + 1) / 2 + b;
+      int x = a, y = b;
+      if (l[b] > l[a]) { x = b; y = a; }
+      ps1[ip] = x; ps2[ip] = y;
+      pnp[ip] = np[x] * np[y];
+      ppoff[ip] = (int)nprimpair;
+      pao1[ip] = ao[x]; pao2[ip] = ao[y];
+      phoff[ip] = (int)nherm_tot;
+      pcls[ip] = pair_class(l[x], l[y]);
+      nprimpair += pnp[ip];
+      nherm_tot += (int64_t)pnp[ip] * nherm(l[x] + l[y]);
+    }
+  if (nprimpair > (1LL << 30) || nherm_tot > (1LL << 31) - 1) { delete P; return ERI_EUNSUPPORTED; }
+  P->nprimpair = (int)nprimpair;
+  P->nherm_tot = nherm_tot;
+  int rc = ERI_OK;
+#define CKP(x)                                   \
+  do {                                           \
+    cudaError_t e_ = (x);                        \
+    if (e_ != cudaSuccess) { rc = eri_fail(e_); goto fail; } \
+  } while (0)
+  {
+    cudaStream_t s = 0;
+    std::vector<RStep> st = make_rsteps();
+    CKP(dalloc(&P->d_sh_l, ns)); CKP(dalloc(&P->d_sh_atom, ns)); CKP(dalloc(&P->d_sh_np, ns));
+    CKP(dalloc(&P->d_sh_po, ns)); CKP(dalloc(&P->d_sh_ao, ns + 1));
+    CKP(dalloc(&P->d_exps, nprim_tot)); CKP(dalloc(&P->d_coefs, nprim_tot)); CKP(dalloc(&P->d_cn, nprim_tot));
+    CKP(dalloc(&P->d_f, nbf)); CKP(dalloc(&P->d_coords, 3 * na));
+    CKP(dalloc(&P->d_ps1, npair)); CKP(dalloc(&P->d_ps2, npair)); CKP(dalloc(&P->d_pnp, npair));
+    CKP(dalloc(&P->d_ppoff, npair)); CKP(dalloc(&P->d_pao1, npair)); CKP(dalloc(&P->d_pao2, npair));
+    CKP(dalloc(&P->d_phoff, npair)); CKP(dalloc(&P->d_pcls, npair));
+    CKP(dalloc(&P->d_Q, npair)); CKP(dalloc(&P->d_qmax, 1)); CKP(dalloc(&P->d_sig, npair));
+    CKP(dalloc(&P->d_ccount, NPAIRCLASS)); CKP(dalloc(&P->d_coff, NPAIRCLASS)); CKP(dalloc(&P->d_sorted, npair));
+    CKP(dalloc(&P->d_pos, npair)); CKP(dalloc(&P->d_counts, (size_t)npair * NPAIRCLASS));
+    CKP(dalloc(&P->d_koff, NPAIRCLASS * NPAIRCLASS)); CKP(dalloc(&P->d_joff, NPAIRCLASS * NPAIRCLASS));
+    CKP(dalloc(&P->d_ktot, NPAIRCLASS * NPAIRCLASS)); CKP(dalloc(&P->d_jtot, NPAIRCLASS * NPAIRCLASS));
+    CKP(dalloc(&P->d_kprim, NPAIRCLASS * NPAIRCLASS));
+    CKP(dalloc(&P->d_boys64, (size_t)BOYS_NT * BOYS_MDIM)); CKP(dalloc(&P->d_boys32, (size_t)BOYS_NT * BOYS_MDIM));
+    CKP(dalloc(&P->d_rsteps, st.size()));
+    CKP(dalloc(&P->d_Dp, (size_t)nbf * nbf)); CKP(dalloc(&P->d_Kh, (size_t)nbf * nbf));
+    CKP(dalloc(&P->d_Dherm, nherm_tot)); CKP(dalloc(&P->d_Jherm, nherm_tot));
+    CKP(dalloc(&P->d_status, 1));
+    if (P->alloc_pairs() != ERI_OK) { rc = ERI_ENOMEM; goto fail; }
+    std::vector<double> ex(basis->exps, basis->exps + nprim_tot), co(basis->coefs, basis->coefs + nprim_tot);
+    CKP(cudaMemcpy(P->d_sh_l, l.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_sh_atom, atom.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_sh_np, np.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_sh_po, po.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_sh_ao, ao.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_exps, ex.data(), sizeof(double) * nprim_tot, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_coefs, co.data(), sizeof(double) * nprim_tot, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_coords, coords, sizeof(double) * 3 * na, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_ps1, ps1.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_ps2, ps2.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_pnp, pnp.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_ppoff, ppoff.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_pao1, pao1.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_pao2, pao2.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_phoff, phoff.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_pcls, pcls.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_rsteps, st.data(), sizeof(RStep) * st.size(), cudaMemcpyHostToDevice));
+    CKP(cudaMemset(P->d_status, 0, sizeof(int)));
+    k_normalize<<<grid1(ns, 64), 64>>>(ns, P->d_sh_l, P->d_sh_np, P->d_sh_po, P->d_exps, P->d_coefs, P->d_cn);
+    k_compfac<<<grid1(ns, 64), 64>>>(ns, P->d_sh_l, P->d_sh_ao, P->d_f);
+    k_boys_table<<<grid1(BOYS_NT, 128), 128>>>(P->d_boys64, P->d_boys32);
+    CKP(cudaGetLastError());
+    P->thresh = o.thresh;
+    rc = P->geometry(s, true);
+    if (rc != ERI_OK) goto fail;
+    CKP(cudaDeviceSynchronize());
+  }
+#undef CKP
+  *out = reinterpret_cast<eri_plan_t*>(P);
+  return ERI_OK;
+fail:
+  P->release();
+  delete P;
+  return rc;
+}
+
+extern "C" int eri_plan_set_coords(eri_plan_t* plan, const double* coords_dev, int32_t freeze_lists, void* stream) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !coords_dev) return ERI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(P->device));
+  CK(cudaMemcpyAsync(P->d_coords, coords_dev, sizeof(double) * 3 * P->natom, cudaMemcpyDeviceToDevice, s));
+  return P->geometry(s, freeze_lists == 0);
+}
+
+extern "C" int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double* K, double thresh, int32_t precision,
+                            void* stream) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !D || (!J && !K)) return ERI_EINVAL;
+  if (precision != ERI_FP64 && precision != ERI_MIXED) return ERI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(P->device));
+  if (thresh >= 0.0 && thresh != P->thresh) {
+    int rc = P->build_lists(thresh, s);
+    if (rc != ERI_OK) return rc;
+  }
+  const int n = P->nbf;
+  const int64_t nn = (int64_t)n * n;
+  k_scale_d<<<grid1(nn, 256), 256, 0, s>>>(n, D, P->d_f, P->d_Dp);
+  CK(cudaGetLastError());
+  const int prec = precision == ERI_MIXED ? 1 : 0;  // mixed tiering arrives with the FP32 path
+  (void)prec;
+  double fj = 0.0, fk = 0.0;
+  if (J) {
+    CK(cudaMemsetAsync(P->d_Jherm, 0, sizeof(double) * (size_t)P->nherm_tot, s));
+    k_hermite_density<<<grid1(P->npair, 64), 64, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_pnp, P->d_ppoff,
+                                                          P->d_phoff, P->d_sh_l, P->d_sh_ao, P->d_sig, P->pairdata(),
+                                                          P->d_Dp, n, P->d_Dherm);
+    CK(cudaGetLastError());
+    JArgs ja;
+    ja.pd = P->pairdata(); ja.sp = P->spinfo(); ja.boys64 = P->d_boys64; ja.boys32 = P->d_boys32;
+    ja.rsteps = P->d_rsteps; ja.Dherm = P->d_Dherm; ja.Jherm = P->d_Jherm; ja.tier = nullptr; ja.tier_want = 0;
+    for (int X = 0; X < NPAIRCLASS; ++X)
+      for (int Y = 0; Y < NPAIRCLASS; ++Y) {
+        ja.wl = P->jlist(X, Y);
+        if (ja.wl.total == 0) continue;
+        const int lab = kClassL1[X] + kClassL2[X], lcd = kClassL1[Y] + kClassL2[Y];
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (lab) {
+          case 0: e = launch_j_lab0(lcd, 0, ja, s, P->nsm); break;
+          case 1: e = launch_j_lab1(lcd, 0, ja, s, P->nsm); break;
+          case 2: e = launch_j_lab2(lcd, 0, ja, s, P->nsm); break;
+          case 3: e = launch_j_lab3(lcd, 0, ja, s, P->nsm); break;
+          case 4: e = launch_j_lab4(lcd, 0, ja, s, P->nsm); break;
+          case 5: e = launch_j_lab5(lcd, 0, ja, s, P->nsm); break;
+          case 6: e = launch_j_lab6(lcd, 0, ja, s, P->nsm); break;
+        }
+        CK(e);
+      }
+    CK(cudaMemsetAsync(J, 0, sizeof(double) * nn, s));
+    k_post_j<<<grid1((int64_t)P->npair * 100, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_pnp, P->d_ppoff,
+                                                            P->d_phoff, P->d_sh_l, P->d_sh_ao, P->d_sig, P->pairdata(),
+                                                            P->d_Jherm, P->d_f, n, J);
+    CK(cudaGetLastError());
+  }
+  if (K) {
+    CK(cudaMemsetAsync(P->d_Kh, 0, sizeof(double) * nn, s));
+    KArgs ka;
+    ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.boys64 = P->d_boys64; ka.boys32 = P->d_boys32;
+    ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Kh = P->d_Kh; ka.tier = nullptr; ka.tier_want = 0; ka.nbf = n;
+    for (int X = 0; X < NPAIRCLASS; ++X)
+      for (int Y = 0; Y <= X; ++Y) {
+        ka.wl = P->klist(X, Y);
+        ka.same_class = X == Y;
+        if (ka.wl.total == 0) continue;
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (X) {
+          case 0: e = launch_k_bra0(Y, 0, ka, s, P->nsm); break;
+          case 1: e = launch_k_bra1(Y, 0, ka, s, P->nsm); break;
+          case 2: e = launch_k_bra2(Y, 0, ka, s, P->nsm); break;
+          case 3: e = launch_k_bra3(Y, 0, ka, s, P->nsm); break;
+          case 4: e = launch_k_bra4(Y, 0, ka, s, P->nsm); break;
+          case 5: e = launch_k_bra5(Y, 0, ka, s, P->nsm); break;
+          case 6: e = launch_k_bra6(Y, 0, ka, s, P->nsm); break;
+          case 7: e = launch_k_bra7(Y, 0, ka, s, P->nsm); break;
+          case 8: e = launch_k_bra8(Y, 0, ka, s, P->nsm); break;
+          case 9: e = launch_k_bra9(Y, 0, ka, s, P->nsm); break;
+        }
+        CK(e);
+      }
+    k_post_k<<<grid1(nn, 256), 256, 0, s>>>(n, P->d_Kh, P->d_f, K);
+    CK(cudaGetLastError());
+  }
+  P->last_flops_j = fj;
+  P->last_flops_k = fk;
+  return ERI_OK;
+}
+
+extern "C" int eri_energy(eri_plan_t* plan, const double* D, const double* J, const double* K, double* E_out,
+                          void* stream) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !D || !E_out) return ERI_EINVAL;
+  CK(cudaSetDevice(P->device));
+  k_energy<<<1, 1024, 0, (cudaStream_t)stream>>>((int64_t)P->nbf * P->nbf, D, J, K, E_out);
+  CK(cudaGetLastError());
+  return ERI_OK;
+}
+
+extern "C" int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int32_t want_j, int32_t want_k,
+                           void* stream) {
+  (void)plan; (void)D; (void)dEdR; (void)want_j; (void)want_k; (void)stream;
+  return ERI_EUNSUPPORTED;
+}
+
+extern "C" int eri_get_lists(eri_plan_t* plan, float* Q, int32_t* sig, int32_t* counts, int32_t* sorted,
+                             int32_t* class_count) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P) return ERI_EINVAL;
+  CK(cudaSetDevice(P->device));
+  CK(cudaDeviceSynchronize());
+  if (Q) CK(cudaMemcpy(Q, P->d_Q, sizeof(float) * P->npair, cudaMemcpyDeviceToHost));
+  if (sig) CK(cudaMemcpy(sig, P->d_sig, sizeof(int) * P->npair, cudaMemcpyDeviceToHost));
+  if (counts) CK(cudaMemcpy(counts, P->d_counts, sizeof(int) * P->npair * NPAIRCLASS, cudaMemcpyDeviceToHost));
+  if (sorted) CK(cudaMemcpy(sorted, P->d_sorted, sizeof(int) * P->nsig, cudaMemcpyDeviceToHost));
+  if (class_count) memcpy(class_count, P->h_ccount, sizeof(int) * NPAIRCLASS);
+  return ERI_OK;
+}
+
+extern "C" int eri_get_stats(eri_plan_t* plan, eri_stats_t* st) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !st) return ERI_EINVAL;
+  CK(cudaSetDevice(P->device));
+  memset(st, 0, sizeof(*st));
+  st->nbf = P->nbf;
+  st->nshell = P->nshell;
+  st->npair = P->npair;
+  st->nsig_pair = P->nsig;
+  for (int i = 0; i < NPAIRCLASS * NPAIRCLASS; ++i) {
+    st->quartets_j += P->h_jtot[i];
+    int X = i / NPAIRCLASS, Y = i % NPAIRCLASS;
+    if (Y <= X) {
+      st->quartets_k += P->h_ktot[i];
+      st->prim_quartets_k += P->h_kprim[i];
+    }
+  }
+  st->flops_j = P->last_flops_j;
+  st->flops_k = P->last_flops_k;
+  int status = 0;
+  CK(cudaMemcpy(&status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  st->device_status = status;
+  return ERI_OK;
+}
+
+extern "C" int eri_plan_destroy(eri_plan_t* plan) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P) return ERI_OK;
+  cudaSetDevice(P->device);
+  cudaDeviceSynchronize();
+  P->release();
+  delete P;
+  return ERI_OK;
+}
+
+extern "C" const char* eri_strerror(int code) {
+  switch (code) {
+    case ERI_OK: return "success";
+    case ERI_EINVAL: return "invalid argument";
+    case ERI_ENOMEM: return "out of memory";
+    case ERI_ECUDA: return "CUDA runtime error";
+    case ERI_EUNSUPPORTED: return "unsupported request";
+    case ERI_ETIMEOUT: return "bounded device wait timed out";
+    case ERI_EDEVICE: return "device-side check failed";
+  }
+  return "unknown error";
+}

@@ -1,0 +1,52 @@
+// Internal plan state behind the opaque eri_plan_t of include/eri.h.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "common.cuh"
+#include "../../include/eri.h"
+
+struct eri_plan_impl {
+  eri_opts_t opts;
+  int device = 0, nsm = 1;
+  int nshell = 0, natom = 0, nbf = 0, npair = 0, nprimpair = 0, nsig = 0;
+  int64_t nherm_tot = 0;
+  double thresh = 1e-12;
+  double last_flops_j = 0.0, last_flops_k = 0.0;
+  // shells
+  int *d_sh_l = nullptr, *d_sh_atom = nullptr, *d_sh_np = nullptr, *d_sh_po = nullptr, *d_sh_ao = nullptr;
+  double *d_exps = nullptr, *d_coefs = nullptr, *d_cn = nullptr, *d_f = nullptr, *d_coords = nullptr;
+  // shell pairs (pair-index order)
+  int *d_ps1 = nullptr, *d_ps2 = nullptr, *d_pnp = nullptr, *d_ppoff = nullptr, *d_pao1 = nullptr, *d_pao2 = nullptr;
+  int *d_phoff = nullptr, *d_pcls = nullptr;
+  // primitive pairs
+  double *d_p = nullptr, *d_P = nullptr, *d_PA = nullptr, *d_PB = nullptr, *d_pref = nullptr;
+  float *d_pf = nullptr, *d_Pf = nullptr, *d_PAf = nullptr, *d_PBf = nullptr, *d_preff = nullptr;
+  // screening and lists
+  float* d_Q = nullptr;
+  unsigned int* d_qmax = nullptr;
+  int *d_sig = nullptr, *d_ccount = nullptr, *d_coff = nullptr, *d_sorted = nullptr, *d_pos = nullptr,
+      *d_counts = nullptr;
+  int64_t *d_koff = nullptr, *d_joff = nullptr, *d_kpre = nullptr, *d_jpre = nullptr, *d_ktot = nullptr,
+          *d_jtot = nullptr, *d_kprim = nullptr;
+  int64_t kpre_cap = 0, jpre_cap = 0;
+  int h_ccount[eri::NPAIRCLASS] = {}, h_coff[eri::NPAIRCLASS] = {};
+  int64_t h_koff[eri::NPAIRCLASS * eri::NPAIRCLASS] = {}, h_joff[eri::NPAIRCLASS * eri::NPAIRCLASS] = {};
+  int64_t h_ktot[eri::NPAIRCLASS * eri::NPAIRCLASS] = {}, h_jtot[eri::NPAIRCLASS * eri::NPAIRCLASS] = {};
+  int64_t h_kprim[eri::NPAIRCLASS * eri::NPAIRCLASS] = {};
+  // tables
+  double* d_boys64 = nullptr;
+  float* d_boys32 = nullptr;
+  eri::RStep* d_rsteps = nullptr;
+  // per-build workspace
+  double *d_Dp = nullptr, *d_Kh = nullptr, *d_Dherm = nullptr, *d_Jherm = nullptr;
+  int* d_status = nullptr;
+
+  int alloc_pairs();
+  int geometry(cudaStream_t s, bool rebuild_q);
+  int build_lists(double th, cudaStream_t s);
+  eri::PairData pairdata() const;
+  eri::ShellPairInfo spinfo() const;
+  eri::WorkList klist(int X, int Y) const;
+  eri::WorkList jlist(int X, int Y) const;
+  void release();
+};

@@ -1,0 +1,82 @@
+"""The C-ABI library loads, exports every symbol include/eri.h declares, and
+rejects invalid plans on the host before touching a GPU (no compute calls)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def eri():
+    from paper_2406_14920_gb300.build import build
+    build()
+    import paper_2406_14920_gb300 as m
+    return m
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\**(eri_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_exports_every_declared_symbol(eri):
+    L = eri.lib()
+    names = _declared()
+    assert {"eri_plan", "eri_build_jk", "eri_jk_grad"} <= names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_strerror(eri):
+    assert eri.strerror(0) == "success"
+    assert "invalid" in eri.strerror(-1)
+
+
+def _basis_struct(eri, shells, exps, coefs, natom):
+    arr = (eri.ShellT * len(shells))()
+    for i, (a, l, n, o) in enumerate(shells):
+        arr[i].atom, arr[i].l, arr[i].nprim, arr[i].prim_offset = a, l, n, o
+    ex = np.asarray(exps, np.float64)
+    co = np.asarray(coefs, np.float64)
+    b = eri.BasisT(len(shells), natom, arr, ex.ctypes.data_as(C.POINTER(C.c_double)),
+                   co.ctypes.data_as(C.POINTER(C.c_double)))
+    return b, (arr, ex, co)
+
+
+@pytest.mark.parametrize("case,code", [
+    ("l4", -4), ("nprim0", -1), ("negexp", -1), ("badatom", -1), ("nancoord", -1)])
+def test_plan_rejects_bad_input(eri, case, code):
+    shells = [(0, 0, 1, 0), (1, 1, 1, 1)]
+    exps, coefs = [1.0, 0.5], [1.0, 1.0]
+    coords = np.zeros((2, 3))
+    coords[1, 0] = 1.5
+    if case == "l4":
+        shells[1] = (1, 4, 1, 1)
+    if case == "nprim0":
+        shells[0] = (0, 0, 0, 0)
+    if case == "negexp":
+        exps[1] = -0.5
+    if case == "badatom":
+        shells[1] = (5, 1, 1, 1)
+    if case == "nancoord":
+        coords[0, 1] = np.nan
+    b, keep = _basis_struct(eri, shells, exps, coefs, 2)
+    h = C.c_void_p()
+    rc = eri.lib().eri_plan(C.byref(b), coords.ctypes.data_as(C.POINTER(C.c_double)), None, C.byref(h))
+    assert rc == code
+    assert not h.value
+
+
+def test_null_arguments(eri):
+    L = eri.lib()
+    assert L.eri_plan(None, None, None, None) == -1
+    assert L.eri_build_jk(None, None, None, None, -1.0, 0, None) == -1
+    assert L.eri_plan_destroy(None) == 0

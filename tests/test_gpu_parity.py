@@ -1,0 +1,108 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle.
+
+- lists (Schwarz Q as float32, significance, per-class counts, class-sorted
+  order) bit-exact;
+- FP64 J and K within 1e-10 max abs element (the hot-path tolerance);
+- E_J, E_K within 1e-10.
+Sizes: workload 0 (75 bf, 21 shells: every class of shell pair, several
+warps' worth of quartets per class and ragged tails) and small systems that
+isolate class families.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def eri():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_14920_gb300.build import build
+    build()
+    import paper_2406_14920_gb300 as m
+    return m
+
+
+def _oracle_lists(basis, Q, thresh):
+    o = oracle.Oracle(basis)
+    sig, counts = o.lists(thresh, Q)
+    ns = basis.nshell
+    cls = np.zeros(Q.shape[0], int)
+    for a in range(ns):
+        for b in range(a + 1):
+            hi, lo = max(basis.shell_l[a], basis.shell_l[b]), min(basis.shell_l[a], basis.shell_l[b])
+            cls[a * (a + 1) // 2 + b] = hi * (hi + 1) // 2 + lo
+    idx = [i for i in range(Q.shape[0]) if sig[i]]
+    idx.sort(key=lambda i: (cls[i], -float(Q[i]), i))
+    return sig, counts, np.asarray(idx, np.int32)
+
+
+@pytest.mark.parametrize("thresh", [1e-12, 1e-8])
+def test_lists_bit_exact_w0(eri, thresh):
+    basis, D = W.workload(0)
+    plan = eri.Plan(basis, thresh=thresh)
+    L = plan.lists()
+    o = oracle.Oracle(basis)
+    Qo = o.schwarz()
+    assert np.array_equal(L["Q"].view(np.uint32), Qo.view(np.uint32))
+    sig, counts, srt = _oracle_lists(basis, Qo, thresh)
+    assert np.array_equal(L["sig"], sig)
+    assert np.array_equal(L["counts"], counts)
+    assert np.array_equal(L["sorted"], srt)
+
+
+def _jk_check(eri, basis, D, thresh=1e-12):
+    import torch
+    plan = eri.Plan(basis, thresh=thresh)
+    Dt = torch.from_numpy(D).cuda()
+    J, K = plan.build_jk(Dt)
+    E = plan.energy(Dt, J, K).cpu().numpy()
+    J, K = J.cpu().numpy(), K.cpu().numpy()
+    o = oracle.Oracle(basis)
+    Q = o.schwarz()
+    Jr, Kr = o.jk(D, thresh, Q)
+    ej, ek = o.energy(D, Jr, Kr)
+    dj, dk = np.abs(J - Jr).max(), np.abs(K - Kr).max()
+    assert dj < TOL, f"max|dJ| = {dj:.3e}"
+    assert dk < TOL, f"max|dK| = {dk:.3e}"
+    assert abs(E[0] - ej) < TOL and abs(E[1] - ek) < TOL, (E, ej, ek)
+    return plan
+
+
+def test_jk_fp64_w0(eri):
+    basis, D = W.workload(0)
+    _jk_check(eri, basis, D)
+
+
+@pytest.mark.parametrize("comp", [["1s", "1s"], ["1p", "1s1p"], ["1d", "1s1p"], ["1f", "1p"], ["1d1f", "1s"],
+                                  ["1f", "1f"], ["2s1p1d1f"], ["1s1p1d1f", "1s1p1d1f", "1s1p"]])
+def test_jk_fp64_small(eri, comp):
+    basis, D = W.small_system(comp, seed=len(comp) * 7 + len(comp[0]))
+    _jk_check(eri, basis, D)
+
+
+def test_jk_threshold_and_only_one(eri):
+    import torch
+    basis, D = W.small_system(["2s1p1d", "1s1p1f", "1s1p"], seed=9)
+    plan = eri.Plan(basis, thresh=1e-12)
+    Dt = torch.from_numpy(D).cuda()
+    o = oracle.Oracle(basis)
+    Q = o.schwarz()
+    for thresh in (1e-6, 1e-3):
+        J, K = plan.build_jk(Dt, thresh=thresh)
+        Jr, Kr = o.jk(D, thresh, Q)
+        assert np.abs(J.cpu().numpy() - Jr).max() < TOL
+        assert np.abs(K.cpu().numpy() - Kr).max() < TOL
+    Jo, Ko = plan.build_jk(Dt, want_k=False, thresh=1e-12)
+    assert Ko is None
+    Jr, Kr = o.jk(D, 1e-12, Q)
+    assert np.abs(Jo.cpu().numpy() - Jr).max() < TOL
+    Jn, Kn = plan.build_jk(Dt, want_j=False)
+    assert Jn is None and np.abs(Kn.cpu().numpy() - Kr).max() < TOL
