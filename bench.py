@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark: integral-direct J+K build on GB300, mixed precision vs FP64.
+
+One step = one eri_build_jk (J and K) of the 60-atom / 900-basis-function
+workload (40 light atoms 2s1p, 20 heavy atoms 4s3p2d1f, seed 1001) with the
+Schwarz threshold 1e-12; D is already resident in HBM when the timed region
+starts.  The headline value is significant canonical shell quartets per second
+of the mixed-precision path (FP64 tier above tau = 1e-5, FP32 below).  The FP64
+path is timed on the same workload for the mixed-vs-FP64 comparison, and the
+energy error of the mixed path is measured against it.
+
+--impl reference runs the oracle (plain FP64 CPU code) on seeded samples of the
+same quartet list, on the host cores, as the reference arm.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, every rank builds its own copy of the workload (weak
+scaling: independent problems, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "J+K build time & ERI quartets/s: mixed vs FP64 on GB300 at ≤1e-6 Eh error"
+UNIT = "quartets/s"
+WORKLOAD_ID = 1
+WORKLOAD_DESC = ("60 atoms in a seeded random packing (min distance 2.0 bohr): 40 light 2s1p + 20 heavy "
+                 "4s3p2d1f Cartesian shells, 900 basis functions, s/p 3-primitive contractions, D = C C^T "
+                 "with C a random orthonormal 900x120, seed 1001")
+THRESH = 1e-12
+TAU = 1e-5
+# peaks for the ALU roofline: FP32 = 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz;
+# FP64 = GB300 nominal dense FP64 rate
+PEAK_TFLOPS = {0: 1.25, 1: 80.5}
+CLASS_NAMES = ["ss", "ps", "pp", "ds", "dp", "dd", "fs", "fp", "fd", "ff"]
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# quartet sampling from the plan's lists (for the oracle legs)
+# ---------------------------------------------------------------------------
+def sample_quartets(lists, basis, n, seed):
+    """Seeded uniform sample of significant canonical shell quartets."""
+    rng = np.random.default_rng(seed)
+    cc = lists["class_count"]
+    coff = np.concatenate([[0], np.cumsum(cc)])
+    srt, counts = lists["sorted"], lists["counts"]
+    per_cp, bra_w = [], {}
+    for X in range(10):
+        for Y in range(X + 1):
+            bras = srt[coff[X]:coff[X + 1]]
+            nk = counts[bras, Y].astype(np.int64)
+            if X == Y:
+                nk = np.minimum(nk, np.arange(1, len(bras) + 1))
+            per_cp.append(((X, Y), int(nk.sum())))
+            bra_w[(X, Y)] = nk
+    tot = np.array([t for _, t in per_cp], dtype=np.float64)
+    picks = rng.choice(len(per_cp), size=n, p=tot / tot.sum())
+    out = np.zeros((n, 4), np.int32)
+    for q, ci in enumerate(picks):
+        (X, Y), _ = per_cp[ci]
+        nk = bra_w[(X, Y)]
+        i = rng.choice(len(nk), p=nk / nk.sum())
+        k = rng.integers(0, nk[i])
+        pb = int(srt[coff[X] + i])
+        pk = int(srt[coff[Y] + k])
+        for off, p in ((0, pb), (2, pk)):
+            a = int((np.sqrt(8 * p + 1) - 1) // 2)
+            while a * (a + 1) // 2 > p:
+                a -= 1
+            while (a + 1) * (a + 2) // 2 <= p:
+                a += 1
+            out[q, off], out[q, off + 1] = a, p - a * (a + 1) // 2
+    return out
+
+
+def oracle_rate(basis, quartets, target_s):
+    """Oracle (plain FP64 CPU) quartets/s on a bounded sample of the workload."""
+    import oracle
+    o = oracle.Oracle(basis)
+    n0 = min(len(quartets), 64)
+    t = time.perf_counter()
+    o.quartet_batch(quartets[:n0])
+    dt = max(time.perf_counter() - t, 1e-6)
+    n = int(min(len(quartets), max(n0, n0 * target_s / dt)))
+    t = time.perf_counter()
+    o.quartet_batch(quartets[:n])
+    dt = time.perf_counter() - t
+    return n / dt, n, dt, oracle.max_threads()
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2406_14920_gb300", "csrc"))):
+        if f.endswith((".cuh", ".cu")):
+            h.update(open(os.path.join(ROOT, "paper_2406_14920_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(X, Y, tier):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except ValueError:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("kernels", {}).get(f"{CLASS_NAMES[X]}|{CLASS_NAMES[Y]}|{tier}")
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2406_14920_gb300 as eri
+    import workloads as W
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    basis, D = W.workload(WORKLOAD_ID)
+    n = basis.nbf
+    plan = eri.Plan(basis, thresh=THRESH, precision=eri.ERI_MIXED, mixed_tau=TAU, device=local_rank, profile=True)
+    stream = torch.cuda.current_stream(dev)
+    Dd = torch.from_numpy(D).to(dev)
+    J = torch.empty((n, n), dtype=torch.float64, device=dev)
+    K = torch.empty((n, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+    nq = plan.stats()["quartets_k"]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(precision, steps, warmup):
+        for _ in range(warmup):
+            plan.build_jk(Dd, J, K, precision=precision)
+        torch.cuda.synchronize()
+        plan.profile()  # drop warm-up records
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for e0, e1 in ev:
+            flush.fill_(1.0)
+            e0.record(stream)
+            plan.build_jk(Dd, J, K, precision=precision)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        return ms, plan.profile()
+
+    # energies of both paths (untimed) for the accuracy claim
+    plan.build_jk(Dd, J, K, precision=eri.ERI_FP64)
+    e64 = plan.energy(Dd, J, K).cpu().numpy().copy()
+    plan.build_jk(Dd, J, K, precision=eri.ERI_MIXED)
+    emx = plan.energy(Dd, J, K).cpu().numpy().copy()
+    nq32 = plan.stats()["quartets_k_fp32"]
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms_mixed, prof = timed(eri.ERI_MIXED, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms64, prof64 = timed(eri.ERI_FP64, args.fp64_steps, args.fp64_warmup)
+
+    # end to end through the public API: pinned host D in, J and K back to pinned host
+    Dh = torch.from_numpy(D).pin_memory()
+    Jh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    Kh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    Dtmp = torch.empty_like(Dd)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for e0, e1 in ev:
+        flush.fill_(1.0)
+        e0.record(stream)
+        Dtmp.copy_(Dh, non_blocking=True)
+        plan.build_jk(Dtmp, J, K, precision=eri.ERI_MIXED)
+        Jh.copy_(J, non_blocking=True)
+        Kh.copy_(K, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    plan.profile()
+
+    # max over ranks
+    vals = torch.tensor([ms_mixed, ms64, ms_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms_mixed, ms64, ms_e2e = [float(v) for v in vals.cpu()]
+
+    # roofline of the dominant kernel (largest device-time share in the mixed step)
+    dom = max(prof, key=lambda r: r["ms"])
+    per_launch_ms = dom["ms"] / dom["launches"]
+    achieved = dom["flops"] / (per_launch_ms * 1e-3) / 1e12
+    peak = PEAK_TFLOPS[dom["tier"]]
+    tot_ms = sum(r["ms"] for r in prof)
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": traffic_for(dom["bra_class"], dom["ket_class"], dom["tier"]),
+                "kernel": f"({CLASS_NAMES[dom['bra_class']]}|{CLASS_NAMES[dom['ket_class']]}) "
+                          f"{'FP64' if dom['tier'] == 0 else 'FP32'}",
+                "share": round(dom["ms"] / tot_ms, 4),
+                "peak_source": "FP64: GB300 nominal 1.25 TFLOP/s; FP32: 152 SM x 128 x 2 x 2.07 GHz"}
+    fl_total = sum(r["flops"] for r in prof)
+    launches_per_step = len(prof) + 4  # class launches + D scaling, D block maxima, two symmetrisations
+
+    out = {
+        "metric": METRIC, "value": world * nq * args.steps / (ms_mixed * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed tiers)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "nbf": n, "schwarz_thresh": THRESH, "mixed_tau": TAU,
+                   "quartets_per_step": nq, "fp32_quartets_per_step": nq32,
+                   "l2": "flushed before every timed step (256 MiB device write)",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "fp64": {"ms_per_step": ms64 / args.fp64_steps, "value": world * nq * args.fp64_steps / (ms64 * 1e-3),
+                 "steps": args.fp64_steps, "warmup": args.fp64_warmup},
+        "speedup_mixed_vs_fp64": (ms64 / args.fp64_steps) / (ms_mixed / args.steps),
+        "energy": {"E_J_fp64": float(e64[0]), "E_K_fp64": float(e64[1]),
+                   "dE_J_mixed": float(emx[0] - e64[0]), "dE_K_mixed": float(emx[1] - e64[1])},
+        "algorithmic_tflops": {"mixed": fl_total / ((tot_ms / args.steps) * 1e-3) / 1e12},
+        "roofline": roofline,
+        "e2e": {"value": world * nq * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 16 * n * n},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        quartets = sample_quartets(plan.lists(), basis, 4000, seed=1234)
+        rate, ns, dt, cores = oracle_rate(basis, quartets, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{ns} seeded uniformly sampled significant canonical shell quartets of "
+                                         f"this workload, contracted ERI blocks in FP64 ({dt:.1f} s)"}
+    plan.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    import oracle
+    import workloads as W
+    basis, _ = W.workload(WORKLOAD_ID)
+    lists = _lists_without_gpu(basis)
+    quartets = sample_quartets(lists, basis, 20000, seed=4321)
+    o = oracle.Oracle(basis)
+    # size one step to about args.cpu_seconds of CPU work
+    t = time.perf_counter()
+    o.quartet_batch(quartets[:64])
+    per_q = (time.perf_counter() - t) / 64
+    nstep = int(min(len(quartets), max(64, args.cpu_seconds / max(per_q, 1e-9))))
+    for s in range(args.warmup):
+        o.quartet_batch(quartets[(s * 97) % max(1, len(quartets) - nstep):][:nstep])
+    t = time.perf_counter()
+    for s in range(args.steps):
+        o.quartet_batch(quartets[(s * 131) % max(1, len(quartets) - nstep):][:nstep])
+    dt = time.perf_counter() - t
+    value = nstep * args.steps / dt
+    cores = oracle.max_threads()
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "schwarz_thresh": THRESH,
+                       "step": f"{nstep} seeded sampled significant canonical shell quartets"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{nstep} sampled quartets per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def _lists_without_gpu(basis):
+    """Significant pair lists from the oracle's Schwarz bounds (same rule as the library)."""
+    import oracle
+    o = oracle.Oracle(basis)
+    Q = o.schwarz()
+    sig, counts = o.lists(THRESH, Q)
+    ns = basis.nshell
+    cls = np.zeros(Q.shape[0], int)
+    for a in range(ns):
+        for b in range(a + 1):
+            hi, lo = max(basis.shell_l[a], basis.shell_l[b]), min(basis.shell_l[a], basis.shell_l[b])
+            cls[a * (a + 1) // 2 + b] = hi * (hi + 1) // 2 + lo
+    idx = sorted([i for i in range(Q.shape[0]) if sig[i]], key=lambda i: (cls[i], -float(Q[i]), i))
+    cc = np.bincount(cls[idx], minlength=10).astype(np.int32)
+    return {"Q": Q, "sig": sig, "counts": counts, "sorted": np.asarray(idx, np.int32), "class_count": cc}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-warmup", type=int, default=1)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2406_14920_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

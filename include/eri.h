@@ -69,6 +69,9 @@ typedef struct {
   int32_t precision;  /* ERI_FP64 (default) or ERI_MIXED */
   double mixed_tau;   /* FP64 tier: Q_ab Q_cd max|D| >= mixed_tau; default 1e-5 (paper Sec. 4.1) */
   int32_t device;     /* CUDA device ordinal; default: current device */
+  int32_t j_engine;   /* J-only builds (K == NULL): 1 = Hermite J-engine of Eq. j_formula
+                         (default), 0 = contraction of Cartesian ERIs */
+  int32_t profile;    /* 1: record CUDA events around every class launch (see eri_get_profile) */
 } eri_opts_t;
 
 typedef struct {
@@ -143,6 +146,25 @@ int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int32_t want_j,
  */
 int eri_get_lists(eri_plan_t* plan, float* Q, int32_t* sig, int32_t* counts, int32_t* sorted,
                   int32_t* class_count);
+
+/* One class launch of the J/K build, as seen by eri_get_profile. */
+typedef struct {
+  int32_t bra_class, ket_class; /* pair classes 0..9 = ss ps pp ds dp dd fs fp fd ff */
+  int32_t tier;                 /* 0 = FP64, 1 = FP32 (mixed precision) */
+  int32_t launches;             /* profiled launches summed into ms */
+  double ms;                    /* total device time of those launches (CUDA events on the build stream) */
+  int64_t quartets;             /* canonical shell quartets of the last build's launch */
+  int64_t prim_quartets;        /* primitive quartets of the last build's launch */
+  double flops;                 /* algorithmic FLOPs of the last build's launch */
+} eri_launch_prof_t;
+
+/*
+ * Per-launch device times of every eri_build_jk since the previous call, for a
+ * plan created with opts.profile = 1 (Cartesian J/K path).  Fills up to cap
+ * entries of out (host), sets *count to the number of (class pair, tier)
+ * launches, synchronises, and resets the record.
+ */
+int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t cap, int32_t* count);
 
 /* Statistics of the plan and of its last build (host copy; synchronises). */
 int eri_get_stats(eri_plan_t* plan, eri_stats_t* stats);

@@ -57,6 +57,8 @@ def lib():
         L.or_k_block.argtypes = [C.c_void_p, d, C.c_double, f, C.c_int, C.c_int, d]
         L.or_grad.argtypes = [C.c_void_p, d, C.c_double, f, C.c_int, C.c_int, d]
         L.or_max_threads.restype = C.c_int
+        L.or_quartet_batch.argtypes = [C.c_void_p, C.c_int, i]
+        L.or_quartet_batch.restype = C.c_double
         _lib = L
     return _lib
 
@@ -196,6 +198,11 @@ class Oracle:
         out = np.zeros(ncart(self.l[a]) * ncart(self.l[c]))
         lib().or_k_block(self.h, _d(np.ascontiguousarray(D)), float(thresh), _f(Q), a, c, _d(out))
         return out.reshape(ncart(self.l[a]), ncart(self.l[c]))
+
+    def quartet_batch(self, abcd):
+        """Evaluate contracted quartets abcd[n, 4] (sum of |ERI| returned)."""
+        a = np.ascontiguousarray(abcd, np.int32)
+        return lib().or_quartet_batch(self.h, int(a.shape[0]), _i(a))
 
     def grad(self, D, thresh=1e-12, Q=None, want_j=True, want_k=True):
         Q = self.schwarz() if Q is None else np.ascontiguousarray(Q, np.float32)

@@ -919,3 +919,26 @@ int or_max_threads(void) {
   return 1;
 #endif
 }
+
+/*
+ * Evaluate a list of contracted shell quartets (abcd[4*nq], user shell
+ * indices) with or_eri_block, OpenMP over quartets; returns sum of |ERI| so the
+ * work cannot be skipped.  Used to time the oracle on a sample of a workload.
+ */
+double or_quartet_batch(void* h, int nq, const int32_t* abcd) {
+  double total = 0.0;
+#pragma omp parallel reduction(+ : total)
+  {
+    double* X = (double*)malloc(sizeof(double) * 10000);
+#pragma omp for schedule(dynamic, 4)
+    for (int q = 0; q < nq; ++q) {
+      or_ctx* c = (or_ctx*)h;
+      int a = abcd[4 * q], b = abcd[4 * q + 1], cc = abcd[4 * q + 2], d = abcd[4 * q + 3];
+      or_eri_block(h, a, b, cc, d, X);
+      int n = ncart(c->l[a]) * ncart(c->l[b]) * ncart(c->l[cc]) * ncart(c->l[d]);
+      for (int i = 0; i < n; ++i) total += fabs(X[i]);
+    }
+    free(X);
+  }
+  return total;
+}

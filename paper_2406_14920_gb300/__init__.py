@@ -38,7 +38,12 @@ class BasisT(C.Structure):
 
 class OptsT(C.Structure):
     _fields_ = [("thresh", C.c_double), ("precision", C.c_int32), ("mixed_tau", C.c_double),
-                ("device", C.c_int32)]
+                ("device", C.c_int32), ("j_engine", C.c_int32), ("profile", C.c_int32)]
+
+
+class LaunchProfT(C.Structure):
+    _fields_ = [("bra_class", C.c_int32), ("ket_class", C.c_int32), ("tier", C.c_int32), ("launches", C.c_int32),
+                ("ms", C.c_double), ("quartets", C.c_int64), ("prim_quartets", C.c_int64), ("flops", C.c_double)]
 
 
 class StatsT(C.Structure):
@@ -65,6 +70,7 @@ def lib():
         L.eri_get_lists.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.eri_get_stats.argtypes = [vp, C.POINTER(StatsT)]
+        L.eri_get_profile.argtypes = [vp, C.POINTER(LaunchProfT), i32, C.POINTER(C.c_int32)]
         L.eri_plan_destroy.argtypes = [vp]
         L.eri_strerror.argtypes = [C.c_int]
         L.eri_strerror.restype = C.c_char_p
@@ -94,7 +100,8 @@ def _stream_ptr(stream):
 class Plan:
     """An eri_plan over one basis and geometry (see include/eri.h)."""
 
-    def __init__(self, basis, coords=None, thresh=1e-12, precision=ERI_FP64, mixed_tau=1e-5, device=None):
+    def __init__(self, basis, coords=None, thresh=1e-12, precision=ERI_FP64, mixed_tau=1e-5, device=None,
+                 j_engine=True, profile=False):
         L = lib()
         self.basis = basis
         self.nbf = basis.nbf
@@ -118,6 +125,8 @@ class Plan:
         o.precision = int(precision)
         o.mixed_tau = float(mixed_tau)
         o.device = -1 if device is None else int(device)
+        o.j_engine = int(bool(j_engine))
+        o.profile = int(bool(profile))
         h = C.c_void_p()
         _check(L.eri_plan(C.byref(b), crd.ctypes.data_as(C.POINTER(C.c_double)), C.byref(o), C.byref(h)), "eri_plan")
         self.h = h
@@ -177,6 +186,13 @@ class Plan:
                                    P(srt, C.c_int32), P(cc, C.c_int32)), "eri_get_lists")
         return {"Q": Q, "sig": sig, "counts": counts.reshape(self.npair, 10), "sorted": srt[:int(cc.sum())],
                 "class_count": cc}
+
+    def profile(self):
+        """Per (class pair, tier) device times of the builds since the last call."""
+        buf = (LaunchProfT * 256)()
+        n = C.c_int32()
+        _check(lib().eri_get_profile(self.h, buf, 256, C.byref(n)), "eri_get_profile")
+        return [{k: getattr(buf[i], k) for k, _ in LaunchProfT._fields_} for i in range(min(n.value, 256))]
 
     def stats(self):
         s = StatsT()

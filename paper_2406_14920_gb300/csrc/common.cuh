@@ -19,14 +19,16 @@ constexpr int LMAX_PAIR = 2 * LMAX;  // Hermite order of a pair
 constexpr int LMAX_QUARTET = 4 * LMAX + 1;  // +1: gradient raises one bra index
 constexpr int NPAIRCLASS = 10;       // ss ps pp ds dp dd fs fp fd ff
 
-// Boys table: F_m(T_k) at T_k = k * BOYS_H, k = 0..BOYS_NT-1, m = 0..BOYS_MDIM-1.
+// Boys tables on the grid T_k = k * BOYS_H, k = 0..BOYS_NT-1:
+//   FP64: [k][m][j] = F_{m+j}(T_k) / j!, j < 8, m <= BOYS_MMAX (Taylor coefficients),
+//   FP32: [k][m][j], j < 4;  plus exp(-T_k) in both precisions.
 constexpr double BOYS_H = 0.05;
 constexpr double BOYS_INV_H = 20.0;
 constexpr double BOYS_TMAX = 36.0;   // Taylor + downward recursion below, asymptote + upward above
 constexpr int BOYS_NT = 722;         // covers T < 36 + h/2
-constexpr int BOYS_TAYLOR64 = 8;     // |dT| <= 0.025: error ~ dT^8/8! ~ 4e-18 relative
-constexpr int BOYS_TAYLOR32 = 4;     // dT^4/4! ~ 1.6e-8 relative
-constexpr int BOYS_MDIM = LMAX_QUARTET + 1 + BOYS_TAYLOR64;  // 22
+constexpr int BOYS_J64 = 8;          // |dT| <= 0.025: truncation ~ dT^8/8! ~ 4e-18 relative
+constexpr int BOYS_J32 = 4;          // dT^4/4! ~ 1.6e-8 relative
+constexpr int BOYS_MMAX = LMAX_QUARTET;  // 13
 
 __host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 // number of Hermite triples (t,u,v) with t+u+v <= n
@@ -35,7 +37,7 @@ __host__ __device__ constexpr int pair_class(int l1, int l2) { return l1 * (l1 +
 
 // Cartesian components of shell l in lexicographic order (x desc, then y desc):
 // xx,xy,xz,yy,yz,zz for d; xxx,xxy,...,zzz for f.  k-th component exponents.
-__host__ __device__ inline void cart_xyz(int l, int k, int& x, int& y, int& z) {
+__host__ __device__ constexpr void cart_xyz(int l, int k, int& x, int& y, int& z) {
   int r = 0;
   while ((r + 1) * (r + 2) / 2 <= k) ++r;  // r = y + z
   z = k - r * (r + 1) / 2;
@@ -45,9 +47,29 @@ __host__ __device__ inline void cart_xyz(int l, int k, int& x, int& y, int& z) {
 
 // Compact Hermite index: triples grouped by n = t+u+v, inside a group ordered
 // by (u+v) then v (same order as Cartesian components).
-__host__ __device__ inline int herm_index(int t, int u, int v) {
-  int n = t + u + v, r = u + v;
-  return nherm(n - 1) + r * (r + 1) / 2 + v;
+__host__ __device__ constexpr int herm_index(int t, int u, int v) {
+  return nherm(t + u + v - 1) + (u + v) * (u + v + 1) / 2 + v;
+}
+// inverse of herm_index (compile-time foldable when e is a constant)
+__host__ __device__ constexpr int herm_n(int e) {
+  int n = 0;
+  while (nherm(n) <= e) ++n;
+  return n;
+}
+__host__ __device__ constexpr int herm_v(int e) {
+  int k = e - nherm(herm_n(e) - 1), r = 0;
+  while ((r + 1) * (r + 2) / 2 <= k) ++r;
+  return k - r * (r + 1) / 2;
+}
+__host__ __device__ constexpr int herm_u(int e) {
+  int k = e - nherm(herm_n(e) - 1), r = 0;
+  while ((r + 1) * (r + 2) / 2 <= k) ++r;
+  return r - (k - r * (r + 1) / 2);
+}
+__host__ __device__ constexpr int herm_t(int e) {
+  int k = e - nherm(herm_n(e) - 1), r = 0;
+  while ((r + 1) * (r + 2) / 2 <= k) ++r;
+  return herm_n(e) - r;
 }
 
 // One entry of the R recursion table (per compact Hermite index e):
@@ -71,6 +93,8 @@ struct PairData {
   const float* PAf;
   const float* PBf;
   const float* preff;
+  const double* E;     // Hermite coefficients per primitive pair: 3 x (l1+1)(l2+1)(l1+l2+1), x then y then z
+  const float* Ef;
   int n;               // number of primitive pairs (row stride of the [3][n] arrays)
 };
 
@@ -82,6 +106,7 @@ struct ShellPairInfo {
   const int32_t* ao1;      // AO offset of s1
   const int32_t* ao2;      // AO offset of s2
   const int32_t* hoff;     // offset of the Hermite density / Hermite J of the first primitive pair
+  const int32_t* eoff;     // offset of the E tables of the first primitive pair
 };
 
 // Per (bra class, ket class) work description, all device pointers.
@@ -93,51 +118,82 @@ struct WorkList {
   int64_t total;
 };
 
-// Boys F_0..F_M at T (FP64): Taylor around the nearest grid point for F_M, then
-// downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1); above BOYS_TMAX the
-// asymptote F_0 = sqrt(pi/T)/2 and upward recursion.  Own derivation from
-// dF_m/dT = -F_{m+1}; CUDA's exp/sqrt are called, not reproduced.
+// Boys F_0..F_M at T.  Below BOYS_TMAX: Taylor expansion of F_M around the
+// nearest grid point, F_M(T) = sum_j F_{M+j}(T_k) (T_k - T)^j / j!  (from
+// dF_m/dT = -F_{m+1}), exp(-T) = exp(-T_k) exp(T_k - T) with a short Taylor
+// series, then the downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1).
+// Above: F_0 = sqrt(pi/T)/2 (erf(sqrt T) = 1 to double precision) and the upward
+// recursion F_{m+1} = ((2m+1) F_m - exp(-T)) / (2T).  Our own construction
+// ("interpolation and downward recursion", Sec. 2.3); CUDA's exp/rsqrt are
+// called where needed, not reproduced.
+struct BoysTabs {
+  const double* c64;  // [BOYS_NT][BOYS_MMAX+1][BOYS_J64]
+  const double* e64;  // [BOYS_NT] exp(-T_k)
+  const float* c32;   // [BOYS_NT][BOYS_MMAX+1][BOYS_J32]
+  const float* e32;
+};
+
 template <int M>
-__device__ __forceinline__ void boys_f64(double T, const double* __restrict__ tab, double* F) {
+__device__ __forceinline__ void boys_f64(double T, const BoysTabs& bt, double* F) {
   if (T < BOYS_TMAX) {
-    int k = __double2int_rn(T * BOYS_INV_H);
-    double d = k * BOYS_H - T;  // -(T - T_k)
-    const double* row = tab + k * BOYS_MDIM + M;
-    double acc = __ldg(row + BOYS_TAYLOR64 - 1);
+    const int k = __double2int_rn(T * BOYS_INV_H);
+    const double d = k * BOYS_H - T;
+    const double* c = bt.c64 + ((size_t)k * (BOYS_MMAX + 1) + M) * BOYS_J64;
+    double f = __ldg(c + BOYS_J64 - 1);
 #pragma unroll
-    for (int j = BOYS_TAYLOR64 - 2; j >= 0; --j) acc = fma(acc, d * (1.0 / (j + 1)), __ldg(row + j));
-    F[M] = acc;
-    double e = exp(-T);
-    double t2 = 2.0 * T;
+    for (int j = BOYS_J64 - 2; j >= 0; --j) f = fma(f, d, __ldg(c + j));
+    F[M] = f;
+    if (M > 0) {
+      // exp(d), |d| <= h/2, 8 Taylor terms
+      double g = 1.0 / 5040.0;
+      g = fma(g, d, 1.0 / 720.0);
+      g = fma(g, d, 1.0 / 120.0);
+      g = fma(g, d, 1.0 / 24.0);
+      g = fma(g, d, 1.0 / 6.0);
+      g = fma(g, d, 0.5);
+      g = fma(g, d, 1.0);
+      g = fma(g, d, 1.0);
+      const double e = __ldg(bt.e64 + k) * g;
+      const double t2 = 2.0 * T;
 #pragma unroll
-    for (int m = M - 1; m >= 0; --m) F[m] = fma(t2, F[m + 1], e) * (1.0 / (2 * m + 1));
+      for (int m = M - 1; m >= 0; --m) F[m] = fma(t2, F[m + 1], e) * (1.0 / (2 * m + 1));
+    }
   } else {
-    double e = exp(-T);
-    double inv2t = 0.5 / T;
-    F[0] = 0.5 * sqrt(3.14159265358979323846 / T);
+    const double e = exp(-T);
+    const double rt = rsqrt(T);
+    F[0] = 0.88622692545275801365 * rt;  // sqrt(pi)/2
+    const double inv2t = 0.5 * rt * rt;
 #pragma unroll
     for (int m = 0; m < M; ++m) F[m + 1] = fma((double)(2 * m + 1), F[m], -e) * inv2t;
   }
 }
 
 template <int M>
-__device__ __forceinline__ void boys_f32(float T, const float* __restrict__ tab, float* F) {
+__device__ __forceinline__ void boys_f32(float T, const BoysTabs& bt, float* F) {
   if (T < (float)BOYS_TMAX) {
-    int k = __float2int_rn(T * (float)BOYS_INV_H);
-    float d = k * (float)BOYS_H - T;
-    const float* row = tab + k * BOYS_MDIM + M;
-    float acc = __ldg(row + BOYS_TAYLOR32 - 1);
+    const int k = __float2int_rn(T * (float)BOYS_INV_H);
+    const float d = k * (float)BOYS_H - T;
+    const float* c = bt.c32 + ((size_t)k * (BOYS_MMAX + 1) + M) * BOYS_J32;
+    float f = __ldg(c + BOYS_J32 - 1);
 #pragma unroll
-    for (int j = BOYS_TAYLOR32 - 2; j >= 0; --j) acc = fmaf(acc, d * (1.0f / (j + 1)), __ldg(row + j));
-    F[M] = acc;
-    float e = __expf(-T);
-    float t2 = 2.0f * T;
+    for (int j = BOYS_J32 - 2; j >= 0; --j) f = fmaf(f, d, __ldg(c + j));
+    F[M] = f;
+    if (M > 0) {
+      float g = 1.0f / 24.0f;
+      g = fmaf(g, d, 1.0f / 6.0f);
+      g = fmaf(g, d, 0.5f);
+      g = fmaf(g, d, 1.0f);
+      g = fmaf(g, d, 1.0f);
+      const float e = __ldg(bt.e32 + k) * g;
+      const float t2 = 2.0f * T;
 #pragma unroll
-    for (int m = M - 1; m >= 0; --m) F[m] = fmaf(t2, F[m + 1], e) * (1.0f / (2 * m + 1));
+      for (int m = M - 1; m >= 0; --m) F[m] = fmaf(t2, F[m + 1], e) * (1.0f / (2 * m + 1));
+    }
   } else {
-    float e = __expf(-T);
-    float inv2t = 0.5f / T;
-    F[0] = 0.5f * sqrtf(3.14159265f / T);
+    const float e = __expf(-T);
+    const float rt = rsqrtf(T);
+    F[0] = 0.88622692545f * rt;
+    const float inv2t = 0.5f * rt * rt;
 #pragma unroll
     for (int m = 0; m < M; ++m) F[m + 1] = fmaf((float)(2 * m + 1), F[m], -e) * inv2t;
   }
@@ -145,14 +201,10 @@ __device__ __forceinline__ void boys_f32(float T, const float* __restrict__ tab,
 
 template <typename T> struct Boys;
 template <> struct Boys<double> {
-  template <int M> __device__ static void eval(double t, const double* tab64, const float*, double* F) {
-    boys_f64<M>(t, tab64, F);
-  }
+  template <int M> __device__ static void eval(double t, const BoysTabs& bt, double* F) { boys_f64<M>(t, bt, F); }
 };
 template <> struct Boys<float> {
-  template <int M> __device__ static void eval(float t, const double*, const float* tab32, float* F) {
-    boys_f32<M>(t, tab32, F);
-  }
+  template <int M> __device__ static void eval(float t, const BoysTabs& bt, float* F) { boys_f32<M>(t, bt, F); }
 };
 
 // McMurchie-Davidson E^{ij}_t for one direction, i <= LI, j <= LJ, t <= i+j
@@ -194,6 +246,37 @@ __device__ __forceinline__ void md_e_1d(T PA, T PB, T o2p, T* E) {
 }
 
 __device__ __forceinline__ double atomic_add_d(double* p, double v) { return atomicAdd(p, v); }
+
+// R^0_{tuv}, t+u+v <= L, in registers (fully unrolled; all indices are
+// compile-time constants).  Same scaled recursion as r_build_warp, done in
+// place: inside a level, entries are updated from the highest index down so
+// the level m+1 values they read are still intact.
+template <int L, typename T>
+__device__ __forceinline__ void r_build_reg(const T* F, T pref, T X, T Y, T Z, T c, T* R) {
+  const T Xc = c * X, Yc = c * Y, Zc = c * Z;
+  R[0] = pref * F[L];
+#pragma unroll
+  for (int m = L - 1; m >= 0; --m) {
+#pragma unroll
+    for (int e = nherm(L - m) - 1; e >= 1; --e) {
+      const int t = herm_t(e), u = herm_u(e), v = herm_v(e);
+      if (t > 0) {
+        T val = Xc * R[herm_index(t - 1, u, v)];
+        if (t > 1) val = fma(c * T(t - 1), R[herm_index(t - 2, u, v)], val);
+        R[e] = val;
+      } else if (u > 0) {
+        T val = Yc * R[herm_index(0, u - 1, v)];
+        if (u > 1) val = fma(c * T(u - 1), R[herm_index(0, u - 2, v)], val);
+        R[e] = val;
+      } else {
+        T val = Zc * R[herm_index(0, 0, v - 1)];
+        if (v > 1) val = fma(c * T(v - 1), R[herm_index(0, 0, v - 2)], val);
+        R[e] = val;
+      }
+    }
+    R[0] = pref * F[m];
+  }
+}
 
 // Error codes written by device code into the plan's status word.
 enum : int { DEV_OK = 0, DEV_BOUNDS = 1 };

@@ -3,7 +3,7 @@
 // in parallel.
 #pragma once
 #include <algorithm>
-#include "kernels.cuh"
+#include "kernels_b.cuh"
 
 namespace eri {
 
@@ -42,42 +42,57 @@ inline cudaError_t launch_persistent(Kern kern, size_t smem, int64_t items, int 
   return cudaSuccess;
 }
 
+// Register kernel for the smallest classes, warp kernel for the rest.
+__host__ __device__ constexpr bool use_thread_kernel(int la, int lb, int lc, int ld) {
+  return la + lb + lc + ld <= 3 && ncart(la) * ncart(lb) * ncart(lc) * ncart(ld) <= 27;
+}
+
 template <int LA, int LB, int LC, int LD, typename T>
-cudaError_t launch_k_t(const KArgs& a, cudaStream_t s, int nsm) {
-  if (a.wl.total <= 0) return cudaSuccess;
-  using S = KShape<LA, LB, LC, LD, T>;
-  constexpr int WPB = 4;
+cudaError_t launch_jk_t(const JKArgs& a, cudaStream_t s, int nsm) {
+  if (a.k.wl.total <= 0) return cudaSuccess;
   LaunchInfo li;
-  auto kern = k_warp_kernel<LA, LB, LC, LD, T>;
-  cudaError_t e = launch_persistent(kern, WPB * S::smem_per_warp(), a.wl.total, WPB, nsm, &li);
-  if (e != cudaSuccess) return e;
-  kern<<<li.grid, li.block, li.smem, s>>>(a);
+  if constexpr (use_thread_kernel(LA, LB, LC, LD)) {
+    auto kern = jk_thread_kernel<LA, LB, LC, LD, T>;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, 0);
+    if (e != cudaSuccess) return e;
+    int64_t need = (a.k.wl.total + 127) / 128;
+    int64_t grid = std::min<int64_t>(need, (int64_t)nsm * std::max(occ, 1));
+    kern<<<(int)grid, 128, 0, s>>>(a);
+  } else {
+    using S = BShape<LA, LB, LC, LD, T>;
+    constexpr int WPB = 4;
+    auto kern = jk_warp_kernel<LA, LB, LC, LD, T>;
+    cudaError_t e = launch_persistent(kern, WPB * S::smem_per_warp(), a.k.wl.total, WPB, nsm, &li);
+    if (e != cudaSuccess) return e;
+    kern<<<li.grid, li.block, li.smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
 template <int X, int Y>
-cudaError_t launch_k_xy(int prec, const KArgs& a, cudaStream_t s, int nsm) {
+cudaError_t launch_jk_xy(int prec, const JKArgs& a, cudaStream_t s, int nsm) {
   if constexpr (Y <= X) {
     constexpr int LA = ClassL<X>::l1, LB = ClassL<X>::l2, LC = ClassL<Y>::l1, LD = ClassL<Y>::l2;
-    return prec ? launch_k_t<LA, LB, LC, LD, float>(a, s, nsm) : launch_k_t<LA, LB, LC, LD, double>(a, s, nsm);
+    return prec ? launch_jk_t<LA, LB, LC, LD, float>(a, s, nsm) : launch_jk_t<LA, LB, LC, LD, double>(a, s, nsm);
   } else {
     return cudaErrorInvalidValue;
   }
 }
 
 template <int X>
-cudaError_t launch_k_x(int Y, int prec, const KArgs& a, cudaStream_t s, int nsm) {
+cudaError_t launch_jk_x(int Y, int prec, const JKArgs& a, cudaStream_t s, int nsm) {
   switch (Y) {
-    case 0: return launch_k_xy<X, 0>(prec, a, s, nsm);
-    case 1: return launch_k_xy<X, 1>(prec, a, s, nsm);
-    case 2: return launch_k_xy<X, 2>(prec, a, s, nsm);
-    case 3: return launch_k_xy<X, 3>(prec, a, s, nsm);
-    case 4: return launch_k_xy<X, 4>(prec, a, s, nsm);
-    case 5: return launch_k_xy<X, 5>(prec, a, s, nsm);
-    case 6: return launch_k_xy<X, 6>(prec, a, s, nsm);
-    case 7: return launch_k_xy<X, 7>(prec, a, s, nsm);
-    case 8: return launch_k_xy<X, 8>(prec, a, s, nsm);
-    case 9: return launch_k_xy<X, 9>(prec, a, s, nsm);
+    case 0: return launch_jk_xy<X, 0>(prec, a, s, nsm);
+    case 1: return launch_jk_xy<X, 1>(prec, a, s, nsm);
+    case 2: return launch_jk_xy<X, 2>(prec, a, s, nsm);
+    case 3: return launch_jk_xy<X, 3>(prec, a, s, nsm);
+    case 4: return launch_jk_xy<X, 4>(prec, a, s, nsm);
+    case 5: return launch_jk_xy<X, 5>(prec, a, s, nsm);
+    case 6: return launch_jk_xy<X, 6>(prec, a, s, nsm);
+    case 7: return launch_jk_xy<X, 7>(prec, a, s, nsm);
+    case 8: return launch_jk_xy<X, 8>(prec, a, s, nsm);
+    case 9: return launch_jk_xy<X, 9>(prec, a, s, nsm);
   }
   return cudaErrorInvalidValue;
 }
@@ -113,16 +128,16 @@ cudaError_t launch_j_lab(int LCD, int prec, const JArgs& a, cudaStream_t s, int 
 }
 
 // entry points defined in the per-class translation units
-cudaError_t launch_k_bra0(int, int, const KArgs&, cudaStream_t, int);
-cudaError_t launch_k_bra1(int, int, const KArgs&, cudaStream_t, int);
-cudaError_t launch_k_bra2(int, int, const KArgs&, cudaStream_t, int);
-cudaError_t launch_k_bra3(int, int, const KArgs&, cudaStream_t, int);
-cudaError_t launch_k_bra4(int, int, const KArgs&, cudaStream_t, int);
-cudaError_t launch_k_bra5(int, int, const KArgs&, cudaStream_t, int);
-cudaError_t launch_k_bra6(int, int, const KArgs&, cudaStream_t, int);
-cudaError_t launch_k_bra7(int, int, const KArgs&, cudaStream_t, int);
-cudaError_t launch_k_bra8(int, int, const KArgs&, cudaStream_t, int);
-cudaError_t launch_k_bra9(int, int, const KArgs&, cudaStream_t, int);
+cudaError_t launch_jk_bra0(int, int, const JKArgs&, cudaStream_t, int);
+cudaError_t launch_jk_bra1(int, int, const JKArgs&, cudaStream_t, int);
+cudaError_t launch_jk_bra2(int, int, const JKArgs&, cudaStream_t, int);
+cudaError_t launch_jk_bra3(int, int, const JKArgs&, cudaStream_t, int);
+cudaError_t launch_jk_bra4(int, int, const JKArgs&, cudaStream_t, int);
+cudaError_t launch_jk_bra5(int, int, const JKArgs&, cudaStream_t, int);
+cudaError_t launch_jk_bra6(int, int, const JKArgs&, cudaStream_t, int);
+cudaError_t launch_jk_bra7(int, int, const JKArgs&, cudaStream_t, int);
+cudaError_t launch_jk_bra8(int, int, const JKArgs&, cudaStream_t, int);
+cudaError_t launch_jk_bra9(int, int, const JKArgs&, cudaStream_t, int);
 cudaError_t launch_j_lab0(int, int, const JArgs&, cudaStream_t, int);
 cudaError_t launch_j_lab1(int, int, const JArgs&, cudaStream_t, int);
 cudaError_t launch_j_lab2(int, int, const JArgs&, cudaStream_t, int);

@@ -13,28 +13,44 @@ struct KArgs {
   PairData pd;
   ShellPairInfo sp;
   WorkList wl;
-  const double* boys64;
-  const float* boys32;
+  BoysTabs bt;
   const RStep* rsteps;
   const double* Dp;   // density with component norms folded in, nbf x nbf
   double* Kh;         // half-K accumulator, nbf x nbf
-  const uint8_t* tier;  // optional per-item precision tier (nullptr: all items)
-  int tier_want;
+  // precision tiers (mixed mode): a quartet is FP64 (tier 0) when
+  // Q_ab Q_cd max|D'| >= tau over the six D blocks it touches, or when one of
+  // its pairs has an exponent sum above pmax32; otherwise FP32 (tier 1).
+  const float* Q;       // Schwarz bound per pair
+  const float* dmax;    // max |D'| per shell block, nshell x nshell
+  const float* pmaxp;   // largest primitive exponent sum per pair
+  float tau, pmax32;
+  int mixed;            // 0: every item in this launch's precision
+  int tier_want;        // 0 or 1: which tier this launch processes
+  unsigned long long* counter;  // items processed by this launch's tier (may be null)
+  int nshell;
   int nbf;
   int same_class;
 };
+
+__device__ __forceinline__ int quartet_tier(const KArgs& a, int pb_id, int pk_id, int s1, int s2, int s3, int s4) {
+  const float* dm = a.dmax;
+  const int ns = a.nshell;
+  float d = fmaxf(fmaxf(__ldg(dm + s1 * ns + s2), __ldg(dm + s3 * ns + s4)),
+                  fmaxf(fmaxf(__ldg(dm + s1 * ns + s3), __ldg(dm + s1 * ns + s4)),
+                        fmaxf(__ldg(dm + s2 * ns + s3), __ldg(dm + s2 * ns + s4))));
+  const float b = __ldg(a.Q + pb_id) * __ldg(a.Q + pk_id) * d;
+  const bool wide = fmaxf(__ldg(a.pmaxp + pb_id), __ldg(a.pmaxp + pk_id)) > a.pmax32;
+  return (b >= a.tau || wide) ? 0 : 1;
+}
 
 struct JArgs {
   PairData pd;
   ShellPairInfo sp;
   WorkList wl;
-  const double* boys64;
-  const float* boys32;
+  BoysTabs bt;
   const RStep* rsteps;
   const double* Dherm;  // Hermite density per ket primitive pair (sign (-1)^|Q| folded in)
   double* Jherm;        // Hermite J per bra primitive pair (accumulated)
-  const uint8_t* tier;
-  int tier_want;
 };
 
 __device__ __forceinline__ int find_bra(const int64_t* __restrict__ prefix, int n, int64_t item) {
@@ -47,7 +63,15 @@ __device__ __forceinline__ int find_bra(const int64_t* __restrict__ prefix, int 
 }
 
 template <typename T> __device__ __forceinline__ T ldT(const double* p) { return (T)__ldg(p); }
+
+// precision-explicit reciprocal square root (a plain overload inside this
+// namespace would hide ::rsqrt(double) and silently demote FP64 to FP32)
+__device__ __forceinline__ double rsqrt_t(double x) { return ::rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return ::rsqrtf(x); }
 template <typename T> __device__ __forceinline__ T pdv(const double* d, const float* f, int i);
+template <typename T> __device__ __forceinline__ T ldE(const PairData& pd, int i);
+template <> __device__ __forceinline__ double ldE<double>(const PairData& pd, int i) { return __ldg(pd.E + i); }
+template <> __device__ __forceinline__ float ldE<float>(const PairData& pd, int i) { return __ldg(pd.Ef + i); }
 template <> __device__ __forceinline__ double pdv<double>(const double* d, const float*, int i) { return __ldg(d + i); }
 template <> __device__ __forceinline__ float pdv<float>(const double*, const float* f, int i) { return __ldg(f + i); }
 
@@ -107,213 +131,6 @@ __device__ __forceinline__ void r_build_warp(const T* F, T pref, T X, T Y, T Z, 
   }
 }
 
-template <int LA, int LB, int LC, int LD, typename T>
-struct KShape {
-  static constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
-  static constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
-  static constexpr int NCD = NC * ND, HAB = nherm(LAB), B = L + 1, BOX = B * B * B;
-  static constexpr int WS = HAB | 1;
-  static constexpr int NEB = (LA + 1) * (LB + 1) * (LAB + 1), NEK = (LC + 1) * (LD + 1) * (LCD + 1);
-  static constexpr int NPING = L > 0 ? nherm(L - 1) : 1;
-  static constexpr int NPS = (HAB + 31) / 32;
-  // per-warp shared memory, in elements of T
-  static constexpr int SM_BOX = 0, SM_PING = BOX, SM_W = SM_PING + 2 * NPING, SM_EB = SM_W + 32 * WS,
-                       SM_EK = SM_EB + 3 * NEB, SM_KB = SM_EK + 3 * NEK, SM_TOTAL = SM_KB + 2 * NB * 32;
-  static constexpr size_t smem_per_warp() { return sizeof(T) * SM_TOTAL; }
-};
-
-// Exchange over canonical shell quartets (ab|cd), bra class >= ket class.
-//   phase 1 (ket transform, lanes own bra Hermite index P):
-//     W_P[cd] = sum_Q E'_Q^{cd} R_{P+Q},  E' = (-1)^|Q| E      (Eq. eri_formula)
-//   phase 2 (bra transform, lanes own ket pair cd):
-//     (ab|cd) = sum_P E_P^{ab} W_P[cd],
-//   then Kh_ac += w (ab|cd) D_bd, Kh_ad += w (ab|cd) D_bc, Kh_bc += w (ab|cd) D_ad,
-//   Kh_bd += w (ab|cd) D_ac (Eq. k_definition), w = 1/2^[a=b] 1/2^[c=d] 1/2^[ab=cd];
-//   K = Kh + Kh^T afterwards restores all eight permutations (Eq. 8_fold_symmetry).
-template <int LA, int LB, int LC, int LD, typename T>
-__global__ void __launch_bounds__(128) k_warp_kernel(KArgs a) {
-  using S = KShape<LA, LB, LC, LD, T>;
-  constexpr int LAB = S::LAB, LCD = S::LCD, L = S::L, B = S::B;
-  constexpr int NA = S::NA, NB = S::NB, ND = S::ND, NCD = S::NCD, HAB = S::HAB, WS = S::WS;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  T* sm = reinterpret_cast<T*>(smraw) + (size_t)wib * S::SM_TOTAL;
-  T* box = sm + S::SM_BOX;
-  T* ping0 = sm + S::SM_PING;
-  T* ping1 = ping0 + S::NPING;
-  T* W = sm + S::SM_W;
-  T* Eb = sm + S::SM_EB;
-  T* Ek = sm + S::SM_EK;
-  T* Kb = sm + S::SM_KB;
-
-  int pbase[S::NPS];
-#pragma unroll
-  for (int j = 0; j < S::NPS; ++j) {
-    int P = lane + 32 * j;
-    pbase[j] = 0;
-    if (P < HAB) {
-      RStep s = a.rsteps[P];
-      pbase[j] = (s.t * B + s.u) * B + s.v;
-    }
-  }
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t total = a.wl.total;
-  const int nbf = a.nbf;
-  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; item < total; item += nwarps) {
-    if (a.tier && a.tier[item] != a.tier_want) continue;
-    const int ib = find_bra(a.wl.prefix, a.wl.nbra, item);
-    const int ik = (int)(item - __ldg(a.wl.prefix + ib));
-    const int pb_id = __ldg(a.wl.bra + ib), pk_id = __ldg(a.wl.ket + ik);
-    const int s1 = __ldg(a.sp.s1 + pb_id), s2 = __ldg(a.sp.s2 + pb_id);
-    const int s3 = __ldg(a.sp.s1 + pk_id), s4 = __ldg(a.sp.s2 + pk_id);
-    const int npb = __ldg(a.sp.np + pb_id), offb = __ldg(a.sp.poff + pb_id);
-    const int npk = __ldg(a.sp.np + pk_id), offk = __ldg(a.sp.poff + pk_id);
-    const int ao1 = __ldg(a.sp.ao1 + pb_id), ao2 = __ldg(a.sp.ao2 + pb_id);
-    const int ao3 = __ldg(a.sp.ao1 + pk_id), ao4 = __ldg(a.sp.ao2 + pk_id);
-    T w = T(1);
-    if (s1 == s2) w *= T(0.5);
-    if (s3 == s4) w *= T(0.5);
-    if (pb_id == pk_id) w *= T(0.5);
-
-    for (int c0 = 0; c0 < NCD; c0 += 32) {
-      const int nci = NCD - c0 < 32 ? NCD - c0 : 32;
-      const int cd = c0 + lane;
-      const bool cdv = lane < nci;
-      const int ic = cdv ? cd / ND : 0, id = cdv ? cd % ND : 0;
-      // a-indexed accumulators live in registers (the a loop is unrolled);
-      // b-indexed ones in this lane's own shared-memory column (runtime b loop).
-      T kac[NA], kad[NA];
-#pragma unroll
-      for (int x = 0; x < NA; ++x) {
-        kac[x] = T(0);
-        kad[x] = T(0);
-      }
-      T* kbc = Kb + lane;           // kbc[b * 32]
-      T* kbd = Kb + NB * 32 + lane;  // kbd[b * 32]
-      for (int b = 0; b < NB; ++b) {
-        kbc[b * 32] = T(0);
-        kbd[b * 32] = T(0);
-      }
-      const double* Dcol_d = a.Dp + ao4 + id;  // D'[row][d]
-      const double* Dcol_c = a.Dp + ao3 + ic;  // D'[row][c]
-      for (int pb = 0; pb < npb; ++pb) {
-        Prim<T> bp;
-        bp.load(a.pd, offb + pb);
-        if (lane < 3) md_e_1d<LA, LB, T>(bp.PA[lane], bp.PB[lane], T(0.5) / bp.p, Eb + lane * S::NEB);
-        for (int x = lane; x < nci * WS; x += 32) W[x] = T(0);
-        __syncwarp();
-        for (int pk = 0; pk < npk; ++pk) {
-          Prim<T> kp;
-          kp.load(a.pd, offk + pk);
-          if (lane < 3) {
-            T* e = Ek + lane * S::NEK;
-            md_e_1d<LC, LD, T>(kp.PA[lane], kp.PB[lane], T(0.5) / kp.p, e);
-            // fold (-1)^s into the ket coefficients
-#pragma unroll
-            for (int x = 0; x < S::NEK; ++x)
-              if ((x % (LCD + 1)) & 1) e[x] = -e[x];
-          }
-          const T pq = bp.p * kp.p, ps = bp.p + kp.p;
-          const T rho = pq / ps;
-          const T X = bp.P[0] - kp.P[0], Y = bp.P[1] - kp.P[1], Z = bp.P[2] - kp.P[2];
-          T F[L + 1];
-          Boys<T>::template eval<L>(rho * (X * X + Y * Y + Z * Z), a.boys64, a.boys32, F);
-          const T pref = bp.pref * kp.pref * (T(1) / sqrt(ps));
-          r_build_warp<L, T>(F, pref, X, Y, Z, T(-2) * rho, a.rsteps, ping0, ping1, box, lane);
-          // phase 1: ket transform, trip counts uniform (they depend on cd only)
-#pragma unroll 1
-          for (int ci = 0; ci < nci; ++ci) {
-            int kx, ky, kz, lx, ly, lz;
-            cart_xyz(LC, (c0 + ci) / ND, kx, ky, kz);
-            cart_xyz(LD, (c0 + ci) % ND, lx, ly, lz);
-            const T* ex = Ek + 0 * S::NEK + (kx * (LD + 1) + lx) * (LCD + 1);
-            const T* ey = Ek + 1 * S::NEK + (ky * (LD + 1) + ly) * (LCD + 1);
-            const T* ez = Ek + 2 * S::NEK + (kz * (LD + 1) + lz) * (LCD + 1);
-            const int nx = kx + lx, ny = ky + ly, nz = kz + lz;
-#pragma unroll
-            for (int j = 0; j < S::NPS; ++j) {
-              const int P = lane + 32 * j;
-              if (P < HAB) {
-                T acc = T(0);
-#pragma unroll 1
-                for (int sx = 0; sx <= nx; ++sx) {
-                  T accy = T(0);
-#pragma unroll 1
-                  for (int sy = 0; sy <= ny; ++sy) {
-                    const T* r = box + pbase[j] + sx * B * B + sy * B;
-                    T accz = T(0);
-#pragma unroll 1
-                    for (int sz = 0; sz <= nz; ++sz) accz = fma(ez[sz], r[sz], accz);
-                    accy = fma(ey[sy], accz, accy);
-                  }
-                  acc = fma(ex[sx], accy, acc);
-                }
-                W[ci * WS + P] += acc;
-              }
-            }
-          }
-          __syncwarp();
-        }
-        // phase 2: bra transform and contraction, lane owns column cd
-        if (cdv) {
-          const T* wcol = W + lane * WS;
-#pragma unroll
-          for (int xa = 0; xa < NA; ++xa) {
-            int ix, iy, iz;
-            cart_xyz(LA, xa, ix, iy, iz);
-            const T dad_x = ldT<T>(a.Dp + (size_t)(ao1 + xa) * nbf + ao4 + id);
-            const T dac_x = ldT<T>(a.Dp + (size_t)(ao1 + xa) * nbf + ao3 + ic);
-#pragma unroll 1
-            for (int xb = 0; xb < NB; ++xb) {
-              int jx, jy, jz;
-              cart_xyz(LB, xb, jx, jy, jz);
-              const T* ex = Eb + 0 * S::NEB + (ix * (LB + 1) + jx) * (LAB + 1);
-              const T* ey = Eb + 1 * S::NEB + (iy * (LB + 1) + jy) * (LAB + 1);
-              const T* ez = Eb + 2 * S::NEB + (iz * (LB + 1) + jz) * (LAB + 1);
-              const int nx = ix + jx, ny = iy + jy, nz = iz + jz;
-              T acc = T(0);
-#pragma unroll 1
-              for (int tx = 0; tx <= nx; ++tx) {
-                T accy = T(0);
-#pragma unroll 1
-                for (int ty = 0; ty <= ny; ++ty) {
-                  T accz = T(0);
-#pragma unroll 1
-                  for (int tz = 0; tz <= nz; ++tz) {
-                    // herm_index(tx,ty,tz) for fixed (tx,ty) walks groups n = tx+ty+tz
-                    const int n = tx + ty + tz, r = ty + tz;
-                    accz = fma(ez[tz], wcol[nherm(n - 1) + r * (r + 1) / 2 + tz], accz);
-                  }
-                  accy = fma(ey[ty], accz, accy);
-                }
-                acc = fma(ex[tx], accy, acc);
-              }
-              const T v = w * acc;
-              const size_t rowb = (size_t)(ao2 + xb) * nbf;
-              kac[xa] = fma(v, ldT<T>(Dcol_d + rowb), kac[xa]);
-              kad[xa] = fma(v, ldT<T>(Dcol_c + rowb), kad[xa]);
-              kbc[xb * 32] = fma(v, dad_x, kbc[xb * 32]);
-              kbd[xb * 32] = fma(v, dac_x, kbd[xb * 32]);
-            }
-          }
-        }
-        __syncwarp();
-      }
-      if (cdv) {
-#pragma unroll
-        for (int x = 0; x < NA; ++x) {
-          atomic_add_d(a.Kh + (size_t)(ao1 + x) * nbf + ao3 + ic, (double)kac[x]);
-          atomic_add_d(a.Kh + (size_t)(ao1 + x) * nbf + ao4 + id, (double)kad[x]);
-        }
-        for (int b = 0; b < NB; ++b) {
-          atomic_add_d(a.Kh + (size_t)(ao2 + b) * nbf + ao3 + ic, (double)kbc[b * 32]);
-          atomic_add_d(a.Kh + (size_t)(ao2 + b) * nbf + ao4 + id, (double)kbd[b * 32]);
-        }
-      }
-    }
-  }
-}
-
 template <int LAB, int LCD, typename T>
 struct JShape {
   static constexpr int L = LAB + LCD, B = L + 1, BOX = B * B * B, HAB = nherm(LAB), HCD = nherm(LCD);
@@ -349,7 +166,6 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t total = a.wl.total;
   for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; item < total; item += nwarps) {
-    if (a.tier && a.tier[item] != a.tier_want) continue;
     const int ib = find_bra(a.wl.prefix, a.wl.nbra, item);
     const int ik = (int)(item - __ldg(a.wl.prefix + ib));
     const int pb_id = __ldg(a.wl.bra + ib), pk_id = __ldg(a.wl.ket + ik);
@@ -369,7 +185,7 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
         const T rho = pq / ps;
         const T X = bp.P[0] - kp.P[0], Y = bp.P[1] - kp.P[1], Z = bp.P[2] - kp.P[2];
         T F[L + 1];
-        Boys<T>::template eval<L>(rho * (X * X + Y * Y + Z * Z), a.boys64, a.boys32, F);
+        Boys<T>::template eval<L>(rho * (X * X + Y * Y + Z * Z), a.bt, F);
         const T pref = bp.pref * kp.pref * (T(1) / sqrt(ps));
         r_build_warp<L, T>(F, pref, X, Y, Z, T(-2) * rho, a.rsteps, ping0, ping1, box, lane);
         const double* dq = a.Dherm + hk + (size_t)pk * HCD;

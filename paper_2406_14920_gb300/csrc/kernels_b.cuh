@@ -1,0 +1,288 @@
+// General J+K kernel: one warp per canonical shell quartet, contracted ERI block
+// staged in shared memory.  Used for every class that does not fit the
+// register kernel (kernels_a.cuh).
+//
+// Per quartet, per chunk of CH ket Cartesian pairs cd, per bra primitive pair,
+// the ket primitive pairs are taken G at a time:
+//   step A  (lane g): quartet scalars for ket primitive g -- rho, P-Q, prefactor,
+//           Boys F_0..F_L (Eq. boys_function); all lanes: ket E tables to smem
+//           with (-1)^|Q| folded in;
+//   step B  items (g, e), level by level: R^0 of the G primitive quartets
+//           (Eq. R_recursion);
+//   step C  items (cd, P): W[cd][P] += sum_g sum_Q E'_Q^{cd}(g) R_{P+Q}(g);
+// then for the bra primitive:
+//   step D  items (ab, cd): X[ab][cd] += sum_P E_P^{ab} W[cd][P]        (Eq. eri_formula)
+// and per chunk the contraction, one lane per output element:
+//   Kh_ac, Kh_ad, Kh_bc, Kh_bd (Eq. k_definition), Jh_ab, Jh_cd (Eq. j_definition),
+//   one atomic per element.
+// Every per-primitive-quartet scalar is computed by one lane, not redundantly
+// by the warp (GB300's FP64 pipe charges a full warp issue per instruction
+// whatever the number of active lanes).
+#pragma once
+#include "kernels_a.cuh"
+
+namespace eri {
+
+template <int LA, int LB, int LC, int LD, typename T>
+struct BShape {
+  static constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
+  static constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+  static constexpr int NAB = NA * NB, NCD = NC * ND, HAB = nherm(LAB), HABP = HAB | 1;
+  static constexpr int B = L + 1, BOX = B * B * B, NPING = L > 0 ? nherm(L - 1) : 1;
+  static constexpr int NEB = (LA + 1) * (LB + 1) * (LAB + 1), NEK = (LC + 1) * (LD + 1) * (LCD + 1);
+  static constexpr int NSC = L + 5;  // F'_0..F'_L, PQx, PQy, PQz, c
+  static constexpr int BUDGET = (int)((44 * 1024) / sizeof(T));  // elements of T per warp
+  static constexpr int FIXED = 3 * NEB;
+  static constexpr int PER_G = BOX + 2 * NPING + NSC + 3 * NEK;
+  static constexpr int PER_C = HABP + NAB;
+  static constexpr int G0 = (BUDGET - FIXED - NCD * PER_C) / PER_G;
+  static constexpr int G = G0 >= 1 ? (G0 > 16 ? 16 : G0) : 1;
+  static constexpr int CHMAX = (BUDGET - FIXED - G * PER_G) / PER_C;
+  static constexpr int CH = CHMAX >= NCD ? NCD : (CHMAX < 1 ? 1 : CHMAX);
+  static constexpr int SM_BOX = 0, SM_PING = SM_BOX + G * BOX, SM_SC = SM_PING + G * 2 * NPING,
+                       SM_EK = SM_SC + G * NSC, SM_EB = SM_EK + G * 3 * NEK, SM_W = SM_EB + 3 * NEB,
+                       SM_X = SM_W + CH * HABP, SM_TOTAL = SM_X + NAB * CH;
+  static constexpr size_t smem_per_warp() { return sizeof(T) * SM_TOTAL; }
+};
+
+template <int LA, int LB, int LC, int LD, typename T>
+__global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
+  using S = BShape<LA, LB, LC, LD, T>;
+  constexpr int LAB = S::LAB, LCD = S::LCD, L = S::L, B = S::B, BOX = S::BOX, NSC = S::NSC;
+  constexpr int NA = S::NA, NB = S::NB, ND = S::ND, NAB = S::NAB, NCD = S::NCD, HAB = S::HAB, HABP = S::HABP,
+                CH = S::CH, G = S::G, NEB = S::NEB, NEK = S::NEK, NPING = S::NPING;
+  const KArgs& a = A.k;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  T* sm = reinterpret_cast<T*>(smraw) + (size_t)wib * S::SM_TOTAL;
+  T* boxes = sm + S::SM_BOX;
+  T* pings = sm + S::SM_PING;
+  T* scal = sm + S::SM_SC;
+  T* Ek = sm + S::SM_EK;
+  T* Eb = sm + S::SM_EB;
+  T* Ws = sm + S::SM_W;
+  T* Xs = sm + S::SM_X;
+  const int n = a.nbf;
+  const double* Dp = a.Dp;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t total = a.wl.total;
+  unsigned long long done = 0, doneq = 0, doneb = 0;
+  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; item < total; item += nwarps) {
+    const int ib = find_bra(a.wl.prefix, a.wl.nbra, item);
+    const int ik = (int)(item - __ldg(a.wl.prefix + ib));
+    const int pb_id = __ldg(a.wl.bra + ib), pk_id = __ldg(a.wl.ket + ik);
+    const int s1 = __ldg(a.sp.s1 + pb_id), s2 = __ldg(a.sp.s2 + pb_id);
+    const int s3 = __ldg(a.sp.s1 + pk_id), s4 = __ldg(a.sp.s2 + pk_id);
+    if (a.mixed && quartet_tier(a, pb_id, pk_id, s1, s2, s3, s4) != a.tier_want) continue;
+    const int npb = __ldg(a.sp.np + pb_id), offb = __ldg(a.sp.poff + pb_id), eb0 = __ldg(a.sp.eoff + pb_id);
+    const int npk = __ldg(a.sp.np + pk_id), offk = __ldg(a.sp.poff + pk_id), ek0 = __ldg(a.sp.eoff + pk_id);
+    ++done;
+    doneq += (unsigned long long)npb * npk;
+    doneb += npb;
+    const int ao1 = __ldg(a.sp.ao1 + pb_id), ao2 = __ldg(a.sp.ao2 + pb_id);
+    const int ao3 = __ldg(a.sp.ao1 + pk_id), ao4 = __ldg(a.sp.ao2 + pk_id);
+    T w = T(1);
+    if (s1 == s2) w *= T(0.5);
+    if (s3 == s4) w *= T(0.5);
+    if (pb_id == pk_id) w *= T(0.5);
+
+    for (int c0 = 0; c0 < NCD; c0 += CH) {
+      const int nci = NCD - c0 < CH ? NCD - c0 : CH;
+      for (int x = lane; x < NAB * CH; x += 32) Xs[x] = T(0);
+      for (int pb = 0; pb < npb; ++pb) {
+        for (int x = lane; x < 3 * NEB; x += 32) Eb[x] = ldE<T>(a.pd, eb0 + pb * 3 * NEB + x);
+        for (int x = lane; x < CH * HABP; x += 32) Ws[x] = T(0);
+        const int ipb = offb + pb;
+        const T bp_p = pdv<T>(a.pd.p, a.pd.pf, ipb), bp_pref = pdv<T>(a.pd.pref, a.pd.preff, ipb);
+        const T bPx = pdv<T>(a.pd.P, a.pd.Pf, ipb), bPy = pdv<T>(a.pd.P, a.pd.Pf, a.pd.n + ipb),
+                bPz = pdv<T>(a.pd.P, a.pd.Pf, 2 * a.pd.n + ipb);
+        for (int k0 = 0; k0 < npk; k0 += G) {
+          const int ng = npk - k0 < G ? npk - k0 : G;
+          // step A: ket E tables (sign folded) and per-primitive-quartet scalars
+          for (int x = lane; x < ng * 3 * NEK; x += 32) {
+            const int g = x / (3 * NEK), r = x - g * 3 * NEK;
+            const T v = ldE<T>(a.pd, ek0 + (k0 + g) * 3 * NEK + r);
+            Ek[x] = ((r % (LCD + 1)) & 1) ? -v : v;
+          }
+          if (lane < ng) {
+            const int ipk = offk + k0 + lane;
+            const T kp = pdv<T>(a.pd.p, a.pd.pf, ipk);
+            const T ps = bp_p + kp;
+            const T rho = bp_p * kp / ps;
+            const T X = bPx - pdv<T>(a.pd.P, a.pd.Pf, ipk);
+            const T Y = bPy - pdv<T>(a.pd.P, a.pd.Pf, a.pd.n + ipk);
+            const T Z = bPz - pdv<T>(a.pd.P, a.pd.Pf, 2 * a.pd.n + ipk);
+            T F[L + 1];
+            Boys<T>::template eval<L>(rho * (X * X + Y * Y + Z * Z), a.bt, F);
+            const T pref = bp_pref * pdv<T>(a.pd.pref, a.pd.preff, ipk) * rsqrt_t(ps);
+            T* sc = scal + lane * NSC;
+#pragma unroll
+            for (int m = 0; m <= L; ++m) sc[m] = pref * F[m];
+            sc[L + 1] = X;
+            sc[L + 2] = Y;
+            sc[L + 3] = Z;
+            sc[L + 4] = T(-2) * rho;
+          }
+          __syncwarp();
+          // step B: R^0 for the ng primitive quartets, level by level (scaled form, see r_build_warp)
+          if (L == 0) {
+            if (lane < ng) boxes[lane * BOX] = scal[lane * NSC];
+          } else {
+            if (lane < ng) pings[lane * 2 * NPING] = scal[lane * NSC + L];
+            __syncwarp();
+            int cur = 0;
+            for (int m = L - 1; m >= 0; --m) {
+              const int ne = nherm(L - m);
+              for (int it = lane; it < ng * ne; it += 32) {
+                const int g = it / ne, e = it - g * ne;
+                const T* sc = scal + g * NSC;
+                const T* src = pings + g * 2 * NPING + cur * NPING;
+                const RStep st = a.rsteps[e];
+                T val;
+                if (e == 0) {
+                  val = sc[m];
+                } else {
+                  const T pq = sc[L + 1 + st.dir];
+                  val = pq * src[st.dep1];
+                  if (st.dep2 >= 0) val = fma((T)st.k, src[st.dep2], val);
+                  val *= sc[L + 4];
+                }
+                if (m == 0) boxes[g * BOX + (st.t * B + st.u) * B + st.v] = val;
+                else pings[g * 2 * NPING + (1 - cur) * NPING + e] = val;
+              }
+              __syncwarp();
+              cur = 1 - cur;
+            }
+          }
+          __syncwarp();
+          // step C: ket transform, items (ci, P)
+          for (int it = lane; it < nci * HAB; it += 32) {
+            const int ci = it / HAB, P = it - ci * HAB;
+            const int cd = c0 + ci;
+            int kx, ky, kz, lx, ly, lz;
+            cart_xyz(LC, cd / ND, kx, ky, kz);
+            cart_xyz(LD, cd % ND, lx, ly, lz);
+            const int ox = (kx * (LD + 1) + lx) * (LCD + 1), oy = NEK + (ky * (LD + 1) + ly) * (LCD + 1),
+                      oz = 2 * NEK + (kz * (LD + 1) + lz) * (LCD + 1);
+            const RStep st = a.rsteps[P];
+            const int base = (st.t * B + st.u) * B + st.v;
+            T acc = T(0);
+            for (int g = 0; g < ng; ++g) {
+              const T* ek = Ek + g * 3 * NEK;
+              const T* rb = boxes + g * BOX + base;
+              for (int sx = 0; sx <= kx + lx; ++sx) {
+                T accy = T(0);
+                for (int sy = 0; sy <= ky + ly; ++sy) {
+                  const T* r = rb + sx * B * B + sy * B;
+                  T accz = T(0);
+                  for (int sz = 0; sz <= kz + lz; ++sz) accz = fma(ek[oz + sz], r[sz], accz);
+                  accy = fma(ek[oy + sy], accz, accy);
+                }
+                acc = fma(ek[ox + sx], accy, acc);
+              }
+            }
+            Ws[ci * HABP + P] += acc;
+          }
+          __syncwarp();
+        }
+        // step D: bra transform, items (ab, ci)
+        for (int it = lane; it < NAB * nci; it += 32) {
+          const int iab = it / nci, ci = it - iab * nci;
+          int ix, iy, iz, jx, jy, jz;
+          cart_xyz(LA, iab / NB, ix, iy, iz);
+          cart_xyz(LB, iab % NB, jx, jy, jz);
+          const T* fx = Eb + 0 * NEB + (ix * (LB + 1) + jx) * (LAB + 1);
+          const T* fy = Eb + 1 * NEB + (iy * (LB + 1) + jy) * (LAB + 1);
+          const T* fz = Eb + 2 * NEB + (iz * (LB + 1) + jz) * (LAB + 1);
+          const T* wc = Ws + ci * HABP;
+          T acc = T(0);
+          for (int tx = 0; tx <= ix + jx; ++tx) {
+            T accy = T(0);
+            for (int ty = 0; ty <= iy + jy; ++ty) {
+              T accz = T(0);
+              const int b0 = herm_index(tx, ty, 0);
+              int idx = b0;
+              for (int tz = 0; tz <= iz + jz; ++tz) {
+                accz = fma(fz[tz], wc[idx], accz);
+                // herm_index(tx,ty,tz+1) - herm_index(tx,ty,tz): next group, one further along
+                const int nn = tx + ty + tz + 1, r = ty + tz + 1;
+                idx = nherm(nn - 1) + r * (r + 1) / 2 + tz + 1;
+              }
+              accy = fma(fy[ty], accz, accy);
+            }
+            acc = fma(fx[tx], accy, acc);
+          }
+          Xs[iab * CH + ci] += acc;
+        }
+        __syncwarp();
+      }
+      // contraction of the chunk; one lane per output element
+      const int cfirst = c0 / ND, clast = (c0 + nci - 1) / ND;
+      const int ncr = clast - cfirst + 1;
+      if (a.Kh) {
+        // Kh_ac[a][c] += w sum_{b, d: (c,d) in chunk} X D_bd ; Kh_bc[b][c] += w sum_{a,d} X D_ad
+        for (int o = lane; o < (NA + NB) * ncr; o += 32) {
+          const bool isA = o < NA * ncr;
+          const int oo = isA ? o : o - NA * ncr;
+          const int r = oo / ncr, c = cfirst + oo % ncr;
+          T s = T(0);
+          for (int d = 0; d < ND; ++d) {
+            const int ci = c * ND + d - c0;
+            if (ci < 0 || ci >= nci) continue;
+            if (isA) {
+              for (int b = 0; b < NB; ++b) s = fma(Xs[(r * NB + b) * CH + ci], ldT<T>(Dp + (size_t)(ao2 + b) * n + ao4 + d), s);
+            } else {
+              for (int x = 0; x < NA; ++x) s = fma(Xs[(x * NB + r) * CH + ci], ldT<T>(Dp + (size_t)(ao1 + x) * n + ao4 + d), s);
+            }
+          }
+          const int row = isA ? ao1 + r : ao2 + r;
+          atomic_add_d(a.Kh + (size_t)row * n + ao3 + c, (double)(w * s));
+        }
+        // Kh_ad[a][d] += w sum_{b, c in chunk} X D_bc ; Kh_bd[b][d] += w sum_{a, c} X D_ac
+        for (int o = lane; o < (NA + NB) * ND; o += 32) {
+          const bool isA = o < NA * ND;
+          const int oo = isA ? o : o - NA * ND;
+          const int r = oo / ND, d = oo % ND;
+          T s = T(0);
+          for (int c = cfirst; c <= clast; ++c) {
+            const int ci = c * ND + d - c0;
+            if (ci < 0 || ci >= nci) continue;
+            if (isA) {
+              for (int b = 0; b < NB; ++b) s = fma(Xs[(r * NB + b) * CH + ci], ldT<T>(Dp + (size_t)(ao2 + b) * n + ao3 + c), s);
+            } else {
+              for (int x = 0; x < NA; ++x) s = fma(Xs[(x * NB + r) * CH + ci], ldT<T>(Dp + (size_t)(ao1 + x) * n + ao3 + c), s);
+            }
+          }
+          const int row = isA ? ao1 + r : ao2 + r;
+          atomic_add_d(a.Kh + (size_t)row * n + ao4 + d, (double)(w * s));
+        }
+      }
+      if (A.Jh) {
+        const T w2 = T(2) * w;
+        for (int iab = lane; iab < NAB; iab += 32) {  // Jh_ab += 2w sum_cd X D_cd (chunk part)
+          T s = T(0);
+          for (int ci = 0; ci < nci; ++ci) {
+            const int cd = c0 + ci;
+            s = fma(Xs[iab * CH + ci], ldT<T>(Dp + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND), s);
+          }
+          atomic_add_d(A.Jh + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB, (double)(w2 * s));
+        }
+        for (int ci = lane; ci < nci; ci += 32) {  // Jh_cd += 2w sum_ab X D_ab
+          T s = T(0);
+          for (int iab = 0; iab < NAB; ++iab)
+            s = fma(Xs[iab * CH + ci], ldT<T>(Dp + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB), s);
+          const int cd = c0 + ci;
+          atomic_add_d(A.Jh + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND, (double)(w2 * s));
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (a.counter && lane == 0 && done) {
+    atomicAdd(a.counter, done);
+    atomicAdd(a.counter + 1, doneq);
+    atomicAdd(a.counter + 2, doneb);
+  }
+}
+
+}  // namespace eri

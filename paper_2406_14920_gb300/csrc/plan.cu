@@ -72,14 +72,16 @@ __global__ void k_compfac(int nshell, const int* __restrict__ l, const int* __re
   }
 }
 
-// Boys table F_m(T_k), T_k = k h: series for a high order m_top,
+// Boys tables: F_m(T_k), T_k = k h, from the series for a high order m_top,
 // F_m(T) = exp(-T) sum_i (2T)^i / ((2m+1)(2m+3)...(2m+2i+1)), then the stable
-// downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1).
-__global__ void k_boys_table(double* __restrict__ t64, float* __restrict__ t32) {
+// downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1).  Stored as Taylor
+// coefficients c[k][m][j] = F_{m+j}(T_k) / j!  and exp(-T_k).
+__global__ void k_boys_table(double* __restrict__ c64, double* __restrict__ e64, float* __restrict__ c32,
+                             float* __restrict__ e32) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= BOYS_NT) return;
   const double T = k * BOYS_H;
-  const int mtop = BOYS_MDIM + 24;
+  const int mtop = BOYS_MMAX + BOYS_J64 + 24;
   double term = 1.0 / (2 * mtop + 1), sum = term;
   for (int i = 1; i < 2000; ++i) {
     term *= 2.0 * T / (2 * mtop + 2 * i + 1);
@@ -87,14 +89,22 @@ __global__ void k_boys_table(double* __restrict__ t64, float* __restrict__ t32) 
     if (term < 1e-18 * sum) break;
   }
   const double e = exp(-T);
+  double F[BOYS_MMAX + BOYS_J64 + 1];
   double f = e * sum;
   for (int m = mtop - 1; m >= 0; --m) {
     f = (2.0 * T * f + e) / (2 * m + 1);
-    if (m < BOYS_MDIM) {
-      t64[k * BOYS_MDIM + m] = f;
-      t32[k * BOYS_MDIM + m] = (float)f;
+    if (m <= BOYS_MMAX + BOYS_J64) F[m] = f;
+  }
+  double fact = 1.0;
+  for (int j = 0; j < BOYS_J64; ++j) {
+    if (j > 0) fact *= j;
+    for (int m = 0; m <= BOYS_MMAX; ++m) {
+      c64[((size_t)k * (BOYS_MMAX + 1) + m) * BOYS_J64 + j] = F[m + j] / fact;
+      if (j < BOYS_J32) c32[((size_t)k * (BOYS_MMAX + 1) + m) * BOYS_J32 + j] = (float)(F[m + j] / fact);
     }
   }
+  e64[k] = e;
+  e32[k] = (float)e;
 }
 
 // Primitive-pair data for every shell pair (Eq. pair_definition):
@@ -105,7 +115,8 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
                         const int* __restrict__ poff, const int* __restrict__ sh_atom, const int* __restrict__ sh_np,
                         const int* __restrict__ sh_po, const double* __restrict__ ex, const double* __restrict__ cn,
                         const double* __restrict__ coords, int nprimpair, double* p_, double* P_, double* PA_,
-                        double* PB_, double* pref_, float* pf, float* Pf, float* PAf, float* PBf, float* preff) {
+                        double* PB_, double* pref_, float* pf, float* Pf, float* PAf, float* PBf, float* preff,
+                        float* pmaxp) {
   int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= npair) return;
   const int a = s1[ip], b = s2[ip];
@@ -114,6 +125,7 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
   double AB2 = 0.0;
   for (int d = 0; d < 3; ++d) AB2 += (A[d] - Bc[d]) * (A[d] - Bc[d]);
   int o = poff[ip];
+  double pmx = 0.0;
   const double s2pi52 = 5.9149671727956129;  // sqrt(2 pi^(5/2))
   for (int i = 0; i < sh_np[a]; ++i)
     for (int j = 0; j < sh_np[b]; ++j, ++o) {
@@ -121,6 +133,7 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
       const double p = ea + eb;
       const double pr = cn[sh_po[a] + i] * cn[sh_po[b] + j] * exp(-ea * eb / p * AB2) * s2pi52 / p;
       p_[o] = p;
+      pmx = fmax(pmx, p);
       pref_[o] = pr;
       pf[o] = (float)p;
       preff[o] = (float)pr;
@@ -134,6 +147,19 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
         PBf[d * nprimpair + o] = (float)(P - Bc[d]);
       }
     }
+  pmaxp[ip] = (float)pmx;
+}
+
+// max |D'| over every shell block (used by the mixed-precision tier test)
+__global__ void k_dmax(int ns, const int* __restrict__ l, const int* __restrict__ ao, const double* __restrict__ Dp,
+                       int nbf, float* __restrict__ dmax) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns * ns) return;
+  const int a = t / ns, b = t % ns;
+  double m = 0.0;
+  for (int i = 0; i < ncart(l[a]); ++i)
+    for (int j = 0; j < ncart(l[b]); ++j) m = fmax(m, fabs(Dp[(size_t)(ao[a] + i) * nbf + ao[b] + j]));
+  dmax[t] = __double2float_ru((float)m);
 }
 
 // runtime-l E^{ij}_t (Eq. E_recursion), E[(i*5+j)*9+t], i,j <= 4
@@ -157,10 +183,36 @@ __device__ void md_e_rt(int li, int lj, double PA, double PB, double o2p, double
       }
 }
 
+// Hermite coefficients E^{ij}_t (Eq. E_recursion) of every primitive pair, per
+// direction, stored as (i*(l2+1)+j)*(l1+l2+1)+t, i <= l1, j <= l2 (x, then y, then z).
+__global__ void k_etab(int npair, const int* __restrict__ s1, const int* __restrict__ s2, const int* __restrict__ np,
+                       const int* __restrict__ poff, const int* __restrict__ eoff, const int* __restrict__ sh_l,
+                       PairData pd, double* __restrict__ E, float* __restrict__ Ef) {
+  int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= npair) return;
+  const int l1 = sh_l[s1[ip]], l2 = sh_l[s2[ip]];
+  const int ne = (l1 + 1) * (l2 + 1) * (l1 + l2 + 1);
+  double tmp[225];
+  for (int k = 0; k < np[ip]; ++k) {
+    const int pi = poff[ip] + k;
+    for (int d = 0; d < 3; ++d) {
+      md_e_rt(l1, l2, pd.PA[d * pd.n + pi], pd.PB[d * pd.n + pi], 0.5 / pd.p[pi], tmp);
+      const size_t o = (size_t)eoff[ip] + ((size_t)k * 3 + d) * ne;
+      for (int i = 0; i <= l1; ++i)
+        for (int j = 0; j <= l2; ++j)
+          for (int t = 0; t <= l1 + l2; ++t) {
+            const double v = tmp[(i * 5 + j) * 9 + t];
+            E[o + (i * (l2 + 1) + j) * (l1 + l2 + 1) + t] = v;
+            Ef[o + (i * (l2 + 1) + j) * (l1 + l2 + 1) + t] = (float)v;
+          }
+    }
+  }
+}
+
 // Schwarz bound per shell pair: Q = sqrt(max_{mu,nu} |(mu nu|mu nu)|) in FP64, rounded up to float32.
 __global__ void k_schwarz(int npair, const int* __restrict__ s1, const int* __restrict__ s2, const int* __restrict__ np,
                           const int* __restrict__ poff, const int* __restrict__ sh_l, const int* __restrict__ ao,
-                          const double* __restrict__ f, PairData pd, const double* __restrict__ boys,
+                          const double* __restrict__ f, PairData pd, BoysTabs bt,
                           const RStep* __restrict__ st, float* __restrict__ Q) {
   int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= npair) return;
@@ -181,8 +233,9 @@ __global__ void k_schwarz(int npair, const int* __restrict__ s1, const int* __re
       // generic Boys (runtime order): Taylor at the top order then downward
       if (T < BOYS_TMAX) {
         int k = __double2int_rn(T * BOYS_INV_H);
-        double dd = k * BOYS_H - T, acc = boys[k * BOYS_MDIM + L + BOYS_TAYLOR64 - 1];
-        for (int jj = BOYS_TAYLOR64 - 2; jj >= 0; --jj) acc = acc * dd / (jj + 1) + boys[k * BOYS_MDIM + L + jj];
+        const double* c = bt.c64 + ((size_t)k * (BOYS_MMAX + 1) + L) * BOYS_J64;
+        double dd = k * BOYS_H - T, acc = c[BOYS_J64 - 1];
+        for (int jj = BOYS_J64 - 2; jj >= 0; --jj) acc = acc * dd + c[jj];
         F[L] = acc;
         double e = exp(-T);
         for (int m = L - 1; m >= 0; --m) F[m] = (2 * T * F[m + 1] + e) / (2 * m + 1);
@@ -504,13 +557,20 @@ PairData eri_plan_impl::pairdata() const {
   PairData pd;
   pd.p = d_p; pd.P = d_P; pd.PA = d_PA; pd.PB = d_PB; pd.pref = d_pref;
   pd.pf = d_pf; pd.Pf = d_Pf; pd.PAf = d_PAf; pd.PBf = d_PBf; pd.preff = d_preff;
+  pd.E = d_E; pd.Ef = d_Ef;
   pd.n = nprimpair;
   return pd;
 }
 
+BoysTabs eri_plan_impl::boystabs() const {
+  BoysTabs b;
+  b.c64 = d_boys64; b.e64 = d_bexp64; b.c32 = d_boys32; b.e32 = d_bexp32;
+  return b;
+}
+
 ShellPairInfo eri_plan_impl::spinfo() const {
   ShellPairInfo sp;
-  sp.s1 = d_ps1; sp.s2 = d_ps2; sp.np = d_pnp; sp.poff = d_ppoff; sp.ao1 = d_pao1; sp.ao2 = d_pao2; sp.hoff = d_phoff;
+  sp.s1 = d_ps1; sp.s2 = d_ps2; sp.np = d_pnp; sp.poff = d_ppoff; sp.ao1 = d_pao1; sp.ao2 = d_pao2; sp.hoff = d_phoff; sp.eoff = d_peoff;
   return sp;
 }
 
@@ -518,10 +578,12 @@ ShellPairInfo eri_plan_impl::spinfo() const {
 int eri_plan_impl::geometry(cudaStream_t s, bool rebuild_q) {
   k_pairs<<<grid1(npair, 128), 128, 0, s>>>(npair, d_ps1, d_ps2, d_ppoff, d_sh_atom, d_sh_np, d_sh_po, d_exps, d_cn,
                                         d_coords, nprimpair, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf, d_PBf,
-                                        d_preff);
+                                        d_preff, d_pmaxp);
+  CK(cudaGetLastError());
+  k_etab<<<grid1(npair, 64), 64, 0, s>>>(npair, d_ps1, d_ps2, d_pnp, d_ppoff, d_peoff, d_sh_l, pairdata(), d_E, d_Ef);
   CK(cudaGetLastError());
   if (rebuild_q) {
-    k_schwarz<<<grid1(npair, 64), 64, 0, s>>>(npair, d_ps1, d_ps2, d_pnp, d_ppoff, d_sh_l, d_sh_ao, d_f, pairdata(), d_boys64,
+    k_schwarz<<<grid1(npair, 64), 64, 0, s>>>(npair, d_ps1, d_ps2, d_pnp, d_ppoff, d_sh_l, d_sh_ao, d_f, pairdata(), boystabs(),
                                               d_rsteps, d_Q);
     CK(cudaGetLastError());
     return build_lists(thresh, s);
@@ -603,14 +665,76 @@ void eri_plan_impl::release() {
   void* ptrs[] = {d_sh_l, d_sh_atom, d_sh_np, d_sh_po, d_sh_ao, d_exps, d_coefs, d_cn, d_f, d_coords, d_ps1, d_ps2,
                   d_pnp, d_ppoff, d_pao1, d_pao2, d_phoff, d_pcls, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf,
                   d_PBf, d_preff, d_Q, d_qmax, d_sig, d_ccount, d_coff, d_sorted, d_pos, d_counts, d_koff, d_joff,
-                  d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Dherm,
-                  d_Jherm, d_status};
+                  d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Jh, d_Dherm,
+                  d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters};
+  for (auto& e : prof_events) cudaEventDestroy(e);
+  prof_events.clear();
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
+// pairs with an exponent sum above this stay in FP64 in mixed mode (FP32 range)
+static const double kPmax32 = 3.0e3;
+
 static const int kClassL1[NPAIRCLASS] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 static const int kClassL2[NPAIRCLASS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+
+cudaError_t eri_plan_impl::prof_event_pair(cudaEvent_t* a, cudaEvent_t* b) {
+  while ((int)prof_events.size() < prof_ev_used + 2) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    prof_events.push_back(e);
+  }
+  *a = prof_events[prof_ev_used];
+  *b = prof_events[prof_ev_used + 1];
+  prof_ev_used += 2;
+  return cudaSuccess;
+}
+
+// Algorithmic FLOPs of the McMurchie-Davidson J/K path as implemented (FMA = 2):
+//   per primitive quartet: Boys 2(L+1)+20, R recursion 3 sum_{m<L} (nherm(L-m)-1),
+//     ket transform 2 nherm(la+lb) sum_{cd} prod_t (k_t+l_t+1);
+//   per bra primitive of a quartet: bra transform 2 ncd sum_{ab} prod_t (i_t+j_t+1);
+//   per contracted quartet: K 8 nab ncd, J 4 nab ncd.
+static double sum_terms(int la, int lb) {
+  double s = 0.0;
+  for (int x = 0; x < ncart(la); ++x)
+    for (int y = 0; y < ncart(lb); ++y) {
+      int ix, iy, iz, jx, jy, jz;
+      cart_xyz(la, x, ix, iy, iz);
+      cart_xyz(lb, y, jx, jy, jz);
+      s += (double)(ix + jx + 1) * (iy + jy + 1) * (iz + jz + 1);
+    }
+  return s;
+}
+static double class_flops(int X, int Y, double nq, double npq, double nbp, bool dj, bool dk) {
+  const int la = kClassL1[X], lb = kClassL2[X], lc = kClassL1[Y], ld = kClassL2[Y];
+  const int L = la + lb + lc + ld;
+  double rf = 0.0;
+  for (int m = 0; m < L; ++m) rf += 3.0 * (nherm(L - m) - 1);
+  const double nab = ncart(la) * ncart(lb), ncd = ncart(lc) * ncart(ld);
+  const double per_pq = 2.0 * (L + 1) + 20.0 + rf + 2.0 * nherm(la + lb) * sum_terms(lc, ld);
+  const double per_bp = 2.0 * ncd * sum_terms(la, lb);
+  const double per_q = (dk ? 8.0 : 0.0) * nab * ncd + (dj ? 4.0 : 0.0) * nab * ncd;
+  return npq * per_pq + nbp * per_bp + nq * per_q;
+}
+
+static cudaError_t launch_jk_class(int X, int Y, int prec, const JKArgs& ja, cudaStream_t s, int nsm) {
+  switch (X) {
+    case 0: return launch_jk_bra0(Y, prec, ja, s, nsm);
+    case 1: return launch_jk_bra1(Y, prec, ja, s, nsm);
+    case 2: return launch_jk_bra2(Y, prec, ja, s, nsm);
+    case 3: return launch_jk_bra3(Y, prec, ja, s, nsm);
+    case 4: return launch_jk_bra4(Y, prec, ja, s, nsm);
+    case 5: return launch_jk_bra5(Y, prec, ja, s, nsm);
+    case 6: return launch_jk_bra6(Y, prec, ja, s, nsm);
+    case 7: return launch_jk_bra7(Y, prec, ja, s, nsm);
+    case 8: return launch_jk_bra8(Y, prec, ja, s, nsm);
+    case 9: return launch_jk_bra9(Y, prec, ja, s, nsm);
+  }
+  return cudaErrorInvalidValue;
+}
 
 extern "C" int eri_default_opts(eri_opts_t* o) {
   if (!o) return ERI_EINVAL;
@@ -618,6 +742,8 @@ extern "C" int eri_default_opts(eri_opts_t* o) {
   o->precision = ERI_FP64;
   o->mixed_tau = 1e-5;
   o->device = -1;
+  o->j_engine = 1;
+  o->profile = 0;
   return ERI_OK;
 }
 
@@ -665,8 +791,9 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
   // shell pairs in pair-index order (a >= b), oriented so that s1 has the higher l
   const int npair = ns * (ns + 1) / 2;
   P->npair = npair;
-  std::vector<int> ps1(npair), ps2(npair), pnp(npair), ppoff(npair), pao1(npair), pao2(npair), phoff(npair), pcls(npair);
-  int64_t nprimpair = 0, nherm_tot = 0;
+  std::vector<int> ps1(npair), ps2(npair), pnp(npair), ppoff(npair), pao1(npair), pao2(npair), phoff(npair), pcls(npair),
+      peoff(npair);
+  int64_t nprimpair = 0, nherm_tot = 0, ne_tot = 0;
   for (int a = 0; a < ns; ++a)
     for (int b = 0; b <= a; ++b) {
       int ip = a * (a + 1) / 2 + b;
@@ -678,10 +805,15 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
       pao1[ip] = ao[x]; pao2[ip] = ao[y];
       phoff[ip] = (int)nherm_tot;
       pcls[ip] = pair_class(l[x], l[y]);
+      peoff[ip] = (int)ne_tot;
       nprimpair += pnp[ip];
       nherm_tot += (int64_t)pnp[ip] * nherm(l[x] + l[y]);
+      ne_tot += (int64_t)pnp[ip] * 3 * (l[x] + 1) * (l[y] + 1) * (l[x] + l[y] + 1);
     }
-  if (nprimpair > (1LL << 30) || nherm_tot > (1LL << 31) - 1) { delete P; return ERI_EUNSUPPORTED; }
+  if (nprimpair > (1LL << 30) || nherm_tot > (1LL << 31) - 1 || ne_tot > (1LL << 31) - 1) {
+    delete P;
+    return ERI_EUNSUPPORTED;
+  }
   P->nprimpair = (int)nprimpair;
   P->nherm_tot = nherm_tot;
   int rc = ERI_OK;
@@ -706,9 +838,15 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
     CKP(dalloc(&P->d_koff, NPAIRCLASS * NPAIRCLASS)); CKP(dalloc(&P->d_joff, NPAIRCLASS * NPAIRCLASS));
     CKP(dalloc(&P->d_ktot, NPAIRCLASS * NPAIRCLASS)); CKP(dalloc(&P->d_jtot, NPAIRCLASS * NPAIRCLASS));
     CKP(dalloc(&P->d_kprim, NPAIRCLASS * NPAIRCLASS));
-    CKP(dalloc(&P->d_boys64, (size_t)BOYS_NT * BOYS_MDIM)); CKP(dalloc(&P->d_boys32, (size_t)BOYS_NT * BOYS_MDIM));
+    CKP(dalloc(&P->d_boys64, (size_t)BOYS_NT * (BOYS_MMAX + 1) * BOYS_J64));
+    CKP(dalloc(&P->d_boys32, (size_t)BOYS_NT * (BOYS_MMAX + 1) * BOYS_J32));
+    CKP(dalloc(&P->d_bexp64, BOYS_NT)); CKP(dalloc(&P->d_bexp32, BOYS_NT));
+    CKP(dalloc(&P->d_peoff, npair)); CKP(dalloc(&P->d_E, ne_tot)); CKP(dalloc(&P->d_Ef, ne_tot));
+    CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_dmax, (size_t)ns * ns));
+    CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3));
     CKP(dalloc(&P->d_rsteps, st.size()));
     CKP(dalloc(&P->d_Dp, (size_t)nbf * nbf)); CKP(dalloc(&P->d_Kh, (size_t)nbf * nbf));
+    CKP(dalloc(&P->d_Jh, (size_t)nbf * nbf));
     CKP(dalloc(&P->d_Dherm, nherm_tot)); CKP(dalloc(&P->d_Jherm, nherm_tot));
     CKP(dalloc(&P->d_status, 1));
     if (P->alloc_pairs() != ERI_OK) { rc = ERI_ENOMEM; goto fail; }
@@ -728,12 +866,13 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
     CKP(cudaMemcpy(P->d_pao1, pao1.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
     CKP(cudaMemcpy(P->d_pao2, pao2.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
     CKP(cudaMemcpy(P->d_phoff, phoff.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(P->d_peoff, peoff.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
     CKP(cudaMemcpy(P->d_pcls, pcls.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
     CKP(cudaMemcpy(P->d_rsteps, st.data(), sizeof(RStep) * st.size(), cudaMemcpyHostToDevice));
     CKP(cudaMemset(P->d_status, 0, sizeof(int)));
     k_normalize<<<grid1(ns, 64), 64>>>(ns, P->d_sh_l, P->d_sh_np, P->d_sh_po, P->d_exps, P->d_coefs, P->d_cn);
     k_compfac<<<grid1(ns, 64), 64>>>(ns, P->d_sh_l, P->d_sh_ao, P->d_f);
-    k_boys_table<<<grid1(BOYS_NT, 128), 128>>>(P->d_boys64, P->d_boys32);
+    k_boys_table<<<grid1(BOYS_NT, 128), 128>>>(P->d_boys64, P->d_bexp64, P->d_boys32, P->d_bexp32);
     CKP(cudaGetLastError());
     P->thresh = o.thresh;
     rc = P->geometry(s, true);
@@ -773,18 +912,18 @@ extern "C" int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double
   const int64_t nn = (int64_t)n * n;
   k_scale_d<<<grid1(nn, 256), 256, 0, s>>>(n, D, P->d_f, P->d_Dp);
   CK(cudaGetLastError());
-  const int prec = precision == ERI_MIXED ? 1 : 0;  // mixed tiering arrives with the FP32 path
-  (void)prec;
   double fj = 0.0, fk = 0.0;
-  if (J) {
+  const bool jengine = J && !K && P->opts.j_engine;
+  if (jengine) {
+    // J alone: Hermite density -> J-engine -> Hermite J to Cartesian (Eq. j_formula)
     CK(cudaMemsetAsync(P->d_Jherm, 0, sizeof(double) * (size_t)P->nherm_tot, s));
     k_hermite_density<<<grid1(P->npair, 64), 64, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_pnp, P->d_ppoff,
                                                           P->d_phoff, P->d_sh_l, P->d_sh_ao, P->d_sig, P->pairdata(),
                                                           P->d_Dp, n, P->d_Dherm);
     CK(cudaGetLastError());
     JArgs ja;
-    ja.pd = P->pairdata(); ja.sp = P->spinfo(); ja.boys64 = P->d_boys64; ja.boys32 = P->d_boys32;
-    ja.rsteps = P->d_rsteps; ja.Dherm = P->d_Dherm; ja.Jherm = P->d_Jherm; ja.tier = nullptr; ja.tier_want = 0;
+    ja.pd = P->pairdata(); ja.sp = P->spinfo(); ja.bt = P->boystabs();
+    ja.rsteps = P->d_rsteps; ja.Dherm = P->d_Dherm; ja.Jherm = P->d_Jherm;
     for (int X = 0; X < NPAIRCLASS; ++X)
       for (int Y = 0; Y < NPAIRCLASS; ++Y) {
         ja.wl = P->jlist(X, Y);
@@ -804,37 +943,61 @@ extern "C" int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double
       }
     CK(cudaMemsetAsync(J, 0, sizeof(double) * nn, s));
     k_post_j<<<grid1((int64_t)P->npair * 100, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_pnp, P->d_ppoff,
-                                                            P->d_phoff, P->d_sh_l, P->d_sh_ao, P->d_sig, P->pairdata(),
-                                                            P->d_Jherm, P->d_f, n, J);
+                                                                 P->d_phoff, P->d_sh_l, P->d_sh_ao, P->d_sig,
+                                                                 P->pairdata(), P->d_Jherm, P->d_f, n, J);
     CK(cudaGetLastError());
-  }
-  if (K) {
-    CK(cudaMemsetAsync(P->d_Kh, 0, sizeof(double) * nn, s));
-    KArgs ka;
-    ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.boys64 = P->d_boys64; ka.boys32 = P->d_boys32;
-    ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Kh = P->d_Kh; ka.tier = nullptr; ka.tier_want = 0; ka.nbf = n;
+  } else {
+    // J and/or K from contracted Cartesian ERIs over canonical quartets
+    if (K) CK(cudaMemsetAsync(P->d_Kh, 0, sizeof(double) * nn, s));
+    if (J) CK(cudaMemsetAsync(P->d_Jh, 0, sizeof(double) * nn, s));
+    CK(cudaMemsetAsync(P->d_counters, 0, sizeof(unsigned long long) * NPAIRCLASS * NPAIRCLASS * 6, s));
+    const bool mixed = precision == ERI_MIXED;
+    if (mixed) {
+      k_dmax<<<grid1((int64_t)P->nshell * P->nshell, 256), 256, 0, s>>>(P->nshell, P->d_sh_l, P->d_sh_ao, P->d_Dp, n,
+                                                                         P->d_dmax);
+      CK(cudaGetLastError());
+    }
+    JKArgs ja;
+    KArgs& ka = ja.k;
+    ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
+    ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Kh = K ? P->d_Kh : nullptr;
+    ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp;
+    ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
+    ka.nshell = P->nshell;
+    ka.nbf = n;
+    ja.Jh = J ? P->d_Jh : nullptr;
+    P->last_mixed = mixed;
+    P->last_do_j = J != nullptr;
+    P->last_do_k = K != nullptr;
     for (int X = 0; X < NPAIRCLASS; ++X)
       for (int Y = 0; Y <= X; ++Y) {
         ka.wl = P->klist(X, Y);
         ka.same_class = X == Y;
         if (ka.wl.total == 0) continue;
-        cudaError_t e = cudaErrorInvalidValue;
-        switch (X) {
-          case 0: e = launch_k_bra0(Y, 0, ka, s, P->nsm); break;
-          case 1: e = launch_k_bra1(Y, 0, ka, s, P->nsm); break;
-          case 2: e = launch_k_bra2(Y, 0, ka, s, P->nsm); break;
-          case 3: e = launch_k_bra3(Y, 0, ka, s, P->nsm); break;
-          case 4: e = launch_k_bra4(Y, 0, ka, s, P->nsm); break;
-          case 5: e = launch_k_bra5(Y, 0, ka, s, P->nsm); break;
-          case 6: e = launch_k_bra6(Y, 0, ka, s, P->nsm); break;
-          case 7: e = launch_k_bra7(Y, 0, ka, s, P->nsm); break;
-          case 8: e = launch_k_bra8(Y, 0, ka, s, P->nsm); break;
-          case 9: e = launch_k_bra9(Y, 0, ka, s, P->nsm); break;
+        for (int tier = 0; tier < (mixed ? 2 : 1); ++tier) {
+          ka.tier_want = tier;
+          ka.counter = P->d_counters + ((X * NPAIRCLASS + Y) * 2 + tier) * 3;
+          cudaEvent_t e0 = nullptr, e1 = nullptr;
+          if (P->opts.profile) {
+            CK(P->prof_event_pair(&e0, &e1));
+            CK(cudaEventRecord(e0, s));
+          }
+          CK(launch_jk_class(X, Y, tier, ja, s, P->nsm));
+          if (P->opts.profile) {
+            CK(cudaEventRecord(e1, s));
+            P->prof_log.push_back({X, Y, tier, P->prof_ev_used - 2});
+          }
         }
-        CK(e);
       }
-    k_post_k<<<grid1(nn, 256), 256, 0, s>>>(n, P->d_Kh, P->d_f, K);
-    CK(cudaGetLastError());
+    P->prof_builds += P->opts.profile ? 1 : 0;
+    if (K) {
+      k_post_k<<<grid1(nn, 256), 256, 0, s>>>(n, P->d_Kh, P->d_f, K);
+      CK(cudaGetLastError());
+    }
+    if (J) {
+      k_post_k<<<grid1(nn, 256), 256, 0, s>>>(n, P->d_Jh, P->d_f, J);
+      CK(cudaGetLastError());
+    }
   }
   P->last_flops_j = fj;
   P->last_flops_k = fk;
@@ -888,11 +1051,64 @@ extern "C" int eri_get_stats(eri_plan_t* plan, eri_stats_t* st) {
       st->prim_quartets_k += P->h_kprim[i];
     }
   }
-  st->flops_j = P->last_flops_j;
-  st->flops_k = P->last_flops_k;
+  {
+    unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6];
+    CK(cudaMemcpy(c, P->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+    double fl = 0.0;
+    for (int X = 0; X < NPAIRCLASS; ++X)
+      for (int Y = 0; Y <= X; ++Y)
+        for (int t = 0; t < 2; ++t) {
+          const unsigned long long* q = c + ((X * NPAIRCLASS + Y) * 2 + t) * 3;
+          fl += class_flops(X, Y, (double)q[0], (double)q[1], (double)q[2], P->last_do_j, P->last_do_k);
+          if (t == 1) st->quartets_k_fp32 += (int64_t)q[0];
+        }
+    st->flops_k = fl;
+    st->flops_j = 0.0;
+  }
   int status = 0;
   CK(cudaMemcpy(&status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   st->device_status = status;
+  return ERI_OK;
+}
+
+extern "C" int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t cap, int32_t* count) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !count || (cap > 0 && !out)) return ERI_EINVAL;
+  CK(cudaSetDevice(P->device));
+  CK(cudaDeviceSynchronize());
+  unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6];
+  CK(cudaMemcpy(c, P->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+  double ms[NPAIRCLASS * NPAIRCLASS * 2] = {};
+  int nl[NPAIRCLASS * NPAIRCLASS * 2] = {};
+  for (const auto& r : P->prof_log) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, P->prof_events[r.ev], P->prof_events[r.ev + 1]));
+    const int k = (r.X * NPAIRCLASS + r.Y) * 2 + r.tier;
+    ms[k] += t;
+    nl[k] += 1;
+  }
+  int n = 0;
+  for (int k = 0; k < NPAIRCLASS * NPAIRCLASS * 2; ++k) {
+    if (!nl[k]) continue;
+    if (n < cap) {
+      const int X = k / (2 * NPAIRCLASS), Y = (k / 2) % NPAIRCLASS, t = k % 2;
+      const unsigned long long* q = c + k * 3;
+      eri_launch_prof_t& o = out[n];
+      o.bra_class = X;
+      o.ket_class = Y;
+      o.tier = t;
+      o.launches = nl[k];
+      o.ms = ms[k];
+      o.quartets = (int64_t)q[0];
+      o.prim_quartets = (int64_t)q[1];
+      o.flops = class_flops(X, Y, (double)q[0], (double)q[1], (double)q[2], P->last_do_j, P->last_do_k);
+    }
+    ++n;
+  }
+  *count = n;
+  P->prof_log.clear();
+  P->prof_ev_used = 0;
+  P->prof_builds = 0;
   return ERI_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal plan state behind the opaque eri_plan_t of include/eri.h.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 #include "common.cuh"
 #include "../../include/eri.h"
@@ -34,17 +35,30 @@ struct eri_plan_impl {
   int64_t h_ktot[eri::NPAIRCLASS * eri::NPAIRCLASS] = {}, h_jtot[eri::NPAIRCLASS * eri::NPAIRCLASS] = {};
   int64_t h_kprim[eri::NPAIRCLASS * eri::NPAIRCLASS] = {};
   // tables
-  double* d_boys64 = nullptr;
-  float* d_boys32 = nullptr;
+  double *d_boys64 = nullptr, *d_bexp64 = nullptr;
+  float *d_boys32 = nullptr, *d_bexp32 = nullptr;
+  int* d_peoff = nullptr;
+  double* d_E = nullptr;
+  float* d_Ef = nullptr;
   eri::RStep* d_rsteps = nullptr;
   // per-build workspace
-  double *d_Dp = nullptr, *d_Kh = nullptr, *d_Dherm = nullptr, *d_Jherm = nullptr;
+  double *d_Dp = nullptr, *d_Kh = nullptr, *d_Jh = nullptr, *d_Dherm = nullptr, *d_Jherm = nullptr;
   int* d_status = nullptr;
+  float *d_pmaxp = nullptr, *d_dmax = nullptr;
+  unsigned long long* d_counters = nullptr;  // [X*10+Y][tier][items, prim quartets, bra primitives]
+  bool last_mixed = false, last_do_j = false, last_do_k = false;
+  // optional per-launch profiling (opts.profile): events recorded around each class launch
+  struct ProfRec { int X, Y, tier, ev; };
+  std::vector<cudaEvent_t> prof_events;
+  std::vector<ProfRec> prof_log;
+  int prof_builds = 0, prof_ev_used = 0;
+  cudaError_t prof_event_pair(cudaEvent_t* a, cudaEvent_t* b);
 
   int alloc_pairs();
   int geometry(cudaStream_t s, bool rebuild_q);
   int build_lists(double th, cudaStream_t s);
   eri::PairData pairdata() const;
+  eri::BoysTabs boystabs() const;
   eri::ShellPairInfo spinfo() const;
   eri::WorkList klist(int X, int Y) const;
   eri::WorkList jlist(int X, int Y) const;

@@ -106,3 +106,35 @@ def test_jk_threshold_and_only_one(eri):
     assert np.abs(Jo.cpu().numpy() - Jr).max() < TOL
     Jn, Kn = plan.build_jk(Dt, want_j=False)
     assert Jn is None and np.abs(Kn.cpu().numpy() - Kr).max() < TOL
+
+
+def test_j_only_cartesian_route(eri):
+    import torch
+    basis, D = W.small_system(["2s1p1d1f", "1s1p1d"], seed=13)
+    plan = eri.Plan(basis, thresh=1e-12, j_engine=False)
+    Dt = torch.from_numpy(D).cuda()
+    J, _ = plan.build_jk(Dt, want_k=False)
+    o = oracle.Oracle(basis)
+    Jr, _ = o.jk(D, 1e-12, o.schwarz())
+    assert np.abs(J.cpu().numpy() - Jr).max() < TOL
+
+
+@pytest.mark.parametrize("tau,etol,mtol", [(1e-5, 1e-6, 1e-6), (1e30, 2e-5, 2e-4)])
+def test_mixed_precision_w0(eri, tau, etol, mtol):
+    """Mixed path: quartets with Q_ab Q_cd max|D| < tau in FP32 (tau = 1e30: all of them).
+    Energy error against the oracle within etol (1e-6 Eh at the default tau)."""
+    import torch
+    basis, D = W.workload(0)
+    plan = eri.Plan(basis, thresh=1e-12, precision=eri.ERI_MIXED, mixed_tau=tau)
+    Dt = torch.from_numpy(D).cuda()
+    J, K = plan.build_jk(Dt)
+    E = plan.energy(Dt, J, K).cpu().numpy()
+    st = plan.stats()
+    o = oracle.Oracle(basis)
+    Jr, Kr = o.jk(D, 1e-12, o.schwarz())
+    ej, ek = o.energy(D, Jr, Kr)
+    assert abs(E[0] - ej) < etol and abs(E[1] - ek) < etol, (E[0] - ej, E[1] - ek)
+    assert np.abs(J.cpu().numpy() - Jr).max() < mtol
+    assert np.abs(K.cpu().numpy() - Kr).max() < mtol
+    if tau > 1:
+        assert st["quartets_k_fp32"] == st["quartets_k"]
