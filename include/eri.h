@@ -169,6 +169,28 @@ int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t cap, int32
 /* Statistics of the plan and of its last build (host copy; synchronises). */
 int eri_get_stats(eri_plan_t* plan, eri_stats_t* stats);
 
+/*
+ * J and K exactly as eri_build_jk(plan, D, J, K, -1, ERI_FP64, stream), for
+ * callers that cannot allocate device memory when they build (code running
+ * during CUDA graph capture, inside a device allocator, or on hosts that
+ * forbid allocation after start-up).  The paper has no counterpart of this
+ * call.  Its scratch (scaled density and half-J / half-K accumulators) is one
+ * fixed device array inside the library, sized for at most
+ * ERI_NOALLOC_MAX_NBF basis functions; a plan with more gets ERI_EUNSUPPORTED
+ * and a message on stderr.  The call allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
+ *   - The first call on a device looks up the array's device address on that
+ *     device (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.
+ *   - Every call, on every plan and stream, uses the same array, which keeps
+ *     the previous call's contents (the accumulators are cleared at the start
+ *     of each call).  Calls whose GPU work overlaps, on different streams or
+ *     threads, race on it: order them.
+ * D, J, K: device pointers as for eri_build_jk; J or K may be NULL.
+ */
+#define ERI_NOALLOC_MAX_NBF 256
+int eri_build_jk_noalloc(eri_plan_t* plan, const double* D, double* J, double* K, void* stream);
+
 /* Free every device and host resource of the plan (NULL is a no-op). */
 int eri_plan_destroy(eri_plan_t* plan);
 

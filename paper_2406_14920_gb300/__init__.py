@@ -71,6 +71,7 @@ def lib():
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.eri_get_stats.argtypes = [vp, C.POINTER(StatsT)]
         L.eri_get_profile.argtypes = [vp, C.POINTER(LaunchProfT), i32, C.POINTER(C.c_int32)]
+        L.eri_build_jk_noalloc.argtypes = [vp, vp, vp, vp, vp]
         L.eri_plan_destroy.argtypes = [vp]
         L.eri_strerror.argtypes = [C.c_int]
         L.eri_strerror.restype = C.c_char_p

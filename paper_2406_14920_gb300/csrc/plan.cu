@@ -1004,6 +1004,52 @@ extern "C" int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double
   return ERI_OK;
 }
 
+// FP64 J/K over canonical quartets with caller-provided scratch (D', half-K,
+// half-J, each nbf*nbf doubles).  Serves eri_build_jk_noalloc (noalloc.cu):
+// launches kernels only, allocates nothing, uses the plan's current lists.
+int eri_build_jk_scratch(eri_plan_t* plan, const double* D, double* J, double* K, double* Dp, double* Kh, double* Jh,
+                         cudaStream_t s) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  const int n = P->nbf;
+  const int64_t nn = (int64_t)n * n;
+  k_scale_d<<<grid1(nn, 256), 256, 0, s>>>(n, D, P->d_f, Dp);
+  CK(cudaGetLastError());
+  if (K) CK(cudaMemsetAsync(Kh, 0, sizeof(double) * nn, s));
+  if (J) CK(cudaMemsetAsync(Jh, 0, sizeof(double) * nn, s));
+  JKArgs ja;
+  KArgs& ka = ja.k;
+  ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
+  ka.rsteps = P->d_rsteps; ka.Dp = Dp; ka.Kh = K ? Kh : nullptr;
+  ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp;
+  ka.tau = 0.0f; ka.pmax32 = 0.0f; ka.mixed = 0; ka.tier_want = 0; ka.counter = nullptr;
+  ka.nshell = P->nshell;
+  ka.nbf = n;
+  ja.Jh = J ? Jh : nullptr;
+  for (int X = 0; X < NPAIRCLASS; ++X)
+    for (int Y = 0; Y <= X; ++Y) {
+      ka.wl = P->klist(X, Y);
+      ka.same_class = X == Y;
+      if (ka.wl.total == 0) continue;
+      CK(launch_jk_class(X, Y, 0, ja, s, P->nsm));
+    }
+  if (K) {
+    k_post_k<<<grid1(nn, 256), 256, 0, s>>>(n, Kh, P->d_f, K);
+    CK(cudaGetLastError());
+  }
+  if (J) {
+    k_post_k<<<grid1(nn, 256), 256, 0, s>>>(n, Jh, P->d_f, J);
+    CK(cudaGetLastError());
+  }
+  return ERI_OK;
+}
+
+int eri_plan_nbf_device(eri_plan_t* plan, int* nbf, int* device) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  *nbf = P->nbf;
+  *device = P->device;
+  return ERI_OK;
+}
+
 extern "C" int eri_energy(eri_plan_t* plan, const double* D, const double* J, const double* K, double* E_out,
                           void* stream) {
   eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
