@@ -112,33 +112,39 @@ def sample_quartets(lists, basis, n, seed):
     cc = lists["class_count"]
     coff = np.concatenate([[0], np.cumsum(cc)])
     srt, counts = lists["sorted"], lists["counts"]
-    per_cp, bra_w = [], {}
+    cps, cums, tots = [], [], []
     for X in range(10):
         for Y in range(X + 1):
             bras = srt[coff[X]:coff[X + 1]]
             nk = counts[bras, Y].astype(np.int64)
             if X == Y:
                 nk = np.minimum(nk, np.arange(1, len(bras) + 1))
-            per_cp.append(((X, Y), int(nk.sum())))
-            bra_w[(X, Y)] = nk
-    tot = np.array([t for _, t in per_cp], dtype=np.float64)
-    picks = rng.choice(len(per_cp), size=n, p=tot / tot.sum())
-    out = np.zeros((n, 4), np.int32)
-    for q, ci in enumerate(picks):
-        (X, Y), _ = per_cp[ci]
-        nk = bra_w[(X, Y)]
-        i = rng.choice(len(nk), p=nk / nk.sum())
-        k = rng.integers(0, nk[i])
-        pb = int(srt[coff[X] + i])
-        pk = int(srt[coff[Y] + k])
-        for off, p in ((0, pb), (2, pk)):
-            a = int((np.sqrt(8 * p + 1) - 1) // 2)
-            while a * (a + 1) // 2 > p:
-                a -= 1
-            while (a + 1) * (a + 2) // 2 <= p:
-                a += 1
-            out[q, off], out[q, off + 1] = a, p - a * (a + 1) // 2
-    return out
+            cps.append((X, Y))
+            cums.append(np.cumsum(nk))
+            tots.append(int(nk.sum()))
+    tots = np.asarray(tots, dtype=np.float64)
+    per = rng.multinomial(n, tots / tots.sum())
+    rows = []
+    for (X, Y), cum, m in zip(cps, cums, per):
+        if m == 0:
+            continue
+        u = rng.integers(0, cum[-1], size=m)
+        i = np.searchsorted(cum, u, side="right")
+        k = u - np.concatenate([[0], cum])[i]  # offset inside bra i's range of kets
+        pb = srt[coff[X] + i]
+        pk = srt[coff[Y] + k]
+        rows.append(np.stack([pb, pk], axis=1))
+    pp = np.concatenate(rows)[rng.permutation(n)]
+
+    def split(p):
+        a = np.floor((np.sqrt(8.0 * p + 1.0) - 1.0) / 2.0).astype(np.int64)
+        a -= (a * (a + 1) // 2 > p)
+        a += ((a + 1) * (a + 2) // 2 <= p)
+        return a, p - a * (a + 1) // 2
+
+    a, b = split(pp[:, 0].astype(np.int64))
+    c, d = split(pp[:, 1].astype(np.int64))
+    return np.ascontiguousarray(np.stack([a, b, c, d], axis=1), dtype=np.int32)
 
 
 def oracle_rate(basis, quartets, target_s):
@@ -276,6 +282,16 @@ def run_ours(args, rank, world, local_rank):
                 "share": round(dom["ms"] / tot_ms, 4),
                 "peak_source": "FP64: GB300 nominal 1.25 TFLOP/s; FP32: 152 SM x 128 x 2 x 2.07 GHz"}
     fl_total = sum(r["flops"] for r in prof)
+    tier_ms = {"fp64": sum(r["ms"] for r in prof if r["tier"] == 0) / args.steps,
+               "fp32": sum(r["ms"] for r in prof if r["tier"] == 1) / args.steps}
+    top = sorted(prof, key=lambda r: -r["ms"])[:8]
+    profile_top = [{"class": f"({CLASS_NAMES[r['bra_class']]}|{CLASS_NAMES[r['ket_class']]})",
+                    "tier": "fp64" if r["tier"] == 0 else "fp32", "ms_per_step": round(r["ms"] / args.steps, 2),
+                    "tflops": round(r["flops"] / (r["ms"] / r["launches"] * 1e-3) / 1e12, 4)} for r in top]
+    fp64_top = sorted(prof64, key=lambda r: -r["ms"])[:5]
+    fp64_profile_top = [{"class": f"({CLASS_NAMES[r['bra_class']]}|{CLASS_NAMES[r['ket_class']]})",
+                         "ms_per_step": round(r["ms"] / args.fp64_steps, 2),
+                         "tflops": round(r["flops"] / (r["ms"] / r["launches"] * 1e-3) / 1e12, 4)} for r in fp64_top]
     launches_per_step = len(prof) + 4  # class launches + D scaling, D block maxima, two symmetrisations
 
     out = {
@@ -292,7 +308,11 @@ def run_ours(args, rank, world, local_rank):
         "speedup_mixed_vs_fp64": (ms64 / args.fp64_steps) / (ms_mixed / args.steps),
         "energy": {"E_J_fp64": float(e64[0]), "E_K_fp64": float(e64[1]),
                    "dE_J_mixed": float(emx[0] - e64[0]), "dE_K_mixed": float(emx[1] - e64[1])},
-        "algorithmic_tflops": {"mixed": fl_total / ((tot_ms / args.steps) * 1e-3) / 1e12},
+        "algorithmic_tflops": {"mixed": fl_total / ((tot_ms / args.steps) * 1e-3) / 1e12,
+                               "fp64": sum(r["flops"] for r in prof64) / (sum(r["ms"] for r in prof64) / args.fp64_steps * 1e-3) / 1e12},
+        "tier_ms_per_step": tier_ms,
+        "profile_top": profile_top,
+        "fp64_profile_top": fp64_profile_top,
         "roofline": roofline,
         "e2e": {"value": world * nq * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 16 * n * n},
@@ -300,7 +320,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        quartets = sample_quartets(plan.lists(), basis, 4000, seed=1234)
+        quartets = sample_quartets(plan.lists(), basis, 400000, seed=1234)
         rate, ns, dt, cores = oracle_rate(basis, quartets, args.cpu_seconds)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{ns} seeded uniformly sampled significant canonical shell quartets of "
@@ -317,7 +337,7 @@ def run_reference(args):
     import workloads as W
     basis, _ = W.workload(WORKLOAD_ID)
     lists = _lists_without_gpu(basis)
-    quartets = sample_quartets(lists, basis, 20000, seed=4321)
+    quartets = sample_quartets(lists, basis, 400000, seed=4321)
     o = oracle.Oracle(basis)
     # size one step to about args.cpu_seconds of CPU work
     t = time.perf_counter()
@@ -369,10 +389,25 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="small case for ncu section captures: the first 20 atoms of the workload, two mixed builds")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.ncu_case:
+        import torch
+        import paper_2406_14920_gb300 as eri
+        import workloads as W
+        basis, D = W.workload(WORKLOAD_ID)
+        b2, D2 = W.subset_atoms(basis, D, list(range(20)))
+        plan = eri.Plan(b2, thresh=THRESH, precision=eri.ERI_MIXED, mixed_tau=TAU)
+        Dt = torch.from_numpy(D2).cuda()
+        for _ in range(2):
+            plan.build_jk(Dt)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": True, "nbf": b2.nbf, "quartets": plan.stats()["quartets_k"]}))
+        return
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)

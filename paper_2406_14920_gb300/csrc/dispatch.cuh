@@ -63,7 +63,7 @@ cudaError_t launch_jk_t(const JKArgs& a, cudaStream_t s, int nsm) {
     using S = BShape<LA, LB, LC, LD, T>;
     constexpr int WPB = 4;
     auto kern = jk_warp_kernel<LA, LB, LC, LD, T>;
-    cudaError_t e = launch_persistent(kern, WPB * S::smem_per_warp(), a.k.wl.total, WPB, nsm, &li);
+    cudaError_t e = launch_persistent(kern, S::table_bytes() + WPB * S::smem_per_warp(), a.k.wl.total, WPB, nsm, &li);
     if (e != cudaSuccess) return e;
     kern<<<li.grid, li.block, li.smem, s>>>(a);
   }

@@ -31,7 +31,9 @@ struct BShape {
   static constexpr int B = L + 1, BOX = B * B * B, NPING = L > 0 ? nherm(L - 1) : 1;
   static constexpr int NEB = (LA + 1) * (LB + 1) * (LAB + 1), NEK = (LC + 1) * (LD + 1) * (LCD + 1);
   static constexpr int NSC = L + 5;  // F'_0..F'_L, PQx, PQy, PQz, c
-  static constexpr int BUDGET = (int)((44 * 1024) / sizeof(T));  // elements of T per warp
+  // shared memory per warp: FP64 needs only one warp per SM sub-partition to fill
+  // its pipe, FP32 needs many warps to hide latency
+  static constexpr int BUDGET = sizeof(T) == 8 ? (44 * 1024) / 8 : (12 * 1024) / 4;  // elements of T per warp
   static constexpr int FIXED = 3 * NEB;
   static constexpr int PER_G = BOX + 2 * NPING + NSC + 3 * NEK;
   static constexpr int PER_C = HABP + NAB;
@@ -42,8 +44,22 @@ struct BShape {
   static constexpr int SM_BOX = 0, SM_PING = SM_BOX + G * BOX, SM_SC = SM_PING + G * 2 * NPING,
                        SM_EK = SM_SC + G * NSC, SM_EB = SM_EK + G * 3 * NEK, SM_W = SM_EB + 3 * NEB,
                        SM_X = SM_W + CH * HABP, SM_TOTAL = SM_X + NAB * CH;
-  static constexpr size_t smem_per_warp() { return sizeof(T) * SM_TOTAL; }
+  __host__ __device__ static constexpr size_t smem_per_warp() { return sizeof(T) * SM_TOTAL; }
+  // block-shared index tables (ints): cd table, ab table, P table, W row bases
+  static constexpr int LEXB = (LAB + 1) * (LAB + 1);
+  static constexpr int TAB_INTS = 2 * NCD + 2 * NAB + HAB + LEXB;
+  static constexpr int TABLE_BYTES = ((4 * TAB_INTS + 15) / 16) * 16;
+  __host__ __device__ static constexpr size_t table_bytes() { return TABLE_BYTES; }
 };
+
+// W is stored per cd with a "lexicographic" Hermite index (t, then u, then v)
+// so that for fixed (t, u) consecutive v are consecutive: lex(t,u,v) = base(t,u) + v.
+__host__ __device__ constexpr int lex_base(int lmax, int t, int u) {
+  int b = 0;
+  for (int x = 0; x < t; ++x) b += (lmax - x + 1) * (lmax - x + 2) / 2;
+  for (int y = 0; y < u; ++y) b += lmax - t - y + 1;
+  return b;
+}
 
 template <int LA, int LB, int LC, int LD, typename T>
 __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
@@ -54,7 +70,39 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
   const KArgs& a = A.k;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  T* sm = reinterpret_cast<T*>(smraw) + (size_t)wib * S::SM_TOTAL;
+  // index tables shared by the block: per ket pair cd the E offsets and term
+  // counts, the same per bra pair ab, per bra Hermite index P its box offset
+  // and its W slot, and the W row bases for step D
+  int* tab_cd = reinterpret_cast<int*>(smraw);
+  int* tab_ab = tab_cd + 2 * NCD;
+  int* tab_p = tab_ab + 2 * NAB;
+  int* tab_lex = tab_p + HAB;
+  for (int i = threadIdx.x; i < NCD; i += blockDim.x) {
+    int kx, ky, kz, lx, ly, lz;
+    cart_xyz(LC, i / ND, kx, ky, kz);
+    cart_xyz(LD, i % ND, lx, ly, lz);
+    tab_cd[2 * i] = ((kx * (LD + 1) + lx) * (LCD + 1)) | ((NEK + (ky * (LD + 1) + ly) * (LCD + 1)) << 10) |
+                    ((2 * NEK + (kz * (LD + 1) + lz) * (LCD + 1)) << 20);
+    tab_cd[2 * i + 1] = (kx + lx) | ((ky + ly) << 4) | ((kz + lz) << 8);
+  }
+  for (int i = threadIdx.x; i < NAB; i += blockDim.x) {
+    int ix, iy, iz, jx, jy, jz;
+    cart_xyz(LA, i / NB, ix, iy, iz);
+    cart_xyz(LB, i % NB, jx, jy, jz);
+    tab_ab[2 * i] = ((ix * (LB + 1) + jx) * (LAB + 1)) | ((NEB + (iy * (LB + 1) + jy) * (LAB + 1)) << 10) |
+                    ((2 * NEB + (iz * (LB + 1) + jz) * (LAB + 1)) << 20);
+    tab_ab[2 * i + 1] = (ix + jx) | ((iy + jy) << 4) | ((iz + jz) << 8);
+  }
+  for (int i = threadIdx.x; i < HAB; i += blockDim.x) {
+    const int t = herm_t(i), u = herm_u(i), v = herm_v(i);
+    tab_p[i] = ((t * B + u) * B + v) | ((lex_base(LAB, t, u) + v) << 16);
+  }
+  for (int i = threadIdx.x; i < S::LEXB; i += blockDim.x) {
+    const int t = i / (LAB + 1), u = i % (LAB + 1);
+    tab_lex[i] = (t + u <= LAB) ? lex_base(LAB, t, u) : 0;
+  }
+  __syncthreads();
+  T* sm = reinterpret_cast<T*>(smraw + S::table_bytes()) + (size_t)wib * S::SM_TOTAL;
   T* boxes = sm + S::SM_BOX;
   T* pings = sm + S::SM_PING;
   T* scal = sm + S::SM_SC;
@@ -131,6 +179,7 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
             if (lane < ng) pings[lane * 2 * NPING] = scal[lane * NSC + L];
             __syncwarp();
             int cur = 0;
+#pragma unroll
             for (int m = L - 1; m >= 0; --m) {
               const int ne = nherm(L - m);
               for (int it = lane; it < ng * ne; it += 32) {
@@ -158,56 +207,46 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
           // step C: ket transform, items (ci, P)
           for (int it = lane; it < nci * HAB; it += 32) {
             const int ci = it / HAB, P = it - ci * HAB;
-            const int cd = c0 + ci;
-            int kx, ky, kz, lx, ly, lz;
-            cart_xyz(LC, cd / ND, kx, ky, kz);
-            cart_xyz(LD, cd % ND, lx, ly, lz);
-            const int ox = (kx * (LD + 1) + lx) * (LCD + 1), oy = NEK + (ky * (LD + 1) + ly) * (LCD + 1),
-                      oz = 2 * NEK + (kz * (LD + 1) + lz) * (LCD + 1);
-            const RStep st = a.rsteps[P];
-            const int base = (st.t * B + st.u) * B + st.v;
+            const int c0w = tab_cd[2 * (c0 + ci)], c1w = tab_cd[2 * (c0 + ci) + 1];
+            const int ox = c0w & 1023, oy = (c0w >> 10) & 1023, oz = c0w >> 20;
+            const int nx = c1w & 15, ny = (c1w >> 4) & 15, nz = c1w >> 8;
+            const int pw = tab_p[P];
+            const int base = pw & 0xffff;
             T acc = T(0);
             for (int g = 0; g < ng; ++g) {
               const T* ek = Ek + g * 3 * NEK;
               const T* rb = boxes + g * BOX + base;
-              for (int sx = 0; sx <= kx + lx; ++sx) {
+              for (int sx = 0; sx <= nx; ++sx) {
                 T accy = T(0);
-                for (int sy = 0; sy <= ky + ly; ++sy) {
+                for (int sy = 0; sy <= ny; ++sy) {
                   const T* r = rb + sx * B * B + sy * B;
                   T accz = T(0);
-                  for (int sz = 0; sz <= kz + lz; ++sz) accz = fma(ek[oz + sz], r[sz], accz);
+                  for (int sz = 0; sz <= nz; ++sz) accz = fma(ek[oz + sz], r[sz], accz);
                   accy = fma(ek[oy + sy], accz, accy);
                 }
                 acc = fma(ek[ox + sx], accy, acc);
               }
             }
-            Ws[ci * HABP + P] += acc;
+            Ws[ci * HABP + (pw >> 16)] += acc;
           }
           __syncwarp();
         }
         // step D: bra transform, items (ab, ci)
         for (int it = lane; it < NAB * nci; it += 32) {
           const int iab = it / nci, ci = it - iab * nci;
-          int ix, iy, iz, jx, jy, jz;
-          cart_xyz(LA, iab / NB, ix, iy, iz);
-          cart_xyz(LB, iab % NB, jx, jy, jz);
-          const T* fx = Eb + 0 * NEB + (ix * (LB + 1) + jx) * (LAB + 1);
-          const T* fy = Eb + 1 * NEB + (iy * (LB + 1) + jy) * (LAB + 1);
-          const T* fz = Eb + 2 * NEB + (iz * (LB + 1) + jz) * (LAB + 1);
+          const int a0w = tab_ab[2 * iab], a1w = tab_ab[2 * iab + 1];
+          const T* fx = Eb + (a0w & 1023);
+          const T* fy = Eb + ((a0w >> 10) & 1023);
+          const T* fz = Eb + (a0w >> 20);
+          const int nx = a1w & 15, ny = (a1w >> 4) & 15, nz = a1w >> 8;
           const T* wc = Ws + ci * HABP;
           T acc = T(0);
-          for (int tx = 0; tx <= ix + jx; ++tx) {
+          for (int tx = 0; tx <= nx; ++tx) {
             T accy = T(0);
-            for (int ty = 0; ty <= iy + jy; ++ty) {
+            for (int ty = 0; ty <= ny; ++ty) {
+              const T* wr = wc + tab_lex[tx * (LAB + 1) + ty];
               T accz = T(0);
-              const int b0 = herm_index(tx, ty, 0);
-              int idx = b0;
-              for (int tz = 0; tz <= iz + jz; ++tz) {
-                accz = fma(fz[tz], wc[idx], accz);
-                // herm_index(tx,ty,tz+1) - herm_index(tx,ty,tz): next group, one further along
-                const int nn = tx + ty + tz + 1, r = ty + tz + 1;
-                idx = nherm(nn - 1) + r * (r + 1) / 2 + tz + 1;
-              }
+              for (int tz = 0; tz <= nz; ++tz) accz = fma(fz[tz], wr[tz], accz);
               accy = fma(fy[ty], accz, accy);
             }
             acc = fma(fx[tx], accy, acc);

@@ -347,11 +347,27 @@ __global__ void k_counts(int npair, const float* __restrict__ Q, const int* __re
   counts[t] = lo;
 }
 
+// cumnp[coff[Y] + k] = primitive pairs of the first k kets of class Y (one thread per class)
+__global__ void k_cumnp(const int* __restrict__ sorted, const int* __restrict__ coff, const int* __restrict__ ccount,
+                        const int* __restrict__ np, int64_t* __restrict__ cumnp) {
+  const int Y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (Y >= NPAIRCLASS) return;
+  int64_t acc = 0;
+  const int* kl = sorted + coff[Y];
+  int64_t* out = cumnp + coff[Y] + Y;  // class Y occupies ccount[Y] + 1 slots
+  for (int k = 0; k < ccount[Y]; ++k) {
+    out[k] = acc;
+    acc += np[kl[k]];
+  }
+  out[ccount[Y]] = acc;
+}
+
 // prefix arrays of the K (canonical) and J (ordered) work lists, one thread per class pair
 __global__ void k_prefix(const int* __restrict__ sorted, const int* __restrict__ coff, const int* __restrict__ ccount,
                          const int* __restrict__ counts, const int64_t* __restrict__ koff, const int64_t* __restrict__ joff,
                          int64_t* __restrict__ kpre, int64_t* __restrict__ jpre, int64_t* __restrict__ ktot,
-                         int64_t* __restrict__ jtot, const int* __restrict__ np, int64_t* __restrict__ kprim) {
+                         int64_t* __restrict__ jtot, const int* __restrict__ np, const int64_t* __restrict__ cumnp,
+                         int64_t* __restrict__ kprim) {
   const int cp = blockIdx.x * blockDim.x + threadIdx.x;
   if (cp >= NPAIRCLASS * NPAIRCLASS) return;
   const int X = cp / NPAIRCLASS, Y = cp % NPAIRCLASS;
@@ -374,9 +390,7 @@ __global__ void k_prefix(const int* __restrict__ sorted, const int* __restrict__
       int c = counts[bl[i] * NPAIRCLASS + Y];
       if (X == Y && c > i + 1) c = i + 1;
       acck += c;
-      int64_t s = 0;
-      for (int k = 0; k < c; ++k) s += np[kl[k]];
-      accp += s * np[bl[i]];
+      accp += cumnp[coff[Y] + Y + c] * np[bl[i]];
     }
     kp[nb] = acck;
     ktot[cp] = acck;
@@ -631,8 +645,9 @@ int eri_plan_impl::build_lists(double th, cudaStream_t s) {
   }
   CK(cudaMemcpyAsync(d_koff, h_koff, sizeof(h_koff), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_joff, h_joff, sizeof(h_joff), cudaMemcpyHostToDevice, s));
+  k_cumnp<<<1, 32, 0, s>>>(d_sorted, d_coff, d_ccount, d_pnp, d_cumnp);
   k_prefix<<<1, 128, 0, s>>>(d_sorted, d_coff, d_ccount, d_counts, d_koff, d_joff, d_kpre, d_jpre, d_ktot, d_jtot,
-                             d_pnp, d_kprim);
+                             d_pnp, d_cumnp, d_kprim);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(h_ktot, d_ktot, sizeof(h_ktot), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h_jtot, d_jtot, sizeof(h_jtot), cudaMemcpyDeviceToHost, s));
@@ -666,7 +681,7 @@ void eri_plan_impl::release() {
                   d_pnp, d_ppoff, d_pao1, d_pao2, d_phoff, d_pcls, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf,
                   d_PBf, d_preff, d_Q, d_qmax, d_sig, d_ccount, d_coff, d_sorted, d_pos, d_counts, d_koff, d_joff,
                   d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Jh, d_Dherm,
-                  d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters};
+                  d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp};
   for (auto& e : prof_events) cudaEventDestroy(e);
   prof_events.clear();
   for (void* p : ptrs)
@@ -835,6 +850,7 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
     CKP(dalloc(&P->d_Q, npair)); CKP(dalloc(&P->d_qmax, 1)); CKP(dalloc(&P->d_sig, npair));
     CKP(dalloc(&P->d_ccount, NPAIRCLASS)); CKP(dalloc(&P->d_coff, NPAIRCLASS)); CKP(dalloc(&P->d_sorted, npair));
     CKP(dalloc(&P->d_pos, npair)); CKP(dalloc(&P->d_counts, (size_t)npair * NPAIRCLASS));
+    CKP(dalloc(&P->d_cumnp, (size_t)npair + NPAIRCLASS));
     CKP(dalloc(&P->d_koff, NPAIRCLASS * NPAIRCLASS)); CKP(dalloc(&P->d_joff, NPAIRCLASS * NPAIRCLASS));
     CKP(dalloc(&P->d_ktot, NPAIRCLASS * NPAIRCLASS)); CKP(dalloc(&P->d_jtot, NPAIRCLASS * NPAIRCLASS));
     CKP(dalloc(&P->d_kprim, NPAIRCLASS * NPAIRCLASS));

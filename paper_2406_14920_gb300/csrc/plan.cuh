@@ -30,6 +30,7 @@ struct eri_plan_impl {
   int64_t *d_koff = nullptr, *d_joff = nullptr, *d_kpre = nullptr, *d_jpre = nullptr, *d_ktot = nullptr,
           *d_jtot = nullptr, *d_kprim = nullptr;
   int64_t kpre_cap = 0, jpre_cap = 0;
+  int64_t* d_cumnp = nullptr;
   int h_ccount[eri::NPAIRCLASS] = {}, h_coff[eri::NPAIRCLASS] = {};
   int64_t h_koff[eri::NPAIRCLASS * eri::NPAIRCLASS] = {}, h_joff[eri::NPAIRCLASS * eri::NPAIRCLASS] = {};
   int64_t h_ktot[eri::NPAIRCLASS * eri::NPAIRCLASS] = {}, h_jtot[eri::NPAIRCLASS * eri::NPAIRCLASS] = {};
