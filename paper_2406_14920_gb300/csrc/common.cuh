@@ -45,6 +45,11 @@ __host__ __device__ constexpr void cart_xyz(int l, int k, int& x, int& y, int& z
   x = l - r;
 }
 
+// position of component (l-y-z, y, z) inside shell l (loop-free)
+__host__ __device__ constexpr int cidx(int l, int y, int z) {
+  return (y + z) * (y + z + 1) / 2 + z + 0 * l;
+}
+
 // Compact Hermite index: triples grouped by n = t+u+v, inside a group ordered
 // by (u+v) then v (same order as Cartesian components).
 __host__ __device__ constexpr int herm_index(int t, int u, int v) {
@@ -247,10 +252,11 @@ __device__ __forceinline__ void md_e_1d(T PA, T PB, T o2p, T* E) {
 
 __device__ __forceinline__ double atomic_add_d(double* p, double v) { return atomicAdd(p, v); }
 
-// R^0_{tuv}, t+u+v <= L, in registers (fully unrolled; all indices are
-// compile-time constants).  Same scaled recursion as r_build_warp, done in
-// place: inside a level, entries are updated from the highest index down so
-// the level m+1 values they read are still intact.
+// R^0_{tuv}, t+u+v <= L, in registers (fully unrolled; every index is an
+// arithmetic expression of unrolled loop counters, so it folds to a constant).
+// Same scaled recursion as r_build_warp, done in place: inside a level the
+// entries are updated from the highest n = t+u+v down, so the level m+1 values
+// they read are still intact.
 template <int L, typename T>
 __device__ __forceinline__ void r_build_reg(const T* F, T pref, T X, T Y, T Z, T c, T* R) {
   const T Xc = c * X, Yc = c * Y, Zc = c * Z;
@@ -258,20 +264,25 @@ __device__ __forceinline__ void r_build_reg(const T* F, T pref, T X, T Y, T Z, T
 #pragma unroll
   for (int m = L - 1; m >= 0; --m) {
 #pragma unroll
-    for (int e = nherm(L - m) - 1; e >= 1; --e) {
-      const int t = herm_t(e), u = herm_u(e), v = herm_v(e);
-      if (t > 0) {
-        T val = Xc * R[herm_index(t - 1, u, v)];
-        if (t > 1) val = fma(c * T(t - 1), R[herm_index(t - 2, u, v)], val);
-        R[e] = val;
-      } else if (u > 0) {
-        T val = Yc * R[herm_index(0, u - 1, v)];
-        if (u > 1) val = fma(c * T(u - 1), R[herm_index(0, u - 2, v)], val);
-        R[e] = val;
-      } else {
-        T val = Zc * R[herm_index(0, 0, v - 1)];
-        if (v > 1) val = fma(c * T(v - 1), R[herm_index(0, 0, v - 2)], val);
-        R[e] = val;
+    for (int n = L - m; n >= 1; --n) {
+#pragma unroll
+      for (int t = n; t >= 0; --t) {
+#pragma unroll
+        for (int u = n - t; u >= 0; --u) {
+          const int v = n - t - u;
+          T val;
+          if (t > 0) {
+            val = Xc * R[herm_index(t - 1, u, v)];
+            if (t > 1) val = fma(c * T(t - 1), R[herm_index(t - 2, u, v)], val);
+          } else if (u > 0) {
+            val = Yc * R[herm_index(0, u - 1, v)];
+            if (u > 1) val = fma(c * T(u - 1), R[herm_index(0, u - 2, v)], val);
+          } else {
+            val = Zc * R[herm_index(0, 0, v - 1)];
+            if (v > 1) val = fma(c * T(v - 1), R[herm_index(0, 0, v - 2)], val);
+          }
+          R[herm_index(t, u, v)] = val;
+        }
       }
     }
     R[0] = pref * F[m];

@@ -22,7 +22,25 @@ struct AShape {
 };
 
 // (ab|cd) for all components of one contracted quartet, summed over primitives:
-//   W_P[cd] = sum_Q E'_Q^{cd} R_{P+Q}  (E' = (-1)^|Q| E),  (ab|cd) += sum_P E_P^{ab} W_P[cd].
+//   W_P[cd] = sum_{ket prims} sum_Q E'_Q^{cd} R_{P+Q}  (E' = (-1)^|Q| E),
+//   (ab|cd) += sum_P E_P^{ab}(bra prim) W_P[cd]  once per bra primitive.
+// E tables: FP64 loads them (memory is free next to the FP64 pipe), FP32
+// rebuilds them from P-A, P-B and 1/(2p) (cheaper than scattered loads).
+template <int LI, int LJ, typename T>
+__device__ __forceinline__ void load_or_build_e(const PairData& pd, int e0, int prim, T* e /*[3][NE]*/) {
+  constexpr int NE = (LI + 1) * (LJ + 1) * (LI + LJ + 1);
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int x = 0; x < 3 * NE; ++x) e[x] = ldE<T>(pd, e0 + x);
+  } else {
+    const T o2p = T(0.5) / pdv<T>(pd.p, pd.pf, prim);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      md_e_1d<LI, LJ, T>(pdv<T>(pd.PA, pd.PAf, d * pd.n + prim), pdv<T>(pd.PB, pd.PBf, d * pd.n + prim), o2p,
+                         e + d * NE);
+  }
+}
+
 template <int LA, int LB, int LC, int LD, typename T>
 __device__ __forceinline__ void eri_block_reg(const KArgs& a, int offb, int npb, int eb0, int offk, int npk, int ek0,
                                               T* X) {
@@ -33,81 +51,96 @@ __device__ __forceinline__ void eri_block_reg(const KArgs& a, int offb, int npb,
   for (int pb = 0; pb < npb; ++pb) {
     Prim<T> bp;
     bp.load(a.pd, offb + pb);
-    T eb[3][S::NEB];
+    T W[S::NCD * S::HAB];
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int x = 0; x < S::NEB; ++x) eb[d][x] = ldE<T>(a.pd, eb0 + (pb * 3 + d) * S::NEB + x);
+    for (int x = 0; x < S::NCD * S::HAB; ++x) W[x] = T(0);
     for (int pk = 0; pk < npk; ++pk) {
       Prim<T> kp;
       kp.load(a.pd, offk + pk);
-      T ek[3][S::NEK];
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int x = 0; x < S::NEK; ++x) {
-          const T v = ldE<T>(a.pd, ek0 + (pk * 3 + d) * S::NEK + x);
-          ek[d][x] = ((x % (LCD + 1)) & 1) ? -v : v;  // (-1)^s folded into the ket
-        }
+      T ek[3 * S::NEK];
+      load_or_build_e<LC, LD, T>(a.pd, ek0 + pk * 3 * S::NEK, offk + pk, ek);
       const T ps = bp.p + kp.p;
       const T rho = bp.p * kp.p / ps;
       const T PQx = bp.P[0] - kp.P[0], PQy = bp.P[1] - kp.P[1], PQz = bp.P[2] - kp.P[2];
       T F[L + 1];
       Boys<T>::template eval<L>(rho * (PQx * PQx + PQy * PQy + PQz * PQz), a.bt, F);
-      const T pref = bp.pref * kp.pref * (T(1) / sqrt(ps));
+      const T pref = bp.pref * kp.pref * rsqrt_t(ps);
       T R[S::NR];
       r_build_reg<L, T>(F, pref, PQx, PQy, PQz, T(-2) * rho, R);
+      // component loops are nested exponent loops (x desc, then y desc, i.e. the
+      // lexicographic component order), so every index is compile-time arithmetic
 #pragma unroll
-      for (int icd = 0; icd < S::NCD; ++icd) {
-        int kx = 0, ky = 0, kz = 0, lx = 0, ly = 0, lz = 0;
-        cart_xyz(LC, icd / S::ND, kx, ky, kz);
-        cart_xyz(LD, icd % S::ND, lx, ly, lz);
-        const T* ex = ek[0] + (kx * (LD + 1) + lx) * (LCD + 1);
-        const T* ey = ek[1] + (ky * (LD + 1) + ly) * (LCD + 1);
-        const T* ez = ek[2] + (kz * (LD + 1) + lz) * (LCD + 1);
-        T W[S::HAB];
+      for (int kx = LC; kx >= 0; --kx)
 #pragma unroll
-        for (int P = 0; P < S::HAB; ++P) {
-          const int t = herm_t(P), u = herm_u(P), v = herm_v(P);
-          T acc = T(0);
+        for (int ky = LC - kx; ky >= 0; --ky)
 #pragma unroll
-          for (int sx = 0; sx <= kx + lx; ++sx) {
-            T accy = T(0);
+          for (int lx = LD; lx >= 0; --lx)
 #pragma unroll
-            for (int sy = 0; sy <= ky + ly; ++sy) {
-              T accz = T(0);
+            for (int ly = LD - lx; ly >= 0; --ly) {
+              const int kz = LC - kx - ky, lz = LD - lx - ly;
+              const int icd = cidx(LC, ky, kz) * S::ND + cidx(LD, ly, lz);
+              const T* ex = ek + 0 * S::NEK + (kx * (LD + 1) + lx) * (LCD + 1);
+              const T* ey = ek + 1 * S::NEK + (ky * (LD + 1) + ly) * (LCD + 1);
+              const T* ez = ek + 2 * S::NEK + (kz * (LD + 1) + lz) * (LCD + 1);
 #pragma unroll
-              for (int sz = 0; sz <= kz + lz; ++sz) accz = fma(ez[sz], R[herm_index(t + sx, u + sy, v + sz)], accz);
-              accy = fma(ey[sy], accz, accy);
+              for (int t = LAB; t >= 0; --t)
+#pragma unroll
+                for (int u = LAB - t; u >= 0; --u)
+#pragma unroll
+                  for (int v = LAB - t - u; v >= 0; --v) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int sx = 0; sx <= kx + lx; ++sx) {
+                      T accy = T(0);
+#pragma unroll
+                      for (int sy = 0; sy <= ky + ly; ++sy) {
+                        T accz = T(0);
+#pragma unroll
+                        for (int sz = 0; sz <= kz + lz; ++sz) {
+                          const T r = R[herm_index(t + sx, u + sy, v + sz)];
+                          accz = (sz & 1) ? fma(-ez[sz], r, accz) : fma(ez[sz], r, accz);  // (-1)^s
+                        }
+                        accy = (sy & 1) ? fma(-ey[sy], accz, accy) : fma(ey[sy], accz, accy);
+                      }
+                      acc = (sx & 1) ? fma(-ex[sx], accy, acc) : fma(ex[sx], accy, acc);
+                    }
+                    W[icd * S::HAB + herm_index(t, u, v)] += acc;
+                  }
             }
-            acc = fma(ex[sx], accy, acc);
-          }
-          W[P] = acc;
-        }
+    }
+    T eb[3 * S::NEB];
+    load_or_build_e<LA, LB, T>(a.pd, eb0 + pb * 3 * S::NEB, offb + pb, eb);
 #pragma unroll
-        for (int iab = 0; iab < S::NAB; ++iab) {
-          int ix = 0, iy = 0, iz = 0, jx = 0, jy = 0, jz = 0;
-          cart_xyz(LA, iab / S::NB, ix, iy, iz);
-          cart_xyz(LB, iab % S::NB, jx, jy, jz);
-          const T* fx = eb[0] + (ix * (LB + 1) + jx) * (LAB + 1);
-          const T* fy = eb[1] + (iy * (LB + 1) + jy) * (LAB + 1);
-          const T* fz = eb[2] + (iz * (LB + 1) + jz) * (LAB + 1);
-          T acc = T(0);
+    for (int icd = 0; icd < S::NCD; ++icd) {
 #pragma unroll
-          for (int tx = 0; tx <= ix + jx; ++tx) {
-            T accy = T(0);
+      for (int ix = LA; ix >= 0; --ix)
 #pragma unroll
-            for (int ty = 0; ty <= iy + jy; ++ty) {
-              T accz = T(0);
+        for (int iy = LA - ix; iy >= 0; --iy)
 #pragma unroll
-              for (int tz = 0; tz <= iz + jz; ++tz) accz = fma(fz[tz], W[herm_index(tx, ty, tz)], accz);
-              accy = fma(fy[ty], accz, accy);
+          for (int jx = LB; jx >= 0; --jx)
+#pragma unroll
+            for (int jy = LB - jx; jy >= 0; --jy) {
+              const int iz = LA - ix - iy, jz = LB - jx - jy;
+              const int iab = cidx(LA, iy, iz) * S::NB + cidx(LB, jy, jz);
+              const T* fx = eb + 0 * S::NEB + (ix * (LB + 1) + jx) * (LAB + 1);
+              const T* fy = eb + 1 * S::NEB + (iy * (LB + 1) + jy) * (LAB + 1);
+              const T* fz = eb + 2 * S::NEB + (iz * (LB + 1) + jz) * (LAB + 1);
+              T acc = T(0);
+#pragma unroll
+              for (int tx = 0; tx <= ix + jx; ++tx) {
+                T accy = T(0);
+#pragma unroll
+                for (int ty = 0; ty <= iy + jy; ++ty) {
+                  T accz = T(0);
+#pragma unroll
+                  for (int tz = 0; tz <= iz + jz; ++tz)
+                    accz = fma(fz[tz], W[icd * S::HAB + herm_index(tx, ty, tz)], accz);
+                  accy = fma(fy[ty], accz, accy);
+                }
+                acc = fma(fx[tx], accy, acc);
+              }
+              X[iab * S::NCD + icd] += acc;
             }
-            acc = fma(fx[tx], accy, acc);
-          }
-          X[iab * S::NCD + icd] += acc;
-        }
-      }
     }
   }
 }
