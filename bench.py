@@ -39,7 +39,11 @@ WORKLOAD_DESC = ("60 atoms in a seeded random packing (min distance 2.0 bohr): 4
                  "4s3p2d1f Cartesian shells, 900 basis functions, s/p 3-primitive contractions, D = C C^T "
                  "with C a random orthonormal 900x120, seed 1001")
 THRESH = 1e-12
-TAU = 1e-5
+# FP32/FP64 tier threshold on the density-weighted Schwarz bound.  The paper's
+# default is 1e-5; 1e-3 keeps the measured energy error near 1e-9 Eh on this
+# workload (1000x inside the 1e-6 Eh budget), and every run
+# reports the measured error against the FP64 path.
+TAU = 1e-3
 # peaks for the ALU roofline: FP32 = 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz;
 # FP64 = GB300 nominal dense FP64 rate
 PEAK_TFLOPS = {0: 1.25, 1: 80.5}
@@ -196,7 +200,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     basis, D = W.workload(WORKLOAD_ID)
     n = basis.nbf
-    plan = eri.Plan(basis, thresh=THRESH, precision=eri.ERI_MIXED, mixed_tau=TAU, device=local_rank, profile=True)
+    plan = eri.Plan(basis, thresh=THRESH, precision=eri.ERI_MIXED, mixed_tau=args.tau, device=local_rank, profile=True)
     stream = torch.cuda.current_stream(dev)
     Dd = torch.from_numpy(D).to(dev)
     J = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -299,7 +303,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed tiers)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "nbf": n, "schwarz_thresh": THRESH, "mixed_tau": TAU,
+        "config": {"workload": WORKLOAD_DESC, "nbf": n, "schwarz_thresh": THRESH, "mixed_tau": args.tau,
                    "quartets_per_step": nq, "fp32_quartets_per_step": nq32,
                    "l2": "flushed before every timed step (256 MiB device write)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
@@ -388,6 +392,7 @@ def main():
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--tau", type=float, default=TAU, help="FP32/FP64 tier threshold of the mixed path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="small case for ncu section captures: the first 20 atoms of the workload, two mixed builds")
@@ -401,7 +406,7 @@ def main():
         import workloads as W
         basis, D = W.workload(WORKLOAD_ID)
         b2, D2 = W.subset_atoms(basis, D, list(range(20)))
-        plan = eri.Plan(b2, thresh=THRESH, precision=eri.ERI_MIXED, mixed_tau=TAU)
+        plan = eri.Plan(b2, thresh=THRESH, precision=eri.ERI_MIXED, mixed_tau=args.tau)
         Dt = torch.from_numpy(D2).cuda()
         for _ in range(2):
             plan.build_jk(Dt)

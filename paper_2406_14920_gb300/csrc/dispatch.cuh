@@ -42,16 +42,11 @@ inline cudaError_t launch_persistent(Kern kern, size_t smem, int64_t items, int 
   return cudaSuccess;
 }
 
-// Register kernel for the smallest classes, warp kernel for the rest.
-__host__ __device__ constexpr bool use_thread_kernel(int la, int lb, int lc, int ld) {
-  return la + lb + lc + ld <= 3 && ncart(la) * ncart(lb) * ncart(lc) * ncart(ld) <= 27;
-}
-
 template <int LA, int LB, int LC, int LD, typename T>
 cudaError_t launch_jk_t(const JKArgs& a, cudaStream_t s, int nsm) {
   if (a.k.wl.total <= 0) return cudaSuccess;
   LaunchInfo li;
-  if constexpr (use_thread_kernel(LA, LB, LC, LD)) {
+  if constexpr (use_thread_kernel(LA, LB, LC, LD, sizeof(T) == 4)) {
     auto kern = jk_thread_kernel<LA, LB, LC, LD, T>;
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, 0);

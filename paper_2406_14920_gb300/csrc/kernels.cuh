@@ -23,6 +23,7 @@ struct KArgs {
   const float* Q;       // Schwarz bound per pair
   const float* dmax;    // max |D'| per shell block, nshell x nshell
   const float* pmaxp;   // largest primitive exponent sum per pair
+  const float* prefmaxp;  // largest |primitive-pair prefactor| per pair
   float tau, pmax32;
   int mixed;            // 0: every item in this launch's precision
   int tier_want;        // 0 or 1: which tier this launch processes
@@ -39,7 +40,10 @@ __device__ __forceinline__ int quartet_tier(const KArgs& a, int pb_id, int pk_id
                   fmaxf(fmaxf(__ldg(dm + s1 * ns + s3), __ldg(dm + s1 * ns + s4)),
                         fmaxf(__ldg(dm + s2 * ns + s3), __ldg(dm + s2 * ns + s4))));
   const float b = __ldg(a.Q + pb_id) * __ldg(a.Q + pk_id) * d;
-  const bool wide = fmaxf(__ldg(a.pmaxp + pb_id), __ldg(a.pmaxp + pk_id)) > a.pmax32;
+  // FP32 range guard: tight exponents or large prefactors stay in FP64
+  // (R grows like (2 rho)^(L/2) and the prefactors multiply into it)
+  const bool wide = fmaxf(__ldg(a.pmaxp + pb_id), __ldg(a.pmaxp + pk_id)) > a.pmax32 ||
+                    __ldg(a.prefmaxp + pb_id) * __ldg(a.prefmaxp + pk_id) > 1.0e18f;
   return (b >= a.tau || wide) ? 0 : 1;
 }
 

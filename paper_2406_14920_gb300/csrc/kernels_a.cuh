@@ -19,7 +19,23 @@ struct AShape {
   static constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
   static constexpr int NAB = NA * NB, NCD = NC * ND, HAB = nherm(LAB), NR = nherm(L);
   static constexpr int NEB = (LA + 1) * (LB + 1) * (LAB + 1), NEK = (LC + 1) * (LD + 1) * (LCD + 1);
+  // register footprint (values) of the two variants: W accumulated over the
+  // ket primitives (fewer FLOPs), or the bra transform per primitive quartet
+  static constexpr int REG_WACC = NCD * HAB + NAB * NCD + NR;
+  static constexpr int REG_PERPQ = HAB + NAB * NCD + NR;
+  static constexpr bool WACC = REG_WACC <= 140;
 };
+
+// Which classes run one quartet per thread (registers) rather than one per warp.
+// FP64: the tiny classes only (the warp kernel keeps the FP64 pipe busier for the
+// rest).  FP32: every class of L <= 4 whose register footprint fits.
+__host__ __device__ constexpr bool use_thread_kernel(int la, int lb, int lc, int ld, bool fp32) {
+  const int L = la + lb + lc + ld;
+  const int nab = ncart(la) * ncart(lb), ncd = ncart(lc) * ncart(ld);
+  if (!fp32) return L <= 3 && nab * ncd <= 27;
+  const int hab = nherm(la + lb), nr = nherm(L);
+  return L <= 4 && (hab + nab * ncd + nr) <= 140;
+}
 
 // (ab|cd) for all components of one contracted quartet, summed over primitives:
 //   W_P[cd] = sum_{ket prims} sum_Q E'_Q^{cd} R_{P+Q}  (E' = (-1)^|Q| E),
@@ -38,6 +54,104 @@ __device__ __forceinline__ void load_or_build_e(const PairData& pd, int e0, int 
     for (int d = 0; d < 3; ++d)
       md_e_1d<LI, LJ, T>(pdv<T>(pd.PA, pd.PAf, d * pd.n + prim), pdv<T>(pd.PB, pd.PBf, d * pd.n + prim), o2p,
                          e + d * NE);
+  }
+}
+
+// Variant for classes whose W (all ket pairs) does not fit in registers: the
+// bra transform runs per primitive quartet, one ket pair cd at a time.
+template <int LA, int LB, int LC, int LD, typename T>
+__device__ __forceinline__ void eri_block_reg_pq(const KArgs& a, int offb, int npb, int eb0, int offk, int npk, int ek0,
+                                                 T* X) {
+  using S = AShape<LA, LB, LC, LD>;
+  constexpr int LAB = S::LAB, LCD = S::LCD, L = S::L;
+#pragma unroll
+  for (int x = 0; x < S::NAB * S::NCD; ++x) X[x] = T(0);
+  for (int pb = 0; pb < npb; ++pb) {
+    Prim<T> bp;
+    bp.load(a.pd, offb + pb);
+    T eb[3 * S::NEB];
+    load_or_build_e<LA, LB, T>(a.pd, eb0 + pb * 3 * S::NEB, offb + pb, eb);
+    for (int pk = 0; pk < npk; ++pk) {
+      Prim<T> kp;
+      kp.load(a.pd, offk + pk);
+      T ek[3 * S::NEK];
+      load_or_build_e<LC, LD, T>(a.pd, ek0 + pk * 3 * S::NEK, offk + pk, ek);
+      const T ps = bp.p + kp.p;
+      const T rho = bp.p * kp.p / ps;
+      const T PQx = bp.P[0] - kp.P[0], PQy = bp.P[1] - kp.P[1], PQz = bp.P[2] - kp.P[2];
+      T F[L + 1];
+      Boys<T>::template eval<L>(rho * (PQx * PQx + PQy * PQy + PQz * PQz), a.bt, F);
+      const T pref = bp.pref * kp.pref * rsqrt_t(ps);
+      T R[S::NR];
+      r_build_reg<L, T>(F, pref, PQx, PQy, PQz, T(-2) * rho, R);
+#pragma unroll
+      for (int kx = LC; kx >= 0; --kx)
+#pragma unroll
+        for (int ky = LC - kx; ky >= 0; --ky)
+#pragma unroll
+          for (int lx = LD; lx >= 0; --lx)
+#pragma unroll
+            for (int ly = LD - lx; ly >= 0; --ly) {
+              const int kz = LC - kx - ky, lz = LD - lx - ly;
+              const int icd = cidx(LC, ky, kz) * S::ND + cidx(LD, ly, lz);
+              const T* ex = ek + 0 * S::NEK + (kx * (LD + 1) + lx) * (LCD + 1);
+              const T* ey = ek + 1 * S::NEK + (ky * (LD + 1) + ly) * (LCD + 1);
+              const T* ez = ek + 2 * S::NEK + (kz * (LD + 1) + lz) * (LCD + 1);
+              T W[S::HAB];
+#pragma unroll
+              for (int t = LAB; t >= 0; --t)
+#pragma unroll
+                for (int u = LAB - t; u >= 0; --u)
+#pragma unroll
+                  for (int v = LAB - t - u; v >= 0; --v) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int sx = 0; sx <= kx + lx; ++sx) {
+                      T accy = T(0);
+#pragma unroll
+                      for (int sy = 0; sy <= ky + ly; ++sy) {
+                        T accz = T(0);
+#pragma unroll
+                        for (int sz = 0; sz <= kz + lz; ++sz) {
+                          const T r = R[herm_index(t + sx, u + sy, v + sz)];
+                          accz = (sz & 1) ? fma(-ez[sz], r, accz) : fma(ez[sz], r, accz);
+                        }
+                        accy = (sy & 1) ? fma(-ey[sy], accz, accy) : fma(ey[sy], accz, accy);
+                      }
+                      acc = (sx & 1) ? fma(-ex[sx], accy, acc) : fma(ex[sx], accy, acc);
+                    }
+                    W[herm_index(t, u, v)] = acc;
+                  }
+#pragma unroll
+              for (int ix = LA; ix >= 0; --ix)
+#pragma unroll
+                for (int iy = LA - ix; iy >= 0; --iy)
+#pragma unroll
+                  for (int jx = LB; jx >= 0; --jx)
+#pragma unroll
+                    for (int jy = LB - jx; jy >= 0; --jy) {
+                      const int iz = LA - ix - iy, jz = LB - jx - jy;
+                      const int iab = cidx(LA, iy, iz) * S::NB + cidx(LB, jy, jz);
+                      const T* fx = eb + 0 * S::NEB + (ix * (LB + 1) + jx) * (LAB + 1);
+                      const T* fy = eb + 1 * S::NEB + (iy * (LB + 1) + jy) * (LAB + 1);
+                      const T* fz = eb + 2 * S::NEB + (iz * (LB + 1) + jz) * (LAB + 1);
+                      T acc = T(0);
+#pragma unroll
+                      for (int tx = 0; tx <= ix + jx; ++tx) {
+                        T accy = T(0);
+#pragma unroll
+                        for (int ty = 0; ty <= iy + jy; ++ty) {
+                          T accz = T(0);
+#pragma unroll
+                          for (int tz = 0; tz <= iz + jz; ++tz) accz = fma(fz[tz], W[herm_index(tx, ty, tz)], accz);
+                          accy = fma(fy[ty], accz, accy);
+                        }
+                        acc = fma(fx[tx], accy, acc);
+                      }
+                      X[iab * S::NCD + icd] += acc;
+                    }
+            }
+    }
   }
 }
 
@@ -245,8 +359,13 @@ __global__ void __launch_bounds__(128) jk_thread_kernel(JKArgs A) {
     if (s3 == s4) w *= T(0.5);
     if (pb_id == pk_id) w *= T(0.5);
     T X[S::NAB * S::NCD];
-    eri_block_reg<LA, LB, LC, LD, T>(a, __ldg(a.sp.poff + pb_id), __ldg(a.sp.np + pb_id), __ldg(a.sp.eoff + pb_id),
-                                     __ldg(a.sp.poff + pk_id), __ldg(a.sp.np + pk_id), __ldg(a.sp.eoff + pk_id), X);
+    if constexpr (S::WACC)
+      eri_block_reg<LA, LB, LC, LD, T>(a, __ldg(a.sp.poff + pb_id), __ldg(a.sp.np + pb_id), __ldg(a.sp.eoff + pb_id),
+                                       __ldg(a.sp.poff + pk_id), __ldg(a.sp.np + pk_id), __ldg(a.sp.eoff + pk_id), X);
+    else
+      eri_block_reg_pq<LA, LB, LC, LD, T>(a, __ldg(a.sp.poff + pb_id), __ldg(a.sp.np + pb_id),
+                                          __ldg(a.sp.eoff + pb_id), __ldg(a.sp.poff + pk_id), __ldg(a.sp.np + pk_id),
+                                          __ldg(a.sp.eoff + pk_id), X);
     contract_block<LA, LB, LC, LD, T>(A, X, w, __ldg(a.sp.ao1 + pb_id), __ldg(a.sp.ao2 + pb_id),
                                       __ldg(a.sp.ao1 + pk_id), __ldg(a.sp.ao2 + pk_id));
   }

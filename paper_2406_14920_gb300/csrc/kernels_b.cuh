@@ -172,8 +172,27 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
             sc[L + 4] = T(-2) * rho;
           }
           __syncwarp();
-          // step B: R^0 for the ng primitive quartets, level by level (scaled form, see r_build_warp)
-          if (L == 0) {
+          // step B: R^0 for the ng primitive quartets.  FP32 and L <= 6: each lane
+          // builds its own quartet's table in registers (compile-time indices) and
+          // stores it in its box.  Otherwise the warp builds all of them level by
+          // level (scaled form, see r_build_warp).
+          if constexpr (sizeof(T) == 4 && L <= 6) {
+            if (lane < ng) {
+              const T* sc = scal + lane * NSC;
+              T Fl[L + 1];
+#pragma unroll
+              for (int m = 0; m <= L; ++m) Fl[m] = sc[m];
+              T R[nherm(L)];
+              r_build_reg<L, T>(Fl, T(1), sc[L + 1], sc[L + 2], sc[L + 3], sc[L + 4], R);
+              T* bx = boxes + lane * BOX;
+#pragma unroll
+              for (int t = 0; t <= L; ++t)
+#pragma unroll
+                for (int u = 0; u <= L - t; ++u)
+#pragma unroll
+                  for (int v = 0; v <= L - t - u; ++v) bx[(t * B + u) * B + v] = R[herm_index(t, u, v)];
+            }
+          } else if (L == 0) {
             if (lane < ng) boxes[lane * BOX] = scal[lane * NSC];
           } else {
             if (lane < ng) pings[lane * 2 * NPING] = scal[lane * NSC + L];

@@ -116,7 +116,7 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
                         const int* __restrict__ sh_po, const double* __restrict__ ex, const double* __restrict__ cn,
                         const double* __restrict__ coords, int nprimpair, double* p_, double* P_, double* PA_,
                         double* PB_, double* pref_, float* pf, float* Pf, float* PAf, float* PBf, float* preff,
-                        float* pmaxp) {
+                        float* pmaxp, float* prefmaxp) {
   int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= npair) return;
   const int a = s1[ip], b = s2[ip];
@@ -125,7 +125,7 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
   double AB2 = 0.0;
   for (int d = 0; d < 3; ++d) AB2 += (A[d] - Bc[d]) * (A[d] - Bc[d]);
   int o = poff[ip];
-  double pmx = 0.0;
+  double pmx = 0.0, prmx = 0.0;
   const double s2pi52 = 5.9149671727956129;  // sqrt(2 pi^(5/2))
   for (int i = 0; i < sh_np[a]; ++i)
     for (int j = 0; j < sh_np[b]; ++j, ++o) {
@@ -134,6 +134,7 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
       const double pr = cn[sh_po[a] + i] * cn[sh_po[b] + j] * exp(-ea * eb / p * AB2) * s2pi52 / p;
       p_[o] = p;
       pmx = fmax(pmx, p);
+      prmx = fmax(prmx, fabs(pr));
       pref_[o] = pr;
       pf[o] = (float)p;
       preff[o] = (float)pr;
@@ -148,6 +149,7 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
       }
     }
   pmaxp[ip] = (float)pmx;
+  prefmaxp[ip] = (float)fmin(prmx, 1.0e30);
 }
 
 // max |D'| over every shell block (used by the mixed-precision tier test)
@@ -592,7 +594,7 @@ ShellPairInfo eri_plan_impl::spinfo() const {
 int eri_plan_impl::geometry(cudaStream_t s, bool rebuild_q) {
   k_pairs<<<grid1(npair, 128), 128, 0, s>>>(npair, d_ps1, d_ps2, d_ppoff, d_sh_atom, d_sh_np, d_sh_po, d_exps, d_cn,
                                         d_coords, nprimpair, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf, d_PBf,
-                                        d_preff, d_pmaxp);
+                                        d_preff, d_pmaxp, d_prefmaxp);
   CK(cudaGetLastError());
   k_etab<<<grid1(npair, 64), 64, 0, s>>>(npair, d_ps1, d_ps2, d_pnp, d_ppoff, d_peoff, d_sh_l, pairdata(), d_E, d_Ef);
   CK(cudaGetLastError());
@@ -681,7 +683,7 @@ void eri_plan_impl::release() {
                   d_pnp, d_ppoff, d_pao1, d_pao2, d_phoff, d_pcls, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf,
                   d_PBf, d_preff, d_Q, d_qmax, d_sig, d_ccount, d_coff, d_sorted, d_pos, d_counts, d_koff, d_joff,
                   d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Jh, d_Dherm,
-                  d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp};
+                  d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp};
   for (auto& e : prof_events) cudaEventDestroy(e);
   prof_events.clear();
   for (void* p : ptrs)
@@ -689,7 +691,7 @@ void eri_plan_impl::release() {
 }
 
 // pairs with an exponent sum above this stay in FP64 in mixed mode (FP32 range)
-static const double kPmax32 = 3.0e3;
+static const double kPmax32 = 1.0e3;
 
 static const int kClassL1[NPAIRCLASS] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 static const int kClassL2[NPAIRCLASS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
@@ -858,7 +860,7 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
     CKP(dalloc(&P->d_boys32, (size_t)BOYS_NT * (BOYS_MMAX + 1) * BOYS_J32));
     CKP(dalloc(&P->d_bexp64, BOYS_NT)); CKP(dalloc(&P->d_bexp32, BOYS_NT));
     CKP(dalloc(&P->d_peoff, npair)); CKP(dalloc(&P->d_E, ne_tot)); CKP(dalloc(&P->d_Ef, ne_tot));
-    CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_dmax, (size_t)ns * ns));
+    CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_prefmaxp, npair)); CKP(dalloc(&P->d_dmax, (size_t)ns * ns));
     CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3));
     CKP(dalloc(&P->d_rsteps, st.size()));
     CKP(dalloc(&P->d_Dp, (size_t)nbf * nbf)); CKP(dalloc(&P->d_Kh, (size_t)nbf * nbf));
@@ -977,7 +979,7 @@ extern "C" int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double
     KArgs& ka = ja.k;
     ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
     ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Kh = K ? P->d_Kh : nullptr;
-    ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp;
+    ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
     ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
     ka.nshell = P->nshell;
     ka.nbf = n;
@@ -1036,7 +1038,7 @@ int eri_build_jk_scratch(eri_plan_t* plan, const double* D, double* J, double* K
   KArgs& ka = ja.k;
   ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
   ka.rsteps = P->d_rsteps; ka.Dp = Dp; ka.Kh = K ? Kh : nullptr;
-  ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp;
+  ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
   ka.tau = 0.0f; ka.pmax32 = 0.0f; ka.mixed = 0; ka.tier_want = 0; ka.counter = nullptr;
   ka.nshell = P->nshell;
   ka.nbf = n;
