@@ -199,3 +199,42 @@ class Plan:
         s = StatsT()
         _check(lib().eri_get_stats(self.h, C.byref(s)), "eri_get_stats")
         return {k: getattr(s, k) for k, _ in StatsT._fields_}
+
+
+def _autograd_function():
+    import torch
+
+    class JKEnergy(torch.autograd.Function):
+        """E = 1/2 tr(D J) - 1/4 tr(D K) (SI Eq. si_E_J_K) as a differentiable function
+        of the nuclear coordinates (natom x 3, float64, CUDA) and the density D.
+
+        forward: moves the plan's atoms (eri_plan_set_coords), builds J and K, and
+        returns E.  backward: dE/dR from eri_jk_grad (derivative ERIs contracted with
+        D, D held fixed) and dE/dD = J - K/2.
+        """
+
+        @staticmethod
+        def forward(ctx, coords, D, plan, freeze_lists=False):
+            plan.set_coords(coords.detach().contiguous(), freeze_lists=freeze_lists)
+            J, K = plan.build_jk(D.detach().contiguous())
+            E = plan.energy(D.detach(), J, K).sum()
+            ctx.save_for_backward(D, J, K)
+            ctx.plan = plan
+            return E
+
+        @staticmethod
+        def backward(ctx, gE):
+            D, J, K = ctx.saved_tensors
+            gR = gD = None
+            if ctx.needs_input_grad[0]:
+                gR = ctx.plan.grad(D.detach().contiguous()) * gE
+            if ctx.needs_input_grad[1]:
+                gD = (J - 0.5 * K) * gE
+            return gR, gD, None, None
+
+    return JKEnergy
+
+
+def jk_energy(coords, D, plan, freeze_lists=False):
+    """Differentiable E_J + E_K; see JKEnergy."""
+    return _autograd_function().apply(coords, D, plan, freeze_lists)

@@ -98,6 +98,7 @@ struct PairData {
   const float* PAf;
   const float* PBf;
   const float* preff;
+  const double* ea;    // exponent of the s1 (higher-l shell) primitive
   const double* E;     // Hermite coefficients per primitive pair: 3 x (l1+1)(l2+1)(l1+l2+1), x then y then z
   const float* Ef;
   int n;               // number of primitive pairs (row stride of the [3][n] arrays)

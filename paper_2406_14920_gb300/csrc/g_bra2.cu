@@ -1,0 +1,7 @@
+// Gradient kernels with bra pair class 2 (all ket classes, FP64).
+#include "dispatch.cuh"
+namespace eri {
+cudaError_t launch_grad_bra2(int Y, const GradArgs& a, cudaStream_t s, int nsm) {
+  return launch_grad_x<2>(Y, a, s, nsm);
+}
+}  // namespace eri

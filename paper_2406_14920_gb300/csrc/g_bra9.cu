@@ -1,0 +1,7 @@
+// Gradient kernels with bra pair class 9 (all ket classes, FP64).
+#include "dispatch.cuh"
+namespace eri {
+cudaError_t launch_grad_bra9(int Y, const GradArgs& a, cudaStream_t s, int nsm) {
+  return launch_grad_x<9>(Y, a, s, nsm);
+}
+}  // namespace eri

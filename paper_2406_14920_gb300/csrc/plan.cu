@@ -116,7 +116,7 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
                         const int* __restrict__ sh_po, const double* __restrict__ ex, const double* __restrict__ cn,
                         const double* __restrict__ coords, int nprimpair, double* p_, double* P_, double* PA_,
                         double* PB_, double* pref_, float* pf, float* Pf, float* PAf, float* PBf, float* preff,
-                        float* pmaxp, float* prefmaxp) {
+                        float* pmaxp, float* prefmaxp, double* ea_) {
   int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= npair) return;
   const int a = s1[ip], b = s2[ip];
@@ -133,6 +133,7 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
       const double p = ea + eb;
       const double pr = cn[sh_po[a] + i] * cn[sh_po[b] + j] * exp(-ea * eb / p * AB2) * s2pi52 / p;
       p_[o] = p;
+      ea_[o] = ea;
       pmx = fmax(pmx, p);
       prmx = fmax(prmx, fabs(pr));
       pref_[o] = pr;
@@ -573,7 +574,7 @@ PairData eri_plan_impl::pairdata() const {
   PairData pd;
   pd.p = d_p; pd.P = d_P; pd.PA = d_PA; pd.PB = d_PB; pd.pref = d_pref;
   pd.pf = d_pf; pd.Pf = d_Pf; pd.PAf = d_PAf; pd.PBf = d_PBf; pd.preff = d_preff;
-  pd.E = d_E; pd.Ef = d_Ef;
+  pd.E = d_E; pd.Ef = d_Ef; pd.ea = d_ea;
   pd.n = nprimpair;
   return pd;
 }
@@ -594,7 +595,7 @@ ShellPairInfo eri_plan_impl::spinfo() const {
 int eri_plan_impl::geometry(cudaStream_t s, bool rebuild_q) {
   k_pairs<<<grid1(npair, 128), 128, 0, s>>>(npair, d_ps1, d_ps2, d_ppoff, d_sh_atom, d_sh_np, d_sh_po, d_exps, d_cn,
                                         d_coords, nprimpair, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf, d_PBf,
-                                        d_preff, d_pmaxp, d_prefmaxp);
+                                        d_preff, d_pmaxp, d_prefmaxp, d_ea);
   CK(cudaGetLastError());
   k_etab<<<grid1(npair, 64), 64, 0, s>>>(npair, d_ps1, d_ps2, d_pnp, d_ppoff, d_peoff, d_sh_l, pairdata(), d_E, d_Ef);
   CK(cudaGetLastError());
@@ -683,7 +684,7 @@ void eri_plan_impl::release() {
                   d_pnp, d_ppoff, d_pao1, d_pao2, d_phoff, d_pcls, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf,
                   d_PBf, d_preff, d_Q, d_qmax, d_sig, d_ccount, d_coff, d_sorted, d_pos, d_counts, d_koff, d_joff,
                   d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Jh, d_Dherm,
-                  d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp};
+                  d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp, d_ea};
   for (auto& e : prof_events) cudaEventDestroy(e);
   prof_events.clear();
   for (void* p : ptrs)
@@ -860,7 +861,7 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
     CKP(dalloc(&P->d_boys32, (size_t)BOYS_NT * (BOYS_MMAX + 1) * BOYS_J32));
     CKP(dalloc(&P->d_bexp64, BOYS_NT)); CKP(dalloc(&P->d_bexp32, BOYS_NT));
     CKP(dalloc(&P->d_peoff, npair)); CKP(dalloc(&P->d_E, ne_tot)); CKP(dalloc(&P->d_Ef, ne_tot));
-    CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_prefmaxp, npair)); CKP(dalloc(&P->d_dmax, (size_t)ns * ns));
+    CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_prefmaxp, npair)); CKP(dalloc(&P->d_ea, nprimpair)); CKP(dalloc(&P->d_dmax, (size_t)ns * ns));
     CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3));
     CKP(dalloc(&P->d_rsteps, st.size()));
     CKP(dalloc(&P->d_Dp, (size_t)nbf * nbf)); CKP(dalloc(&P->d_Kh, (size_t)nbf * nbf));
@@ -1078,10 +1079,46 @@ extern "C" int eri_energy(eri_plan_t* plan, const double* D, const double* J, co
   return ERI_OK;
 }
 
+static cudaError_t launch_grad_class(int X, int Y, const GradArgs& ga, cudaStream_t s, int nsm) {
+  switch (X) {
+    case 0: return launch_grad_bra0(Y, ga, s, nsm);
+    case 1: return launch_grad_bra1(Y, ga, s, nsm);
+    case 2: return launch_grad_bra2(Y, ga, s, nsm);
+    case 3: return launch_grad_bra3(Y, ga, s, nsm);
+    case 4: return launch_grad_bra4(Y, ga, s, nsm);
+    case 5: return launch_grad_bra5(Y, ga, s, nsm);
+    case 6: return launch_grad_bra6(Y, ga, s, nsm);
+    case 7: return launch_grad_bra7(Y, ga, s, nsm);
+    case 8: return launch_grad_bra8(Y, ga, s, nsm);
+    case 9: return launch_grad_bra9(Y, ga, s, nsm);
+  }
+  return cudaErrorInvalidValue;
+}
+
 extern "C" int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int32_t want_j, int32_t want_k,
                            void* stream) {
-  (void)plan; (void)D; (void)dEdR; (void)want_j; (void)want_k; (void)stream;
-  return ERI_EUNSUPPORTED;
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !D || !dEdR) return ERI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(P->device));
+  const int n = P->nbf;
+  const int64_t nn = (int64_t)n * n;
+  k_scale_d<<<grid1(nn, 256), 256, 0, s>>>(n, D, P->d_f, P->d_Dp);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(dEdR, 0, sizeof(double) * 3 * P->natom, s));
+  if (!want_j && !want_k) return ERI_OK;
+  GradArgs ga;
+  ga.pd = P->pairdata(); ga.sp = P->spinfo(); ga.bt = P->boystabs(); ga.rsteps = P->d_rsteps; ga.Dp = P->d_Dp;
+  ga.ea = P->d_ea; ga.sh_atom = P->d_sh_atom; ga.grad = dEdR; ga.nbf = n;
+  ga.cj = want_j ? 1.0 : 0.0;
+  ga.ck = want_k ? 1.0 : 0.0;
+  for (int X = 0; X < NPAIRCLASS; ++X)
+    for (int Y = 0; Y < NPAIRCLASS; ++Y) {
+      ga.wl = P->jlist(X, Y);
+      if (ga.wl.total == 0) continue;
+      CK(launch_grad_class(X, Y, ga, s, P->nsm));
+    }
+  return ERI_OK;
 }
 
 extern "C" int eri_get_lists(eri_plan_t* plan, float* Q, int32_t* sig, int32_t* counts, int32_t* sorted,

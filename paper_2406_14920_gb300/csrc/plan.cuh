@@ -46,6 +46,7 @@ struct eri_plan_impl {
   double *d_Dp = nullptr, *d_Kh = nullptr, *d_Jh = nullptr, *d_Dherm = nullptr, *d_Jherm = nullptr;
   int* d_status = nullptr;
   float *d_pmaxp = nullptr, *d_dmax = nullptr, *d_prefmaxp = nullptr;
+  double* d_ea = nullptr;
   unsigned long long* d_counters = nullptr;  // [X*10+Y][tier][items, prim quartets, bra primitives]
   bool last_mixed = false, last_do_j = false, last_do_k = false;
   // optional per-launch profiling (opts.profile): events recorded around each class launch
