@@ -99,6 +99,31 @@ int eri_default_opts(eri_opts_t* opts);
 int eri_plan(const eri_basis_t* basis, const double* coords, const eri_opts_t* opts, eri_plan_t** out);
 
 /*
+ * One plan over nmol independent molecules (bases[m], coords[m]: host, as for
+ * eri_plan), so that one eri_build_jk / eri_jk_grad covers all of them: each
+ * class launch walks the quartets of every molecule (the paper's batch of many
+ * systems, processed together).  Shell pairs and quartets never mix molecules;
+ * thresholds apply per molecule (Q_max is each molecule's own), so molecule m
+ * gets exactly the lists a single-molecule plan of it would get.
+ * Packed layout of every matrix argument of the other calls (D, J, K): molecule
+ * m's nbf_m x nbf_m row-major block starts at element mat_off[m]
+ * (eri_plan_layout); dEdR and coordinates are natom_m x 3 per molecule, molecule
+ * after molecule (atom_off).  eri_energy writes 2 doubles per molecule.
+ * nmol in 1..65535; eri_plan(b, c, o, out) equals eri_plan_batch(1, &b, &c, o, out).
+ * Errors as for eri_plan.
+ */
+int eri_plan_batch(int32_t nmol, const eri_basis_t* const* bases, const double* const* coords,
+                   const eri_opts_t* opts, eri_plan_t** out);
+
+/*
+ * Layout of a plan's packed matrices (host outputs, each may be NULL):
+ *   *nmol; mat_off int64 [nmol+1] (element offsets, mat_off[nmol] = total);
+ *   nbf int32 [nmol]; atom_off int32 [nmol+1] (first atom of each molecule).
+ * Call once with only nmol to size the arrays.
+ */
+int eri_plan_layout(eri_plan_t* plan, int32_t* nmol, int64_t* mat_off, int32_t* nbf, int32_t* atom_off);
+
+/*
  * Move the atoms: coords_dev is a DEVICE pointer to natom*3 doubles.  Pair
  * data, Schwarz bounds and lists are rebuilt on `stream`, then the call waits
  * for the new list sizes (a device->host copy).  Use for finite differences
@@ -110,17 +135,58 @@ int eri_plan_set_coords(eri_plan_t* plan, const double* coords_dev, int32_t free
 /*
  * J_mn = sum_ls (mn|ls) D_ls and K_ml = sum_ns (mn|ls) D_ns over the quartets
  * whose Schwarz bound Q_ab Q_cd >= thresh (Eq. j_definition, Eq. k_definition,
- * Eq. kernel_upperbound).  D, J, K: device, nbf*nbf.  J or K may be NULL to
+ * Eq. kernel_upperbound).  D, J, K: device, nbf*nbf (packed per molecule for
+ * a batched plan).  D must be symmetric.  J or K may be NULL to
  * skip that matrix (J alone runs only the J-engine).  thresh < 0 keeps the
  * plan's threshold; another value rebuilds the lists first (with a host wait).
  * precision: ERI_FP64 or ERI_MIXED (tier split at the plan's mixed_tau).
+ * With thresh < 0 and opts.profile = 0 the call only enqueues work on
+ * `stream` (no host wait, no allocation), so it may be captured into a CUDA graph.
  */
 int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double* K, double thresh, int32_t precision,
                  void* stream);
 
 /*
+ * The same build as eri_build_jk(plan, D, J, K, -1, precision, stream), run as
+ * one CUDA graph: the first call for a given (D, J, K, precision) captures the
+ * whole build (density scaling, every class launch of every molecule, the
+ * symmetrisation) on a stream of the plan and instantiates it; later calls with
+ * the same pointers replay it with one cudaGraphLaunch on `stream` (the contents
+ * of D may change between calls).  Inside the graph the class launches fork onto
+ * four branches, longest first, so independent classes overlap.  New pointers or
+ * precision re-capture (the old graph is released after a wait on `stream`);
+ * a list rebuild (another threshold, new coordinates without frozen lists)
+ * drops the graph.  Profiling (opts.profile) does not apply to graph builds.
+ * Errors: as eri_build_jk; a failed capture returns ERI_ECUDA and leaves no graph.
+ */
+int eri_build_jk_graph(eri_plan_t* plan, const double* D, double* J, double* K, int32_t precision, void* stream);
+
+/*
+ * Autotuner for the work-tile length (consecutive shell quartets a warp, or for
+ * the thread kernel each lane, takes before moving on; the walk steps a cursor
+ * through the bra prefix array instead of searching it per quartet).  For every
+ * (bra class, ket class, tier) launch of this plan and density, candidate
+ * lengths (1, 2, 4, 8, and 16 for warp kernels) are timed with CUDA events on
+ * three windows of the launch's own list, each window sized so the current
+ * length takes about trial_ms, and the fastest (by more than 3 %) is kept in
+ * the plan.  Synchronises `stream` repeatedly; writes only plan scratch; J and
+ * K are unchanged.  Later builds (and graphs captured after it) use the tiles.
+ * Errors: ERI_EINVAL (trial_ms <= 0, NULL, bad precision), ERI_ECUDA.
+ */
+int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision, double trial_ms, void* stream);
+
+/*
+ * Read or set the plan's tile table (host int32 [10][10][2] indexed
+ * [bra class][ket class][tier], entries with ket class > bra class unused;
+ * 0 in eri_set_tiles = built-in default, valid values 0..1024).  Use them to
+ * cache autotuner results across runs.
+ */
+int eri_get_tiles(eri_plan_t* plan, int32_t* tiles);
+int eri_set_tiles(eri_plan_t* plan, const int32_t* tiles);
+
+/*
  * E_J = 1/2 sum D_mn J_mn and E_K = -1/4 sum D_mn K_mn (SI Eq. si_E_J_K):
- * E_out is a DEVICE pointer to 2 doubles {E_J, E_K}.  J or K may be NULL
+ * E_out is a DEVICE pointer to 2 doubles {E_J, E_K} per molecule.  J or K may be NULL
  * (its energy is written as 0).
  */
 int eri_energy(eri_plan_t* plan, const double* D, const double* J, const double* K, double* E_out, void* stream);
@@ -137,10 +203,12 @@ int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int32_t want_j,
 /*
  * Copy the plan's lists to HOST buffers for inspection (each may be NULL):
  *   Q      float32 [npair]        Schwarz bound per shell pair, pair index a(a+1)/2+b (a >= b)
+ *                                 (batched: molecule after molecule, local shell indices)
  *   sig    int32   [npair]        1 iff Q * Qmax >= thresh
  *   counts int32   [npair * 10]   kets of each pair class significant with the pair
  *   sorted int32   [npair]        significant pair indices, class by class (ss ps pp ds dp dd fs fp fd ff),
- *                                 each class by Q descending then pair index ascending
+ *                                 inside a class molecule by molecule, each by Q descending then
+ *                                 pair index ascending
  *   class_count int32 [10]        length of each class in `sorted`
  * Synchronises the device.
  */
@@ -177,7 +245,7 @@ int eri_get_stats(eri_plan_t* plan, eri_stats_t* stats);
  * call.  Its scratch (scaled density and half-J / half-K accumulators) is one
  * fixed device array inside the library, sized for at most
  * ERI_NOALLOC_MAX_NBF basis functions; a plan with more gets ERI_EUNSUPPORTED
- * and a message on stderr.  The call allocates nothing: no cudaMalloc, no
+ * and a message on stderr, and so does a batched plan.  The call allocates nothing: no cudaMalloc, no
  * cudaFree, no allocating library routine.
  *   - The first call on a device looks up the array's device address on that
  *     device (cudaGetSymbolAddress); make that first call before any stream

@@ -63,8 +63,16 @@ def lib():
         vp, d, i32 = C.c_void_p, C.POINTER(C.c_double), C.c_int32
         L.eri_default_opts.argtypes = [C.POINTER(OptsT)]
         L.eri_plan.argtypes = [C.POINTER(BasisT), d, C.POINTER(OptsT), C.POINTER(vp)]
+        L.eri_plan_batch.argtypes = [i32, C.POINTER(C.POINTER(BasisT)), C.POINTER(d), C.POINTER(OptsT),
+                                     C.POINTER(vp)]
+        L.eri_plan_layout.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_int32)]
         L.eri_plan_set_coords.argtypes = [vp, vp, i32, vp]
         L.eri_build_jk.argtypes = [vp, vp, vp, vp, C.c_double, i32, vp]
+        L.eri_build_jk_graph.argtypes = [vp, vp, vp, vp, i32, vp]
+        L.eri_autotune.argtypes = [vp, vp, i32, C.c_double, vp]
+        L.eri_get_tiles.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.eri_set_tiles.argtypes = [vp, C.POINTER(C.c_int32)]
         L.eri_energy.argtypes = [vp, vp, vp, vp, vp, vp]
         L.eri_jk_grad.argtypes = [vp, vp, vp, i32, i32, vp]
         L.eri_get_lists.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -98,28 +106,47 @@ def _stream_ptr(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+def _basis_t(basis):
+    """eri_basis_t for one basis (returns the struct and the arrays it points into)."""
+    shells = (ShellT * basis.nshell)()
+    for s in range(basis.nshell):
+        shells[s].atom = int(basis.shell_atom[s])
+        shells[s].l = int(basis.shell_l[s])
+        shells[s].nprim = int(basis.shell_nprim[s])
+        shells[s].prim_offset = int(basis.shell_prim_offset[s])
+    exps = np.ascontiguousarray(basis.exps, np.float64)
+    coefs = np.ascontiguousarray(basis.coefs, np.float64)
+    b = BasisT(basis.nshell, basis.natom, shells, exps.ctypes.data_as(C.POINTER(C.c_double)),
+               coefs.ctypes.data_as(C.POINTER(C.c_double)))
+    return b, (shells, exps, coefs)
+
+
 class Plan:
-    """An eri_plan over one basis and geometry (see include/eri.h)."""
+    """An eri_plan over one basis and geometry, or (a list of bases) an
+    eri_plan_batch over several independent molecules (see include/eri.h).
+
+    Batched plans take and return packed matrices: a 1-D float64 tensor with
+    molecule m's nbf_m x nbf_m block at ``mat_off[m]`` (``pack`` / ``unpack``).
+    """
 
     def __init__(self, basis, coords=None, thresh=1e-12, precision=ERI_FP64, mixed_tau=1e-5, device=None,
                  j_engine=True, profile=False):
         L = lib()
+        self.batched = isinstance(basis, (list, tuple))
+        bases = list(basis) if self.batched else [basis]
+        if coords is None:
+            coords = [b.coords for b in bases]
+        elif not self.batched:
+            coords = [coords]
         self.basis = basis
-        self.nbf = basis.nbf
-        self.natom = basis.natom
-        self.npair = basis.nshell * (basis.nshell + 1) // 2
-        shells = (ShellT * basis.nshell)()
-        for s in range(basis.nshell):
-            shells[s].atom = int(basis.shell_atom[s])
-            shells[s].l = int(basis.shell_l[s])
-            shells[s].nprim = int(basis.shell_nprim[s])
-            shells[s].prim_offset = int(basis.shell_prim_offset[s])
-        self._exps = np.ascontiguousarray(basis.exps, np.float64)
-        self._coefs = np.ascontiguousarray(basis.coefs, np.float64)
-        b = BasisT(basis.nshell, basis.natom, shells, self._exps.ctypes.data_as(C.POINTER(C.c_double)),
-                   self._coefs.ctypes.data_as(C.POINTER(C.c_double)))
-        self._shells = shells
-        crd = np.ascontiguousarray(basis.coords if coords is None else coords, np.float64)
+        keep = []
+        bts = (BasisT * len(bases))()
+        for m, bs in enumerate(bases):
+            bt, arrs = _basis_t(bs)
+            bts[m] = bt
+            keep.append(arrs)
+        crds = [np.ascontiguousarray(c, np.float64).reshape(-1) for c in coords]
+        self._keep = (keep, crds)
         o = OptsT()
         L.eri_default_opts(C.byref(o))
         o.thresh = float(thresh)
@@ -129,9 +156,42 @@ class Plan:
         o.j_engine = int(bool(j_engine))
         o.profile = int(bool(profile))
         h = C.c_void_p()
-        _check(L.eri_plan(C.byref(b), crd.ctypes.data_as(C.POINTER(C.c_double)), C.byref(o), C.byref(h)), "eri_plan")
+        if self.batched:
+            bp = (C.POINTER(BasisT) * len(bases))(*[C.pointer(bts[m]) for m in range(len(bases))])
+            cp = (C.POINTER(C.c_double) * len(bases))(*[c.ctypes.data_as(C.POINTER(C.c_double)) for c in crds])
+            _check(L.eri_plan_batch(len(bases), bp, cp, C.byref(o), C.byref(h)), "eri_plan_batch")
+        else:
+            _check(L.eri_plan(C.byref(bts[0]), crds[0].ctypes.data_as(C.POINTER(C.c_double)), C.byref(o),
+                              C.byref(h)), "eri_plan")
         self.h = h
         self.precision = int(precision)
+        nm = C.c_int32()
+        _check(L.eri_plan_layout(h, C.byref(nm), None, None, None), "eri_plan_layout")
+        self.nmol = nm.value
+        self.mat_off = np.zeros(self.nmol + 1, np.int64)
+        self.mat_n = np.zeros(self.nmol, np.int32)
+        self.atom_off = np.zeros(self.nmol + 1, np.int32)
+        _check(L.eri_plan_layout(h, None, self.mat_off.ctypes.data_as(C.POINTER(C.c_int64)),
+                                 self.mat_n.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 self.atom_off.ctypes.data_as(C.POINTER(C.c_int32))), "eri_plan_layout")
+        self.nbf = int(self.mat_n.sum())
+        self.nmat = int(self.mat_off[-1])
+        self.natom = int(self.atom_off[-1])
+        self.npair = sum(b.nshell * (b.nshell + 1) // 2 for b in bases)
+
+    def _mat_shape(self):
+        return (self.nmat,) if self.batched else (self.nbf, self.nbf)
+
+    def pack(self, mats):
+        """Packed 1-D tensor from a list of per-molecule nbf_m x nbf_m tensors."""
+        import torch
+        return torch.cat([m.reshape(-1) for m in mats]).contiguous()
+
+    def unpack(self, packed):
+        """Per-molecule nbf_m x nbf_m views of a packed tensor."""
+        v = packed.reshape(-1)
+        return [v[int(self.mat_off[m]):int(self.mat_off[m + 1])].view(int(self.mat_n[m]), int(self.mat_n[m]))
+                for m in range(self.nmol)]
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:
@@ -147,20 +207,63 @@ class Plan:
     def build_jk(self, D, J=None, K=None, want_j=True, want_k=True, thresh=-1.0, precision=None, stream=None):
         """J, K (torch float64 CUDA tensors, nbf x nbf) for the density D."""
         import torch
-        n = self.nbf
+        shp = self._mat_shape()
         if want_j and J is None:
-            J = torch.empty((n, n), dtype=torch.float64, device=D.device)
+            J = torch.empty(shp, dtype=torch.float64, device=D.device)
         if want_k and K is None:
-            K = torch.empty((n, n), dtype=torch.float64, device=D.device)
+            K = torch.empty(shp, dtype=torch.float64, device=D.device)
         prec = self.precision if precision is None else int(precision)
         _check(lib().eri_build_jk(self.h, _ptr(D), _ptr(J if want_j else None), _ptr(K if want_k else None),
                                   float(thresh), prec, _stream_ptr(stream)), "eri_build_jk")
         return (J if want_j else None), (K if want_k else None)
 
+    def build_jk_graph(self, D, J, K, precision=None, stream=None):
+        """As build_jk into preallocated J / K (either may be None), replayed
+        from a CUDA graph captured on the first call with these tensors."""
+        prec = self.precision if precision is None else int(precision)
+        _check(lib().eri_build_jk_graph(self.h, _ptr(D), _ptr(J), _ptr(K), prec, _stream_ptr(stream)),
+               "eri_build_jk_graph")
+        return J, K
+
+    def autotune(self, D, precision=None, trial_ms=5.0, cache=None, stream=None):
+        """Pick work-tile lengths per class launch (eri_autotune).  With `cache`
+        (a JSON path), a table stored there for this device and plan shape is
+        loaded instead of tuning, and a fresh result is stored."""
+        import json
+        import torch
+        prec = self.precision if precision is None else int(precision)
+        dev = torch.cuda.get_device_name(D.device)
+        key = f"{dev}|prec{prec}|nbf{self.nbf}|nmol{self.nmol}"
+        db = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                db = json.load(f)
+            if key in db:
+                self.set_tiles(np.asarray(db[key], np.int32))
+                return self.tiles()
+        _check(lib().eri_autotune(self.h, _ptr(D), prec, float(trial_ms), _stream_ptr(stream)), "eri_autotune")
+        t = self.tiles()
+        if cache:
+            db[key] = t.reshape(-1).tolist()
+            tmp = f"{cache}.tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(db, f)
+            os.replace(tmp, cache)
+        return t
+
+    def tiles(self):
+        t = np.zeros(200, np.int32)
+        _check(lib().eri_get_tiles(self.h, t.ctypes.data_as(C.POINTER(C.c_int32))), "eri_get_tiles")
+        return t.reshape(10, 10, 2)
+
+    def set_tiles(self, tiles):
+        t = np.ascontiguousarray(np.asarray(tiles, np.int32).reshape(-1))
+        _check(lib().eri_set_tiles(self.h, t.ctypes.data_as(C.POINTER(C.c_int32))), "eri_set_tiles")
+
     def energy(self, D, J, K, out=None, stream=None):
         import torch
         if out is None:
-            out = torch.empty(2, dtype=torch.float64, device=D.device)
+            out = torch.empty(2 * self.nmol if self.batched else 2, dtype=torch.float64, device=D.device)
         _check(lib().eri_energy(self.h, _ptr(D), _ptr(J), _ptr(K), _ptr(out), _stream_ptr(stream)), "eri_energy")
         return out
 

@@ -113,15 +113,23 @@ struct ShellPairInfo {
   const int32_t* ao2;      // AO offset of s2
   const int32_t* hoff;     // offset of the Hermite density / Hermite J of the first primitive pair
   const int32_t* eoff;     // offset of the E tables of the first primitive pair
+  // molecules (a plan may hold several independent molecules): pairs never
+  // cross molecules, and D, J, K are packed one nbf_m x nbf_m block per molecule
+  const int32_t* pmol;     // molecule of each pair
+  const int64_t* mat_off;  // offset of each molecule's block in packed D / J / K
+  const int32_t* mat_n;    // nbf of each molecule (row stride of its block)
 };
 
 // Per (bra class, ket class) work description, all device pointers.
 struct WorkList {
   const int32_t* bra;      // sorted pair ids of the bra class
-  const int32_t* ket;      // sorted pair ids of the ket class
+  const int32_t* ket;      // sorted pair ids of the ket class (molecule by molecule)
+  const int32_t* kseg;     // start of each molecule's segment in `ket`, stride NPAIRCLASS
   const int64_t* prefix;   // [nbra+1] inclusive prefix of kets per bra position
   int nbra;
   int64_t total;
+  int64_t first;           // items [first, total) are processed (0 except in tuning trials)
+  int tile;                // consecutive items per worker tile (warp kernels: per warp; thread kernel: per lane)
 };
 
 // Boys F_0..F_M at T.  Below BOYS_TMAX: Taylor expansion of F_M around the

@@ -15,30 +15,37 @@ struct KArgs {
   WorkList wl;
   BoysTabs bt;
   const RStep* rsteps;
-  const double* Dp;   // density with component norms folded in, nbf x nbf
-  double* Kh;         // half-K accumulator, nbf x nbf
+  const double* Dp;   // density with component norms folded in (packed per molecule)
+  double* Kh;         // half-K accumulator (packed per molecule)
   // precision tiers (mixed mode): a quartet is FP64 (tier 0) when
   // Q_ab Q_cd max|D'| >= tau over the six D blocks it touches, or when one of
   // its pairs has an exponent sum above pmax32; otherwise FP32 (tier 1).
   const float* Q;       // Schwarz bound per pair
-  const float* dmax;    // max |D'| per shell block, nshell x nshell
+  const float* dmax;    // max |D'| over the two D blocks of each shell pair (pair index)
   const float* pmaxp;   // largest primitive exponent sum per pair
   const float* prefmaxp;  // largest |primitive-pair prefactor| per pair
+  const int* shloc;     // shell index inside its molecule, per (global) shell
+  const int* pbase;     // first pair index of each molecule
   float tau, pmax32;
   int mixed;            // 0: every item in this launch's precision
   int tier_want;        // 0 or 1: which tier this launch processes
   unsigned long long* counter;  // items processed by this launch's tier (may be null)
-  int nshell;
-  int nbf;
   int same_class;
 };
 
-__device__ __forceinline__ int quartet_tier(const KArgs& a, int pb_id, int pk_id, int s1, int s2, int s3, int s4) {
+// pair index of shells x, y of molecule `mol` (pairs are stored a >= b, a(a+1)/2 + b)
+__device__ __forceinline__ int pair_index(const KArgs& a, int mol, int x, int y) {
+  const int lx = __ldg(a.shloc + x), ly = __ldg(a.shloc + y);
+  const int hi = lx > ly ? lx : ly, lo = lx > ly ? ly : lx;
+  return __ldg(a.pbase + mol) + hi * (hi + 1) / 2 + lo;
+}
+
+__device__ __forceinline__ int quartet_tier(const KArgs& a, int mol, int pb_id, int pk_id, int s1, int s2, int s3,
+                                            int s4) {
   const float* dm = a.dmax;
-  const int ns = a.nshell;
-  float d = fmaxf(fmaxf(__ldg(dm + s1 * ns + s2), __ldg(dm + s3 * ns + s4)),
-                  fmaxf(fmaxf(__ldg(dm + s1 * ns + s3), __ldg(dm + s1 * ns + s4)),
-                        fmaxf(__ldg(dm + s2 * ns + s3), __ldg(dm + s2 * ns + s4))));
+  float d = fmaxf(fmaxf(__ldg(dm + pb_id), __ldg(dm + pk_id)),
+                  fmaxf(fmaxf(__ldg(dm + pair_index(a, mol, s1, s3)), __ldg(dm + pair_index(a, mol, s1, s4))),
+                        fmaxf(__ldg(dm + pair_index(a, mol, s2, s3)), __ldg(dm + pair_index(a, mol, s2, s4)))));
   const float b = __ldg(a.Q + pb_id) * __ldg(a.Q + pk_id) * d;
   // FP32 range guard: tight exponents or large prefactors stay in FP64
   // (R grows like (2 rho)^(L/2) and the prefactors multiply into it)
@@ -65,6 +72,28 @@ __device__ __forceinline__ int find_bra(const int64_t* __restrict__ prefix, int 
   }
   return lo;
 }
+
+// Position in a work list: bra ib covers items [bs, be).  Workers take tiles of
+// consecutive items and step through them, moving the cursor forward over the
+// prefix array instead of searching it again for every item.
+struct BraCursor {
+  int ib;
+  int64_t bs, be;
+  __device__ __forceinline__ BraCursor(const WorkList& wl, int64_t item) {
+    ib = find_bra(wl.prefix, wl.nbra, item);
+    bs = __ldg(wl.prefix + ib);
+    be = __ldg(wl.prefix + ib + 1);
+  }
+  // ket index of `item` (item >= every item seen before, < wl.total)
+  __device__ __forceinline__ int at(const WorkList& wl, int64_t item) {
+    while (item >= be) {
+      ++ib;
+      bs = be;
+      be = __ldg(wl.prefix + ib + 1);
+    }
+    return (int)(item - bs);
+  }
+};
 
 template <typename T> __device__ __forceinline__ T ldT(const double* p) { return (T)__ldg(p); }
 
@@ -169,10 +198,16 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
   }
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t total = a.wl.total;
-  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; item < total; item += nwarps) {
-    const int ib = find_bra(a.wl.prefix, a.wl.nbra, item);
-    const int ik = (int)(item - __ldg(a.wl.prefix + ib));
-    const int pb_id = __ldg(a.wl.bra + ib), pk_id = __ldg(a.wl.ket + ik);
+  const int64_t tile = a.wl.tile, ntiles = (total - a.wl.first + tile - 1) / tile;
+  for (int64_t tl = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; tl < ntiles; tl += nwarps) {
+  const int64_t i0 = a.wl.first + tl * tile, i1 = i0 + tile < total ? i0 + tile : total;
+  BraCursor cur(a.wl, i0);
+  for (int64_t item = i0; item < i1; ++item) {
+    const int ik = cur.at(a.wl, item);
+    const int ib = cur.ib;
+    const int pb_id = __ldg(a.wl.bra + ib);
+    const int mol = __ldg(a.sp.pmol + pb_id);
+    const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
     const int npb = __ldg(a.sp.np + pb_id), offb = __ldg(a.sp.poff + pb_id);
     const int npk = __ldg(a.sp.np + pk_id), offk = __ldg(a.sp.poff + pk_id);
     const int hb = __ldg(a.sp.hoff + pb_id), hk = __ldg(a.sp.hoff + pk_id);
@@ -217,6 +252,7 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
         if (P < HAB) atomic_add_d(a.Jherm + hb + (size_t)pb * HAB + P, (double)acc[j]);
       }
     }
+  }
   }
 }
 

@@ -263,11 +263,13 @@ __device__ __forceinline__ void eri_block_reg(const KArgs& a, int offb, int npb,
 // (Eq. j_definition, Eq. k_definition with the canonical-quartet weights; the
 // transposes are added by the post kernels).
 template <int LA, int LB, int LC, int LD, typename T>
-__device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w, int ao1, int ao2, int ao3, int ao4) {
+__device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w, int ao1, int ao2, int ao3, int ao4,
+                                               int64_t base, int n) {
   using S = AShape<LA, LB, LC, LD>;
-  const int n = A.k.nbf;
-  const double* Dp = A.k.Dp;
-  if (A.k.Kh) {
+  const double* Dp = A.k.Dp + base;
+  double* Kh = A.k.Kh ? A.k.Kh + base : nullptr;
+  double* Jh = A.Jh ? A.Jh + base : nullptr;
+  if (Kh) {
 #pragma unroll
     for (int ia = 0; ia < S::NA; ++ia) {
 #pragma unroll
@@ -278,7 +280,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
           for (int id = 0; id < S::ND; ++id)
             s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], ldT<T>(Dp + (size_t)(ao2 + ib) * n + ao4 + id), s);
-        atomic_add_d(A.k.Kh + (size_t)(ao1 + ia) * n + ao3 + ic, (double)(w * s));
+        atomic_add_d(Kh + (size_t)(ao1 + ia) * n + ao3 + ic, (double)(w * s));
       }
 #pragma unroll
       for (int id = 0; id < S::ND; ++id) {  // Kh_ad += w (ab|cd) D_bc
@@ -288,7 +290,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
           for (int ic = 0; ic < S::NC; ++ic)
             s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], ldT<T>(Dp + (size_t)(ao2 + ib) * n + ao3 + ic), s);
-        atomic_add_d(A.k.Kh + (size_t)(ao1 + ia) * n + ao4 + id, (double)(w * s));
+        atomic_add_d(Kh + (size_t)(ao1 + ia) * n + ao4 + id, (double)(w * s));
       }
     }
 #pragma unroll
@@ -301,7 +303,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
           for (int id = 0; id < S::ND; ++id)
             s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], ldT<T>(Dp + (size_t)(ao1 + ia) * n + ao4 + id), s);
-        atomic_add_d(A.k.Kh + (size_t)(ao2 + ib) * n + ao3 + ic, (double)(w * s));
+        atomic_add_d(Kh + (size_t)(ao2 + ib) * n + ao3 + ic, (double)(w * s));
       }
 #pragma unroll
       for (int id = 0; id < S::ND; ++id) {  // Kh_bd += w (ab|cd) D_ac
@@ -311,11 +313,11 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
           for (int ic = 0; ic < S::NC; ++ic)
             s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], ldT<T>(Dp + (size_t)(ao1 + ia) * n + ao3 + ic), s);
-        atomic_add_d(A.k.Kh + (size_t)(ao2 + ib) * n + ao4 + id, (double)(w * s));
+        atomic_add_d(Kh + (size_t)(ao2 + ib) * n + ao4 + id, (double)(w * s));
       }
     }
   }
-  if (A.Jh) {
+  if (Jh) {
     const T w2 = T(2) * w;
 #pragma unroll
     for (int iab = 0; iab < S::NAB; ++iab) {  // Jh_ab += 2w (ab|cd) D_cd
@@ -323,7 +325,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
       for (int icd = 0; icd < S::NCD; ++icd)
         s = fma(X[iab * S::NCD + icd], ldT<T>(Dp + (size_t)(ao3 + icd / S::ND) * n + ao4 + icd % S::ND), s);
-      atomic_add_d(A.Jh + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB, (double)(w2 * s));
+      atomic_add_d(Jh + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB, (double)(w2 * s));
     }
 #pragma unroll
     for (int icd = 0; icd < S::NCD; ++icd) {  // Jh_cd += 2w (ab|cd) D_ab
@@ -331,7 +333,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
       for (int iab = 0; iab < S::NAB; ++iab)
         s = fma(X[iab * S::NCD + icd], ldT<T>(Dp + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB), s);
-      atomic_add_d(A.Jh + (size_t)(ao3 + icd / S::ND) * n + ao4 + icd % S::ND, (double)(w2 * s));
+      atomic_add_d(Jh + (size_t)(ao3 + icd / S::ND) * n + ao4 + icd % S::ND, (double)(w2 * s));
     }
   }
 }
@@ -343,13 +345,24 @@ __global__ void __launch_bounds__(128) jk_thread_kernel(JKArgs A) {
   const int64_t total = a.wl.total;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long done = 0, doneq = 0, doneb = 0;
-  for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
-    const int ib = find_bra(a.wl.prefix, a.wl.nbra, item);
-    const int ik = (int)(item - __ldg(a.wl.prefix + ib));
-    const int pb_id = __ldg(a.wl.bra + ib), pk_id = __ldg(a.wl.ket + ik);
+  // a warp shares a tile of 32 * tile consecutive items, lane l takes items l, l + 32, ...
+  const int64_t span = 32 * (int64_t)a.wl.tile, ntiles = (total - a.wl.first + span - 1) / span;
+  const int lane = threadIdx.x & 31;
+  for (int64_t tl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tl < ntiles;
+       tl += stride >> 5) {
+  const int64_t i0 = a.wl.first + tl * span + lane, i1 = a.wl.first + tl * span + span < total
+                                                           ? a.wl.first + tl * span + span : total;
+  if (i0 >= i1) continue;
+  BraCursor cur(a.wl, i0);
+  for (int64_t item = i0; item < i1; item += 32) {
+    const int ik = cur.at(a.wl, item);
+    const int ib = cur.ib;
+    const int pb_id = __ldg(a.wl.bra + ib);
+    const int mol = __ldg(a.sp.pmol + pb_id);
+    const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
     const int s1 = __ldg(a.sp.s1 + pb_id), s2 = __ldg(a.sp.s2 + pb_id);
     const int s3 = __ldg(a.sp.s1 + pk_id), s4 = __ldg(a.sp.s2 + pk_id);
-    if (a.mixed && quartet_tier(a, pb_id, pk_id, s1, s2, s3, s4) != a.tier_want) continue;
+    if (a.mixed && quartet_tier(a, mol, pb_id, pk_id, s1, s2, s3, s4) != a.tier_want) continue;
     const int npb_ = __ldg(a.sp.np + pb_id), npk_ = __ldg(a.sp.np + pk_id);
     ++done;
     doneq += (unsigned long long)npb_ * npk_;
@@ -367,7 +380,9 @@ __global__ void __launch_bounds__(128) jk_thread_kernel(JKArgs A) {
                                           __ldg(a.sp.eoff + pb_id), __ldg(a.sp.poff + pk_id), __ldg(a.sp.np + pk_id),
                                           __ldg(a.sp.eoff + pk_id), X);
     contract_block<LA, LB, LC, LD, T>(A, X, w, __ldg(a.sp.ao1 + pb_id), __ldg(a.sp.ao2 + pb_id),
-                                      __ldg(a.sp.ao1 + pk_id), __ldg(a.sp.ao2 + pk_id));
+                                      __ldg(a.sp.ao1 + pk_id), __ldg(a.sp.ao2 + pk_id), __ldg(a.sp.mat_off + mol),
+                                      __ldg(a.sp.mat_n + mol));
+  }
   }
   if (a.counter && done) {
     atomicAdd(a.counter, done);

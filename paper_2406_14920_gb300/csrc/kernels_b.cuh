@@ -110,18 +110,22 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
   T* Eb = sm + S::SM_EB;
   T* Ws = sm + S::SM_W;
   T* Xs = sm + S::SM_X;
-  const int n = a.nbf;
-  const double* Dp = a.Dp;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t total = a.wl.total;
   unsigned long long done = 0, doneq = 0, doneb = 0;
-  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; item < total; item += nwarps) {
-    const int ib = find_bra(a.wl.prefix, a.wl.nbra, item);
-    const int ik = (int)(item - __ldg(a.wl.prefix + ib));
-    const int pb_id = __ldg(a.wl.bra + ib), pk_id = __ldg(a.wl.ket + ik);
+  const int64_t tile = a.wl.tile, ntiles = (total - a.wl.first + tile - 1) / tile;
+  for (int64_t tl = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; tl < ntiles; tl += nwarps) {
+  const int64_t i0 = a.wl.first + tl * tile, i1 = i0 + tile < total ? i0 + tile : total;
+  BraCursor cur(a.wl, i0);
+  for (int64_t item = i0; item < i1; ++item) {
+    const int ik = cur.at(a.wl, item);
+    const int ib = cur.ib;
+    const int pb_id = __ldg(a.wl.bra + ib);
+    const int mol = __ldg(a.sp.pmol + pb_id);
+    const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
     const int s1 = __ldg(a.sp.s1 + pb_id), s2 = __ldg(a.sp.s2 + pb_id);
     const int s3 = __ldg(a.sp.s1 + pk_id), s4 = __ldg(a.sp.s2 + pk_id);
-    if (a.mixed && quartet_tier(a, pb_id, pk_id, s1, s2, s3, s4) != a.tier_want) continue;
+    if (a.mixed && quartet_tier(a, mol, pb_id, pk_id, s1, s2, s3, s4) != a.tier_want) continue;
     const int npb = __ldg(a.sp.np + pb_id), offb = __ldg(a.sp.poff + pb_id), eb0 = __ldg(a.sp.eoff + pb_id);
     const int npk = __ldg(a.sp.np + pk_id), offk = __ldg(a.sp.poff + pk_id), ek0 = __ldg(a.sp.eoff + pk_id);
     ++done;
@@ -133,6 +137,11 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
     if (s1 == s2) w *= T(0.5);
     if (s3 == s4) w *= T(0.5);
     if (pb_id == pk_id) w *= T(0.5);
+    const int64_t mbase = __ldg(a.sp.mat_off + mol);
+    const int n = __ldg(a.sp.mat_n + mol);
+    const double* Dp = a.Dp + mbase;
+    double* Kh = a.Kh ? a.Kh + mbase : nullptr;
+    double* Jh = A.Jh ? A.Jh + mbase : nullptr;
 
     for (int c0 = 0; c0 < NCD; c0 += CH) {
       const int nci = NCD - c0 < CH ? NCD - c0 : CH;
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
       // contraction of the chunk; one lane per output element
       const int cfirst = c0 / ND, clast = (c0 + nci - 1) / ND;
       const int ncr = clast - cfirst + 1;
-      if (a.Kh) {
+      if (Kh) {
         // Kh_ac[a][c] += w sum_{b, d: (c,d) in chunk} X D_bd ; Kh_bc[b][c] += w sum_{a,d} X D_ad
         for (int o = lane; o < (NA + NB) * ncr; o += 32) {
           const bool isA = o < NA * ncr;
@@ -294,7 +303,7 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
             }
           }
           const int row = isA ? ao1 + r : ao2 + r;
-          atomic_add_d(a.Kh + (size_t)row * n + ao3 + c, (double)(w * s));
+          atomic_add_d(Kh + (size_t)row * n + ao3 + c, (double)(w * s));
         }
         // Kh_ad[a][d] += w sum_{b, c in chunk} X D_bc ; Kh_bd[b][d] += w sum_{a, c} X D_ac
         for (int o = lane; o < (NA + NB) * ND; o += 32) {
@@ -312,10 +321,10 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
             }
           }
           const int row = isA ? ao1 + r : ao2 + r;
-          atomic_add_d(a.Kh + (size_t)row * n + ao4 + d, (double)(w * s));
+          atomic_add_d(Kh + (size_t)row * n + ao4 + d, (double)(w * s));
         }
       }
-      if (A.Jh) {
+      if (Jh) {
         const T w2 = T(2) * w;
         for (int iab = lane; iab < NAB; iab += 32) {  // Jh_ab += 2w sum_cd X D_cd (chunk part)
           T s = T(0);
@@ -323,18 +332,19 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
             const int cd = c0 + ci;
             s = fma(Xs[iab * CH + ci], ldT<T>(Dp + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND), s);
           }
-          atomic_add_d(A.Jh + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB, (double)(w2 * s));
+          atomic_add_d(Jh + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB, (double)(w2 * s));
         }
         for (int ci = lane; ci < nci; ci += 32) {  // Jh_cd += 2w sum_ab X D_ab
           T s = T(0);
           for (int iab = 0; iab < NAB; ++iab)
             s = fma(Xs[iab * CH + ci], ldT<T>(Dp + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB), s);
           const int cd = c0 + ci;
-          atomic_add_d(A.Jh + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND, (double)(w2 * s));
+          atomic_add_d(Jh + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND, (double)(w2 * s));
         }
       }
       __syncwarp();
     }
+  }
   }
   if (a.counter && lane == 0 && done) {
     atomicAdd(a.counter, done);

@@ -28,8 +28,7 @@ struct GradArgs {
   const double* Dp;
   const double* ea;    // exponent of the s1 primitive of each primitive pair
   const int* sh_atom;
-  double* grad;        // natom * 3
-  int nbf;
+  double* grad;        // natom * 3 (all molecules' atoms)
   double cj, ck;       // weights of the Coulomb and exchange parts (1 or 0)
 };
 
@@ -157,14 +156,18 @@ __global__ void __launch_bounds__(128) grad_warp_kernel(GradArgs a) {
   T* Ek = sm + S::SM_EK;
   T* Eb = sm + S::SM_EB;  // [d][E | GA | GB][NEB]
   T* Ws = sm + S::SM_W;
-  const int n = a.nbf;
-  const double* Dp = a.Dp;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t total = a.wl.total;
-  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; item < total; item += nwarps) {
-    const int ib = find_bra(a.wl.prefix, a.wl.nbra, item);
-    const int ik = (int)(item - __ldg(a.wl.prefix + ib));
-    const int pb_id = __ldg(a.wl.bra + ib), pk_id = __ldg(a.wl.ket + ik);
+  const int64_t tile = a.wl.tile, ntiles = (total - a.wl.first + tile - 1) / tile;
+  for (int64_t tl = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; tl < ntiles; tl += nwarps) {
+  const int64_t i0 = a.wl.first + tl * tile, i1 = i0 + tile < total ? i0 + tile : total;
+  BraCursor cur(a.wl, i0);
+  for (int64_t item = i0; item < i1; ++item) {
+    const int ik = cur.at(a.wl, item);
+    const int ib = cur.ib;
+    const int pb_id = __ldg(a.wl.bra + ib);
+    const int mol = __ldg(a.sp.pmol + pb_id);
+    const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
     const int s1 = __ldg(a.sp.s1 + pb_id), s2 = __ldg(a.sp.s2 + pb_id);
     const int s3 = __ldg(a.sp.s1 + pk_id), s4 = __ldg(a.sp.s2 + pk_id);
     const int npb = __ldg(a.sp.np + pb_id), offb = __ldg(a.sp.poff + pb_id);
@@ -174,6 +177,8 @@ __global__ void __launch_bounds__(128) grad_warp_kernel(GradArgs a) {
     T w = T(1);
     if (s1 == s2) w *= T(0.5);
     if (s3 == s4) w *= T(0.5);
+    const int n = __ldg(a.sp.mat_n + mol);
+    const double* Dp = a.Dp + __ldg(a.sp.mat_off + mol);
     T gA[3] = {0.0, 0.0, 0.0}, gB[3] = {0.0, 0.0, 0.0};
 
     for (int c0 = 0; c0 < NCD; c0 += CH) {
@@ -356,6 +361,7 @@ __global__ void __launch_bounds__(128) grad_warp_kernel(GradArgs a) {
       }
     }
     __syncwarp();
+  }
   }
 }
 

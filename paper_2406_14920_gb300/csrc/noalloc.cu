@@ -15,7 +15,7 @@
 
 int eri_build_jk_scratch(eri_plan_t* plan, const double* D, double* J, double* K, double* Dp, double* Kh, double* Jh,
                          cudaStream_t s);
-int eri_plan_nbf_device(eri_plan_t* plan, int* nbf, int* device);
+int eri_plan_nbf_device(eri_plan_t* plan, int* nbf, int* device, int* nmol);
 
 // Scratch: scaled density D', half-K and half-J accumulators, each nbf x nbf
 // doubles, for nbf <= ERI_NOALLOC_MAX_NBF: 3 * 256 * 256 * 8 B = 1.5 MiB held by
@@ -41,8 +41,9 @@ static int scratch_for(int device, double** out) {
 
 extern "C" int eri_build_jk_noalloc(eri_plan_t* plan, const double* D, double* J, double* K, void* stream) {
   if (!plan || !D || (!J && !K)) return ERI_EINVAL;
-  int nbf = 0, device = 0;
-  eri_plan_nbf_device(plan, &nbf, &device);
+  int nbf = 0, device = 0, nmol = 1;
+  eri_plan_nbf_device(plan, &nbf, &device, &nmol);
+  if (nmol != 1) return ERI_EUNSUPPORTED;
   if (nbf > ERI_NOALLOC_MAX_NBF) {
     fprintf(stderr, "eri_build_jk_noalloc: %d basis functions exceed the fixed scratch limit of %d\n", nbf,
             ERI_NOALLOC_MAX_NBF);

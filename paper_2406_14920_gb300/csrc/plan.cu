@@ -153,16 +153,22 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
   prefmaxp[ip] = (float)fmin(prmx, 1.0e30);
 }
 
-// max |D'| over every shell block (used by the mixed-precision tier test)
-__global__ void k_dmax(int ns, const int* __restrict__ l, const int* __restrict__ ao, const double* __restrict__ Dp,
-                       int nbf, float* __restrict__ dmax) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ns * ns) return;
-  const int a = t / ns, b = t % ns;
-  double m = 0.0;
-  for (int i = 0; i < ncart(l[a]); ++i)
-    for (int j = 0; j < ncart(l[b]); ++j) m = fmax(m, fabs(Dp[(size_t)(ao[a] + i) * nbf + ao[b] + j]));
-  dmax[t] = __double2float_ru((float)m);
+// max |D'| over the blocks (s1, s2) and (s2, s1) of every shell pair (used by
+// the mixed-precision tier test)
+__global__ void k_dmax(int npair, const int* __restrict__ s1, const int* __restrict__ s2, const int* __restrict__ l,
+                       const int* __restrict__ pao1, const int* __restrict__ pao2, const int* __restrict__ pmol,
+                       const int64_t* __restrict__ mat_off, const int* __restrict__ mat_n,
+                       const double* __restrict__ Dp, float* __restrict__ dmax) {
+  int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= npair) return;
+  const int m = pmol[ip], n = mat_n[m];
+  const double* D = Dp + mat_off[m];
+  const int a = pao1[ip], b = pao2[ip], na = ncart(l[s1[ip]]), nb = ncart(l[s2[ip]]);
+  double mx = 0.0;
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < nb; ++j)
+      mx = fmax(mx, fmax(fabs(D[(size_t)(a + i) * n + b + j]), fabs(D[(size_t)(b + j) * n + a + i])));
+  dmax[ip] = __double2float_ru(mx);
 }
 
 // runtime-l E^{ij}_t (Eq. E_recursion), E[(i*5+j)*9+t], i,j <= 4
@@ -297,52 +303,69 @@ __global__ void k_schwarz(int npair, const int* __restrict__ s1, const int* __re
   Q[ip] = __double2float_ru(sqrt(mx));
 }
 
-__global__ void k_qmax(int n, const float* __restrict__ Q, unsigned int* __restrict__ out) {
+// Per-molecule Schwarz maximum (pairs never cross molecules).  Q >= 0, so
+// the unsigned order of the float bits is the float order.
+__global__ void k_qmax(int n, const float* __restrict__ Q, const int* __restrict__ pmol, unsigned int* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float v = i < n ? Q[i] : 0.0f;
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));  // Q >= 0: uint order = float order
+  const int m = i < n ? pmol[i] : -1;
+  unsigned int v = i < n ? __float_as_uint(Q[i]) : 0u;
+  const int m0 = __shfl_sync(0xffffffffu, m, 0);
+  if (__all_sync(0xffffffffu, m == m0 || m < 0)) {
+    v = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && m0 >= 0) atomicMax(out + m0, v);
+  } else if (m >= 0) {
+    atomicMax(out + m, v);
+  }
 }
 
-// significance of each pair: (double)Q * (double)Qmax >= thresh; per-class counts
-__global__ void k_sig(int npair, const float* __restrict__ Q, const unsigned int* __restrict__ qmax_bits, double thresh,
-                      const int* __restrict__ cls, int* __restrict__ sig, int* __restrict__ ccount) {
+// significance of each pair: (double)Q * (double)Qmax(molecule) >= thresh;
+// counts per (molecule, class)
+__global__ void k_sig(int npair, const float* __restrict__ Q, const int* __restrict__ pmol,
+                      const unsigned int* __restrict__ qmax_bits, double thresh, const int* __restrict__ cls,
+                      int* __restrict__ sig, int* __restrict__ ccm) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npair) return;
-  const double qmax = (double)__uint_as_float(*qmax_bits);
+  const int m = pmol[i];
+  const double qmax = (double)__uint_as_float(qmax_bits[m]);
   const int s = ((double)Q[i] * qmax >= thresh) ? 1 : 0;
   sig[i] = s;
-  if (s) atomicAdd(ccount + cls[i], 1);
+  if (s) atomicAdd(ccm + m * NPAIRCLASS + cls[i], 1);
 }
 
-// rank of each significant pair inside its class: Q descending, pair index ascending
+// rank of each significant pair inside its (molecule, class) segment: Q
+// descending, pair index ascending.  The sorted array is class-major, molecule
+// by molecule inside a class: segment (X, m) starts at coff[X] + segloc[m][X].
 __global__ void k_rank(int npair, const float* __restrict__ Q, const int* __restrict__ cls, const int* __restrict__ sig,
-                       const int* __restrict__ coff, int* __restrict__ sorted, int* __restrict__ pos) {
+                       const int* __restrict__ pmol, const int* __restrict__ pbase, const int* __restrict__ coff,
+                       const int* __restrict__ segloc, int* __restrict__ sorted, int* __restrict__ pos) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npair || !sig[i]) return;
   const float qi = Q[i];
-  const int ci = cls[i];
+  const int ci = cls[i], m = pmol[i];
   int r = 0;
-  for (int j = 0; j < npair; ++j) {
+  for (int j = pbase[m]; j < pbase[m + 1]; ++j) {
     if (!sig[j] || cls[j] != ci) continue;
     const float qj = Q[j];
     if (qj > qi || (qj == qi && j < i)) ++r;
   }
-  sorted[coff[ci] + r] = i;
+  sorted[coff[ci] + segloc[m * NPAIRCLASS + ci] + r] = i;
   pos[i] = r;
 }
 
-// counts[pair][Y] = number of kets of class Y with Q_i Q_k >= thresh (binary search on the Q-sorted list)
+// counts[pair][Y] = number of kets of class Y (same molecule) with Q_i Q_k >= thresh
+// (binary search on the Q-sorted segment)
 __global__ void k_counts(int npair, const float* __restrict__ Q, const int* __restrict__ sig,
-                         const int* __restrict__ sorted, const int* __restrict__ coff, const int* __restrict__ ccount,
-                         double thresh, int* __restrict__ counts) {
+                         const int* __restrict__ pmol, const int* __restrict__ sorted, const int* __restrict__ coff,
+                         const int* __restrict__ segloc, const int* __restrict__ ccm, double thresh,
+                         int* __restrict__ counts) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= npair * NPAIRCLASS) return;
   const int i = t / NPAIRCLASS, Y = t % NPAIRCLASS;
   if (!sig[i]) { counts[t] = 0; return; }
+  const int m = pmol[i];
   const double qi = (double)Q[i];
-  const int* lst = sorted + coff[Y];
-  int lo = 0, hi = ccount[Y];  // first position with Q_i Q_k < thresh
+  const int* lst = sorted + coff[Y] + segloc[m * NPAIRCLASS + Y];
+  int lo = 0, hi = ccm[m * NPAIRCLASS + Y];  // first position with Q_i Q_k < thresh
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
     if (qi * (double)Q[lst[mid]] >= thresh) lo = mid + 1; else hi = mid;
@@ -350,62 +373,126 @@ __global__ void k_counts(int npair, const float* __restrict__ Q, const int* __re
   counts[t] = lo;
 }
 
-// cumnp[coff[Y] + k] = primitive pairs of the first k kets of class Y (one thread per class)
+// Exclusive scan of one int64 per thread over the block (blockDim.x a multiple
+// of 32); *total receives the block sum.  Every thread of the block must call it.
+__device__ __forceinline__ int64_t block_exscan(int64_t v, int64_t* wsum, int64_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int64_t t = lane < nw ? wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) wsum[lane] = t;
+  }
+  __syncthreads();
+  const int64_t before = w > 0 ? wsum[w - 1] : 0;
+  *total = wsum[nw - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+// cumnp[coff[Y] + Y + k] = primitive pairs of the first k entries of class Y's
+// sorted list (all molecules, in list order); one block per class
 __global__ void k_cumnp(const int* __restrict__ sorted, const int* __restrict__ coff, const int* __restrict__ ccount,
                         const int* __restrict__ np, int64_t* __restrict__ cumnp) {
-  const int Y = blockIdx.x * blockDim.x + threadIdx.x;
-  if (Y >= NPAIRCLASS) return;
-  int64_t acc = 0;
+  __shared__ int64_t wsum[32];
+  const int Y = blockIdx.x;
+  const int n = ccount[Y];
   const int* kl = sorted + coff[Y];
   int64_t* out = cumnp + coff[Y] + Y;  // class Y occupies ccount[Y] + 1 slots
-  for (int k = 0; k < ccount[Y]; ++k) {
-    out[k] = acc;
-    acc += np[kl[k]];
+  int64_t carry = 0;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    const int64_t v = k < n ? np[kl[k]] : 0;
+    int64_t tot;
+    const int64_t ex = block_exscan(v, wsum, &tot);
+    if (k < n) out[k] = carry + ex;
+    carry += tot;
   }
-  out[ccount[Y]] = acc;
+  if (threadIdx.x == 0) out[n] = carry;
 }
 
-// prefix arrays of the K (canonical) and J (ordered) work lists, one thread per class pair
+// Prefix arrays of the K (canonical) and J (ordered) work lists, one block per
+// class pair (X, Y).  A bra of class X sees the kets of class Y of its own
+// molecule; canonical lists (Y <= X) keep, for X == Y, only kets at or before
+// the bra's own rank in the (molecule, class) segment.
 __global__ void k_prefix(const int* __restrict__ sorted, const int* __restrict__ coff, const int* __restrict__ ccount,
-                         const int* __restrict__ counts, const int64_t* __restrict__ koff, const int64_t* __restrict__ joff,
-                         int64_t* __restrict__ kpre, int64_t* __restrict__ jpre, int64_t* __restrict__ ktot,
-                         int64_t* __restrict__ jtot, const int* __restrict__ np, const int64_t* __restrict__ cumnp,
-                         int64_t* __restrict__ kprim) {
-  const int cp = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cp >= NPAIRCLASS * NPAIRCLASS) return;
+                         const int* __restrict__ segloc, const int* __restrict__ pmol, const int* __restrict__ pos,
+                         const int* __restrict__ counts, const int64_t* __restrict__ koff,
+                         const int64_t* __restrict__ joff, int64_t* __restrict__ kpre, int64_t* __restrict__ jpre,
+                         int64_t* __restrict__ ktot, int64_t* __restrict__ jtot, const int* __restrict__ np,
+                         const int64_t* __restrict__ cumnp, int64_t* __restrict__ kprim) {
+  __shared__ int64_t wsum[32];
+  const int cp = blockIdx.x;
   const int X = cp / NPAIRCLASS, Y = cp % NPAIRCLASS;
+  const bool canon = Y <= X;
   const int nb = ccount[X];
   const int* bl = sorted + coff[X];
-  const int* kl = sorted + coff[Y];
-  int64_t accj = 0;
   int64_t* jp = jpre + joff[cp];
-  for (int i = 0; i < nb; ++i) {
-    jp[i] = accj;
-    accj += counts[bl[i] * NPAIRCLASS + Y];
-  }
-  jp[nb] = accj;
-  jtot[cp] = accj;
-  if (Y <= X) {
-    int64_t acck = 0, accp = 0;
-    int64_t* kp = kpre + koff[cp];
-    for (int i = 0; i < nb; ++i) {
-      kp[i] = acck;
-      int c = counts[bl[i] * NPAIRCLASS + Y];
-      if (X == Y && c > i + 1) c = i + 1;
-      acck += c;
-      accp += cumnp[coff[Y] + Y + c] * np[bl[i]];
+  int64_t* kp = canon ? kpre + koff[cp] : nullptr;
+  const int64_t* cy = cumnp + coff[Y] + Y;
+  int64_t cj_carry = 0, ck_carry = 0, cp_carry = 0;
+  for (int base = 0; base < nb; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    int64_t cj = 0, ck = 0, pp = 0;
+    if (i < nb) {
+      const int b = bl[i];
+      cj = counts[b * NPAIRCLASS + Y];
+      if (canon) {
+        ck = cj;
+        if (X == Y && ck > pos[b] + 1) ck = pos[b] + 1;
+        const int s0 = segloc[pmol[b] * NPAIRCLASS + Y];
+        pp = (cy[s0 + ck] - cy[s0]) * np[b];
+      }
     }
-    kp[nb] = acck;
-    ktot[cp] = acck;
-    kprim[cp] = accp;
+    int64_t tot;
+    const int64_t exj = block_exscan(cj, wsum, &tot);
+    if (i < nb) jp[i] = cj_carry + exj;
+    cj_carry += tot;
+    if (canon) {
+      const int64_t exk = block_exscan(ck, wsum, &tot);
+      if (i < nb) kp[i] = ck_carry + exk;
+      ck_carry += tot;
+      block_exscan(pp, wsum, &tot);
+      cp_carry += tot;
+    }
+  }
+  if (threadIdx.x == 0) {
+    jp[nb] = cj_carry;
+    jtot[cp] = cj_carry;
+    if (canon) {
+      kp[nb] = ck_carry;
+      ktot[cp] = ck_carry;
+      kprim[cp] = cp_carry;
+    }
   }
 }
 
-// D' = D f f (component norms folded in)
-__global__ void k_scale_d(int n, const double* __restrict__ D, const double* __restrict__ f, double* __restrict__ Dp) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Where each molecule's nbf_m x nbf_m block sits in packed D / J / K, and the
+// global AO index of its first function (component factors f are global).
+struct MolMats {
+  const int64_t* off;
+  const int* n;
+  const int* aobase;
+};
+
+// D' = D f f (component norms folded in); grid (x, molecule)
+__global__ void k_scale_d(MolMats mm, const double* __restrict__ D, const double* __restrict__ f,
+                          double* __restrict__ Dp) {
+  const int m = blockIdx.y, n = mm.n[m];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)n * n) return;
-  Dp[i] = D[i] * f[i / n] * f[i % n];
+  const int64_t o = mm.off[m] + i;
+  const int a0 = mm.aobase[m];
+  Dp[o] = D[o] * f[a0 + i / n] * f[a0 + i % n];
 }
 
 // Hermite density per primitive pair (Eq. j_formula, first sub-step):
@@ -413,11 +500,15 @@ __global__ void k_scale_d(int n, const double* __restrict__ D, const double* __r
 // (the pair stands for both orders), 1 for a diagonal pair.
 __global__ void k_hermite_density(int npair, const int* __restrict__ s1, const int* __restrict__ s2,
                                   const int* __restrict__ np, const int* __restrict__ poff, const int* __restrict__ hoff,
-                                  const int* __restrict__ sh_l, const int* __restrict__ ao, const int* __restrict__ sig,
-                                  PairData pd, const double* __restrict__ Dp, int nbf, double* __restrict__ Dh) {
+                                  const int* __restrict__ sh_l, const int* __restrict__ pao1,
+                                  const int* __restrict__ pao2, const int* __restrict__ pmol, MolMats mm,
+                                  const int* __restrict__ sig, PairData pd, const double* __restrict__ Dp,
+                                  double* __restrict__ Dh) {
   int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= npair || !sig[ip]) return;
   const int a = s1[ip], b = s2[ip], la = sh_l[a], lb = sh_l[b], H = nherm(la + lb);
+  const int m = pmol[ip], nbf = mm.n[m];
+  const double* Dm = Dp + mm.off[m];
   const double sc = a == b ? 1.0 : 2.0;
   double E[3][225];
   for (int k = 0; k < np[ip]; ++k) {
@@ -431,7 +522,7 @@ __global__ void k_hermite_density(int npair, const int* __restrict__ s1, const i
       for (int nu = 0; nu < ncart(lb); ++nu) {
         int jx, jy, jz;
         cart_xyz(lb, nu, jx, jy, jz);
-        const double dv = sc * Dp[(size_t)(ao[a] + mu) * nbf + ao[b] + nu];
+        const double dv = sc * Dm[(size_t)(pao1[ip] + mu) * nbf + pao2[ip] + nu];
         for (int tx = 0; tx <= ix + jx; ++tx)
           for (int ty = 0; ty <= iy + jy; ++ty)
             for (int tz = 0; tz <= iz + jz; ++tz) {
@@ -447,8 +538,9 @@ __global__ void k_hermite_density(int npair, const int* __restrict__ s1, const i
 // Cartesian J from Hermite J (Eq. j_formula, last sub-step): thread per (pair, mu, nu)
 __global__ void k_post_j(int npair, const int* __restrict__ s1, const int* __restrict__ s2, const int* __restrict__ np,
                          const int* __restrict__ poff, const int* __restrict__ hoff, const int* __restrict__ sh_l,
-                         const int* __restrict__ ao, const int* __restrict__ sig, PairData pd,
-                         const double* __restrict__ Jh, const double* __restrict__ f, int nbf, double* __restrict__ J) {
+                         const int* __restrict__ pao1, const int* __restrict__ pao2, const int* __restrict__ pmol,
+                         MolMats mm, const int* __restrict__ sig, PairData pd, const double* __restrict__ Jh,
+                         const double* __restrict__ f, double* __restrict__ J) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= npair * 100) return;
   const int ip = t / 100, c = t % 100;
@@ -472,40 +564,48 @@ __global__ void k_post_j(int npair, const int* __restrict__ s1, const int* __res
           v += E[0][(ix * 5 + jx) * 9 + tx] * E[1][(iy * 5 + jy) * 9 + ty] * E[2][(iz * 5 + jz) * 9 + tz] *
                jh[herm_index(tx, ty, tz)];
   }
-  const int r = ao[a] + mu, cc = ao[b] + nu;
-  v *= f[r] * f[cc];
-  J[(size_t)r * nbf + cc] = v;
-  if (a != b) J[(size_t)cc * nbf + r] = v;
+  const int m = pmol[ip], nbf = mm.n[m], a0 = mm.aobase[m];
+  const int r = pao1[ip] + mu, cc = pao2[ip] + nu;
+  v *= f[a0 + r] * f[a0 + cc];
+  double* Jm = J + mm.off[m];
+  Jm[(size_t)r * nbf + cc] = v;
+  if (a != b) Jm[(size_t)cc * nbf + r] = v;
 }
 
-// K = (Kh + Kh^T) f f  (Eq. 8_fold_symmetry: the transposes carry permutations 5-8)
-__global__ void k_post_k(int n, const double* __restrict__ Kh, const double* __restrict__ f, double* __restrict__ K) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// K = (Kh + Kh^T) f f  (Eq. 8_fold_symmetry: the transposes carry permutations 5-8); grid (x, molecule)
+__global__ void k_post_k(MolMats mm, const double* __restrict__ Kh, const double* __restrict__ f,
+                         double* __restrict__ K) {
+  const int m = blockIdx.y, n = mm.n[m];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)n * n) return;
-  const int r = (int)(i / n), c = (int)(i % n);
-  K[i] = (Kh[i] + Kh[(size_t)c * n + r]) * f[r] * f[c];
+  const int r = (int)(i / n), c = (int)(i % n), a0 = mm.aobase[m];
+  const int64_t o = mm.off[m];
+  K[o + i] = (Kh[o + i] + Kh[o + (int64_t)c * n + r]) * f[a0 + r] * f[a0 + c];
 }
 
-// E_J = 1/2 sum D J, E_K = -1/4 sum D K; one block, fixed order (deterministic)
-__global__ void k_energy(int64_t nn, const double* __restrict__ D, const double* __restrict__ J,
+// E_J = 1/2 sum D J, E_K = -1/4 sum D K per molecule (one block each, fixed
+// order: deterministic); E[2m], E[2m+1]
+__global__ void k_energy(MolMats mm, const double* __restrict__ D, const double* __restrict__ J,
                          const double* __restrict__ K, double* __restrict__ E) {
   __shared__ double sj[32], sk[32];
+  const int m = blockIdx.x;
+  const int64_t nn = (int64_t)mm.n[m] * mm.n[m], o = mm.off[m];
   double aj = 0.0, ak = 0.0;
   for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) {
-    if (J) aj += D[i] * J[i];
-    if (K) ak += D[i] * K[i];
+    if (J) aj += D[o + i] * J[o + i];
+    if (K) ak += D[o + i] * K[o + i];
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    aj += __shfl_xor_sync(0xffffffffu, aj, o);
-    ak += __shfl_xor_sync(0xffffffffu, ak, o);
+  for (int w = 16; w > 0; w >>= 1) {
+    aj += __shfl_xor_sync(0xffffffffu, aj, w);
+    ak += __shfl_xor_sync(0xffffffffu, ak, w);
   }
   if ((threadIdx.x & 31) == 0) { sj[threadIdx.x >> 5] = aj; sk[threadIdx.x >> 5] = ak; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double tj = 0.0, tk = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tj += sj[w]; tk += sk[w]; }
-    E[0] = 0.5 * tj;
-    E[1] = -0.25 * tk;
+    E[2 * m] = 0.5 * tj;
+    E[2 * m + 1] = -0.25 * tk;
   }
 }
 
@@ -588,7 +688,18 @@ BoysTabs eri_plan_impl::boystabs() const {
 ShellPairInfo eri_plan_impl::spinfo() const {
   ShellPairInfo sp;
   sp.s1 = d_ps1; sp.s2 = d_ps2; sp.np = d_pnp; sp.poff = d_ppoff; sp.ao1 = d_pao1; sp.ao2 = d_pao2; sp.hoff = d_phoff; sp.eoff = d_peoff;
+  sp.pmol = d_pmol; sp.mat_off = d_mat_off; sp.mat_n = d_mat_n;
   return sp;
+}
+
+dim3 eri_plan_impl::mat_grid(int block) const {
+  return dim3((unsigned)std::max<int64_t>(1, ((int64_t)max_nbf * max_nbf + block - 1) / block), (unsigned)nmol);
+}
+
+static MolMats molmats(const eri_plan_impl* P) {
+  MolMats m;
+  m.off = P->d_mat_off; m.n = P->d_mat_n; m.aobase = P->d_aobase;
+  return m;
 }
 
 // pair data + Schwarz + lists for the current device coordinates
@@ -610,23 +721,41 @@ int eri_plan_impl::geometry(cudaStream_t s, bool rebuild_q) {
 
 int eri_plan_impl::build_lists(double th, cudaStream_t s) {
   thresh = th;
-  CK(cudaMemsetAsync(d_qmax, 0, sizeof(unsigned int), s));
-  CK(cudaMemsetAsync(d_ccount, 0, sizeof(int) * NPAIRCLASS, s));
-  k_qmax<<<grid1(npair, 256), 256, 0, s>>>(npair, d_Q, d_qmax);
-  k_sig<<<grid1(npair, 256), 256, 0, s>>>(npair, d_Q, d_qmax, th, d_pcls, d_sig, d_ccount);
+  if (gexec) {  // a captured build holds the old list sizes and offsets
+    CK(cudaDeviceSynchronize());
+    CK(cudaGraphExecDestroy(gexec));
+    gexec = nullptr;
+  }
+  const int nm10 = nmol * NPAIRCLASS;
+  CK(cudaMemsetAsync(d_qmax, 0, sizeof(unsigned int) * nmol, s));
+  CK(cudaMemsetAsync(d_ccm, 0, sizeof(int) * nm10, s));
+  k_qmax<<<grid1(npair, 256), 256, 0, s>>>(npair, d_Q, d_pmol, d_qmax);
+  k_sig<<<grid1(npair, 256), 256, 0, s>>>(npair, d_Q, d_pmol, d_qmax, th, d_pcls, d_sig, d_ccm);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(h_ccount, d_ccount, sizeof(int) * NPAIRCLASS, cudaMemcpyDeviceToHost, s));
+  h_ccm.assign(nm10, 0);
+  CK(cudaMemcpyAsync(h_ccm.data(), d_ccm, sizeof(int) * nm10, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  int coff[NPAIRCLASS];
+  // class-major layout, molecule by molecule inside a class
+  h_segloc.assign(nm10, 0);
   int acc = 0;
-  nsig = 0;
-  for (int X = 0; X < NPAIRCLASS; ++X) { coff[X] = acc; acc += h_ccount[X]; }
+  for (int X = 0; X < NPAIRCLASS; ++X) {
+    h_coff[X] = acc;
+    int loc = 0;
+    for (int m = 0; m < nmol; ++m) {
+      h_segloc[m * NPAIRCLASS + X] = loc;
+      loc += h_ccm[m * NPAIRCLASS + X];
+    }
+    h_ccount[X] = loc;
+    acc += loc;
+  }
   nsig = acc;
-  for (int X = 0; X < NPAIRCLASS; ++X) h_coff[X] = coff[X];
   CK(cudaMemcpyAsync(d_coff, h_coff, sizeof(int) * NPAIRCLASS, cudaMemcpyHostToDevice, s));
-  k_rank<<<grid1(npair, 256), 256, 0, s>>>(npair, d_Q, d_pcls, d_sig, d_coff, d_sorted, d_pos);
-  k_counts<<<grid1((int64_t)npair * NPAIRCLASS, 256), 256, 0, s>>>(npair, d_Q, d_sig, d_sorted, d_coff, d_ccount, th,
-                                                               d_counts);
+  CK(cudaMemcpyAsync(d_ccount, h_ccount, sizeof(int) * NPAIRCLASS, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_segloc, h_segloc.data(), sizeof(int) * nm10, cudaMemcpyHostToDevice, s));
+  k_rank<<<grid1(npair, 256), 256, 0, s>>>(npair, d_Q, d_pcls, d_sig, d_pmol, d_pbase, d_coff, d_segloc, d_sorted,
+                                           d_pos);
+  k_counts<<<grid1((int64_t)npair * NPAIRCLASS, 256), 256, 0, s>>>(npair, d_Q, d_sig, d_pmol, d_sorted, d_coff,
+                                                                   d_segloc, d_ccm, th, d_counts);
   CK(cudaGetLastError());
   int64_t ko = 0, jo = 0;
   for (int X = 0; X < NPAIRCLASS; ++X)
@@ -648,9 +777,10 @@ int eri_plan_impl::build_lists(double th, cudaStream_t s) {
   }
   CK(cudaMemcpyAsync(d_koff, h_koff, sizeof(h_koff), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_joff, h_joff, sizeof(h_joff), cudaMemcpyHostToDevice, s));
-  k_cumnp<<<1, 32, 0, s>>>(d_sorted, d_coff, d_ccount, d_pnp, d_cumnp);
-  k_prefix<<<1, 128, 0, s>>>(d_sorted, d_coff, d_ccount, d_counts, d_koff, d_joff, d_kpre, d_jpre, d_ktot, d_jtot,
-                             d_pnp, d_cumnp, d_kprim);
+  k_cumnp<<<NPAIRCLASS, 1024, 0, s>>>(d_sorted, d_coff, d_ccount, d_pnp, d_cumnp);
+  k_prefix<<<NPAIRCLASS * NPAIRCLASS, 1024, 0, s>>>(d_sorted, d_coff, d_ccount, d_segloc, d_pmol, d_pos, d_counts,
+                                                     d_koff, d_joff, d_kpre, d_jpre, d_ktot, d_jtot, d_pnp, d_cumnp,
+                                                     d_kprim);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(h_ktot, d_ktot, sizeof(h_ktot), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h_jtot, d_jtot, sizeof(h_jtot), cudaMemcpyDeviceToHost, s));
@@ -661,8 +791,11 @@ int eri_plan_impl::build_lists(double th, cudaStream_t s) {
 
 WorkList eri_plan_impl::klist(int X, int Y) const {
   WorkList w;
+  w.first = 0;
+  w.tile = 1;
   w.bra = d_sorted + h_coff[X];
   w.ket = d_sorted + h_coff[Y];
+  w.kseg = d_segloc + Y;
   w.prefix = d_kpre + h_koff[X * NPAIRCLASS + Y];
   w.nbra = h_ccount[X];
   w.total = h_ktot[X * NPAIRCLASS + Y];
@@ -671,8 +804,11 @@ WorkList eri_plan_impl::klist(int X, int Y) const {
 
 WorkList eri_plan_impl::jlist(int X, int Y) const {
   WorkList w;
+  w.first = 0;
+  w.tile = 4;
   w.bra = d_sorted + h_coff[X];
   w.ket = d_sorted + h_coff[Y];
+  w.kseg = d_segloc + Y;
   w.prefix = d_jpre + h_joff[X * NPAIRCLASS + Y];
   w.nbra = h_ccount[X];
   w.total = h_jtot[X * NPAIRCLASS + Y];
@@ -684,9 +820,22 @@ void eri_plan_impl::release() {
                   d_pnp, d_ppoff, d_pao1, d_pao2, d_phoff, d_pcls, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf,
                   d_PBf, d_preff, d_Q, d_qmax, d_sig, d_ccount, d_coff, d_sorted, d_pos, d_counts, d_koff, d_joff,
                   d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Jh, d_Dherm,
-                  d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp, d_ea};
+                  d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp, d_ea,
+                  d_mat_off, d_mat_n, d_aobase, d_pbase, d_pmol, d_shloc, d_ccm, d_segloc};
   for (auto& e : prof_events) cudaEventDestroy(e);
   prof_events.clear();
+  if (gexec) cudaGraphExecDestroy(gexec);
+  gexec = nullptr;
+  for (int b = 0; b < kBranches; ++b) {
+    if (branch[b]) cudaStreamDestroy(branch[b]);
+    if (join_ev[b]) cudaEventDestroy(join_ev[b]);
+    branch[b] = nullptr;
+    join_ev[b] = nullptr;
+  }
+  if (fork_ev) cudaEventDestroy(fork_ev);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  fork_ev = nullptr;
+  cap_stream = nullptr;
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -696,6 +845,17 @@ static const double kPmax32 = 1.0e3;
 
 static const int kClassL1[NPAIRCLASS] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 static const int kClassL2[NPAIRCLASS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+
+int eri_plan_impl::ensure_streams() {
+  if (cap_stream) return ERI_OK;
+  CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+  for (int b = 0; b < kBranches; ++b) {
+    CK(cudaStreamCreateWithFlags(&branch[b], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&join_ev[b], cudaEventDisableTiming));
+  }
+  return ERI_OK;
+}
 
 cudaError_t eri_plan_impl::prof_event_pair(cudaEvent_t* a, cudaEvent_t* b) {
   while ((int)prof_events.size() < prof_ev_used + 2) {
@@ -738,6 +898,17 @@ static double class_flops(int X, int Y, double nq, double npq, double nbp, bool 
   return npq * per_pq + nbp * per_bp + nq * per_q;
 }
 
+// Default work-tile length: the thread kernel's lanes already take adjacent
+// items; a warp kernel walks 4 consecutive quartets (mostly one bra) per tile.
+static int default_tile(int X, int Y, int tier) {
+  return use_thread_kernel(kClassL1[X], kClassL2[X], kClassL1[Y], kClassL2[Y], tier == 1) ? 1 : 4;
+}
+
+int eri_plan_impl::tile_for(int X, int Y, int tier) const {
+  const int t = tile_k[(X * NPAIRCLASS + Y) * 2 + tier];
+  return t > 0 ? t : default_tile(X, Y, tier);
+}
+
 static cudaError_t launch_jk_class(int X, int Y, int prec, const JKArgs& ja, cudaStream_t s, int nsm) {
   switch (X) {
     case 0: return launch_jk_bra0(Y, prec, ja, s, nsm);
@@ -765,9 +936,8 @@ extern "C" int eri_default_opts(eri_opts_t* o) {
   return ERI_OK;
 }
 
-extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const eri_opts_t* opts, eri_plan_t** out) {
-  if (!basis || !coords || !out || !basis->shells || !basis->exps || !basis->coefs) return ERI_EINVAL;
-  *out = nullptr;
+static int check_basis(const eri_basis_t* basis, const double* coords, int* nprim_out) {
+  if (!basis || !coords || !basis->shells || !basis->exps || !basis->coefs) return ERI_EINVAL;
   const int ns = basis->nshell, na = basis->natom;
   if (ns <= 0 || na <= 0 || ns > 100000) return ERI_EINVAL;
   int nprim_tot = 0;
@@ -782,6 +952,27 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
     if (!(basis->exps[i] > 0.0) || !std::isfinite(basis->exps[i]) || !std::isfinite(basis->coefs[i])) return ERI_EINVAL;
   for (int i = 0; i < 3 * na; ++i)
     if (!std::isfinite(coords[i])) return ERI_EINVAL;
+  *nprim_out = nprim_tot;
+  return ERI_OK;
+}
+
+template <typename T>
+static cudaError_t upload(T* d, const std::vector<T>& h) {
+  return cudaMemcpy(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+}
+
+// One plan over nmol independent molecules.  Shells, atoms and primitives are
+// numbered globally (molecule after molecule); shell pairs are formed inside
+// each molecule only, pair index pairbase[m] + a(a+1)/2 + b for local shells a >= b.
+static int plan_create(int nmol, const eri_basis_t* const* bases, const double* const* coords, const eri_opts_t* opts,
+                       eri_plan_t** out) {
+  if (!out || nmol <= 0 || nmol > 65535 || !bases || !coords) return ERI_EINVAL;
+  *out = nullptr;
+  std::vector<int> nprim_m(nmol);
+  for (int m = 0; m < nmol; ++m) {
+    const int rc = check_basis(bases[m], coords[m], &nprim_m[m]);
+    if (rc != ERI_OK) return rc;
+  }
   eri_opts_t o;
   eri_default_opts(&o);
   if (opts) o = *opts;
@@ -796,38 +987,83 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
   }
   cudaGetDevice(&P->device);
   cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, P->device);
+  P->nmol = nmol;
+  // global numbering
+  std::vector<int> l, atom, np, po, ao, aol, shloc;
+  std::vector<double> ex, co, xyz;
+  P->h_mat_off.assign(nmol + 1, 0);
+  P->h_mat_n.assign(nmol, 0);
+  P->h_aobase.assign(nmol + 1, 0);
+  P->h_atombase.assign(nmol + 1, 0);
+  P->h_pairbase.assign(nmol + 1, 0);
+  std::vector<int> shellbase(nmol + 1, 0);
+  int nbf = 0, nprim_tot = 0;
+  int64_t npair64 = 0;
+  for (int m = 0; m < nmol; ++m) {
+    const eri_basis_t* B = bases[m];
+    shellbase[m] = (int)l.size();
+    P->h_atombase[m] = (int)(xyz.size() / 3);
+    P->h_aobase[m] = nbf;
+    P->h_pairbase[m] = (int)npair64;
+    int nb = 0;
+    for (int s = 0; s < B->nshell; ++s) {
+      const eri_shell_t& sh = B->shells[s];
+      l.push_back(sh.l);
+      atom.push_back(P->h_atombase[m] + sh.atom);
+      np.push_back(sh.nprim);
+      po.push_back(nprim_tot + sh.prim_offset);
+      ao.push_back(nbf + nb);
+      aol.push_back(nb);
+      shloc.push_back(s);
+      nb += ncart(sh.l);
+    }
+    ex.insert(ex.end(), B->exps, B->exps + nprim_m[m]);
+    co.insert(co.end(), B->coefs, B->coefs + nprim_m[m]);
+    xyz.insert(xyz.end(), coords[m], coords[m] + 3 * B->natom);
+    nprim_tot += nprim_m[m];
+    nbf += nb;
+    P->h_mat_n[m] = nb;
+    P->h_mat_off[m + 1] = P->h_mat_off[m] + (int64_t)nb * nb;
+    P->max_nbf = std::max(P->max_nbf, nb);
+    npair64 += (int64_t)B->nshell * (B->nshell + 1) / 2;
+  }
+  const int ns = (int)l.size(), na = (int)(xyz.size() / 3);
+  shellbase[nmol] = ns;
+  P->h_atombase[nmol] = na;
+  P->h_aobase[nmol] = nbf;
+  P->h_pairbase[nmol] = (int)std::min<int64_t>(npair64, INT32_MAX);
+  ao.push_back(nbf);
+  if (npair64 > (1LL << 28)) { delete P; return ERI_EUNSUPPORTED; }
   P->nshell = ns;
   P->natom = na;
-  std::vector<int> l(ns), atom(ns), np(ns), po(ns), ao(ns + 1);
-  int nbf = 0;
-  for (int s = 0; s < ns; ++s) {
-    l[s] = basis->shells[s].l; atom[s] = basis->shells[s].atom; np[s] = basis->shells[s].nprim;
-    po[s] = basis->shells[s].prim_offset; ao[s] = nbf; nbf += ncart(l[s]);
-  }
-  ao[ns] = nbf;
   P->nbf = nbf;
-  // shell pairs in pair-index order (a >= b), oriented so that s1 has the higher l
-  const int npair = ns * (ns + 1) / 2;
+  P->nmat = P->h_mat_off[nmol];
+  // shell pairs, molecule by molecule in pair-index order (a >= b), oriented so that s1 has the higher l
+  const int npair = (int)npair64;
   P->npair = npair;
   std::vector<int> ps1(npair), ps2(npair), pnp(npair), ppoff(npair), pao1(npair), pao2(npair), phoff(npair), pcls(npair),
-      peoff(npair);
+      peoff(npair), pmol(npair);
   int64_t nprimpair = 0, nherm_tot = 0, ne_tot = 0;
-  for (int a = 0; a < ns; ++a)
-    for (int b = 0; b <= a; ++b) {
-      int ip = a * (a + 1) / 2 + b;
-      int x = a, y = b;
-      if (l[b] > l[a]) { x = b; y = a; }
-      ps1[ip] = x; ps2[ip] = y;
-      pnp[ip] = np[x] * np[y];
-      ppoff[ip] = (int)nprimpair;
-      pao1[ip] = ao[x]; pao2[ip] = ao[y];
-      phoff[ip] = (int)nherm_tot;
-      pcls[ip] = pair_class(l[x], l[y]);
-      peoff[ip] = (int)ne_tot;
-      nprimpair += pnp[ip];
-      nherm_tot += (int64_t)pnp[ip] * nherm(l[x] + l[y]);
-      ne_tot += (int64_t)pnp[ip] * 3 * (l[x] + 1) * (l[y] + 1) * (l[x] + l[y] + 1);
-    }
+  for (int m = 0; m < nmol; ++m) {
+    const int sb = shellbase[m], nsm = shellbase[m + 1] - sb;
+    for (int a = 0; a < nsm; ++a)
+      for (int b = 0; b <= a; ++b) {
+        const int ip = P->h_pairbase[m] + a * (a + 1) / 2 + b;
+        int x = sb + a, y = sb + b;
+        if (l[y] > l[x]) std::swap(x, y);
+        ps1[ip] = x; ps2[ip] = y;
+        pnp[ip] = np[x] * np[y];
+        ppoff[ip] = (int)std::min<int64_t>(nprimpair, INT32_MAX);
+        pao1[ip] = aol[x]; pao2[ip] = aol[y];
+        phoff[ip] = (int)std::min<int64_t>(nherm_tot, INT32_MAX);
+        pcls[ip] = pair_class(l[x], l[y]);
+        peoff[ip] = (int)std::min<int64_t>(ne_tot, INT32_MAX);
+        pmol[ip] = m;
+        nprimpair += pnp[ip];
+        nherm_tot += (int64_t)pnp[ip] * nherm(l[x] + l[y]);
+        ne_tot += (int64_t)pnp[ip] * 3 * (l[x] + 1) * (l[y] + 1) * (l[x] + l[y] + 1);
+      }
+  }
   if (nprimpair > (1LL << 30) || nherm_tot > (1LL << 31) - 1 || ne_tot > (1LL << 31) - 1) {
     delete P;
     return ERI_EUNSUPPORTED;
@@ -843,14 +1079,17 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
   {
     cudaStream_t s = 0;
     std::vector<RStep> st = make_rsteps();
+    const size_t nm10 = (size_t)nmol * NPAIRCLASS;
     CKP(dalloc(&P->d_sh_l, ns)); CKP(dalloc(&P->d_sh_atom, ns)); CKP(dalloc(&P->d_sh_np, ns));
-    CKP(dalloc(&P->d_sh_po, ns)); CKP(dalloc(&P->d_sh_ao, ns + 1));
+    CKP(dalloc(&P->d_sh_po, ns)); CKP(dalloc(&P->d_sh_ao, ns + 1)); CKP(dalloc(&P->d_shloc, ns));
     CKP(dalloc(&P->d_exps, nprim_tot)); CKP(dalloc(&P->d_coefs, nprim_tot)); CKP(dalloc(&P->d_cn, nprim_tot));
-    CKP(dalloc(&P->d_f, nbf)); CKP(dalloc(&P->d_coords, 3 * na));
+    CKP(dalloc(&P->d_f, nbf)); CKP(dalloc(&P->d_coords, 3 * (size_t)na));
+    CKP(dalloc(&P->d_mat_off, nmol + 1)); CKP(dalloc(&P->d_mat_n, nmol)); CKP(dalloc(&P->d_aobase, nmol + 1));
+    CKP(dalloc(&P->d_pbase, nmol + 1)); CKP(dalloc(&P->d_ccm, nm10)); CKP(dalloc(&P->d_segloc, nm10));
     CKP(dalloc(&P->d_ps1, npair)); CKP(dalloc(&P->d_ps2, npair)); CKP(dalloc(&P->d_pnp, npair));
     CKP(dalloc(&P->d_ppoff, npair)); CKP(dalloc(&P->d_pao1, npair)); CKP(dalloc(&P->d_pao2, npair));
-    CKP(dalloc(&P->d_phoff, npair)); CKP(dalloc(&P->d_pcls, npair));
-    CKP(dalloc(&P->d_Q, npair)); CKP(dalloc(&P->d_qmax, 1)); CKP(dalloc(&P->d_sig, npair));
+    CKP(dalloc(&P->d_phoff, npair)); CKP(dalloc(&P->d_pcls, npair)); CKP(dalloc(&P->d_pmol, npair));
+    CKP(dalloc(&P->d_Q, npair)); CKP(dalloc(&P->d_qmax, nmol)); CKP(dalloc(&P->d_sig, npair));
     CKP(dalloc(&P->d_ccount, NPAIRCLASS)); CKP(dalloc(&P->d_coff, NPAIRCLASS)); CKP(dalloc(&P->d_sorted, npair));
     CKP(dalloc(&P->d_pos, npair)); CKP(dalloc(&P->d_counts, (size_t)npair * NPAIRCLASS));
     CKP(dalloc(&P->d_cumnp, (size_t)npair + NPAIRCLASS));
@@ -861,33 +1100,24 @@ extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const er
     CKP(dalloc(&P->d_boys32, (size_t)BOYS_NT * (BOYS_MMAX + 1) * BOYS_J32));
     CKP(dalloc(&P->d_bexp64, BOYS_NT)); CKP(dalloc(&P->d_bexp32, BOYS_NT));
     CKP(dalloc(&P->d_peoff, npair)); CKP(dalloc(&P->d_E, ne_tot)); CKP(dalloc(&P->d_Ef, ne_tot));
-    CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_prefmaxp, npair)); CKP(dalloc(&P->d_ea, nprimpair)); CKP(dalloc(&P->d_dmax, (size_t)ns * ns));
+    CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_prefmaxp, npair)); CKP(dalloc(&P->d_ea, nprimpair));
+    CKP(dalloc(&P->d_dmax, npair));
     CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3));
     CKP(dalloc(&P->d_rsteps, st.size()));
-    CKP(dalloc(&P->d_Dp, (size_t)nbf * nbf)); CKP(dalloc(&P->d_Kh, (size_t)nbf * nbf));
-    CKP(dalloc(&P->d_Jh, (size_t)nbf * nbf));
+    CKP(dalloc(&P->d_Dp, (size_t)P->nmat)); CKP(dalloc(&P->d_Kh, (size_t)P->nmat));
+    CKP(dalloc(&P->d_Jh, (size_t)P->nmat));
     CKP(dalloc(&P->d_Dherm, nherm_tot)); CKP(dalloc(&P->d_Jherm, nherm_tot));
     CKP(dalloc(&P->d_status, 1));
     if (P->alloc_pairs() != ERI_OK) { rc = ERI_ENOMEM; goto fail; }
-    std::vector<double> ex(basis->exps, basis->exps + nprim_tot), co(basis->coefs, basis->coefs + nprim_tot);
-    CKP(cudaMemcpy(P->d_sh_l, l.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_sh_atom, atom.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_sh_np, np.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_sh_po, po.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_sh_ao, ao.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_exps, ex.data(), sizeof(double) * nprim_tot, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_coefs, co.data(), sizeof(double) * nprim_tot, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_coords, coords, sizeof(double) * 3 * na, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_ps1, ps1.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_ps2, ps2.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_pnp, pnp.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_ppoff, ppoff.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_pao1, pao1.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_pao2, pao2.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_phoff, phoff.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_peoff, peoff.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_pcls, pcls.data(), sizeof(int) * npair, cudaMemcpyHostToDevice));
-    CKP(cudaMemcpy(P->d_rsteps, st.data(), sizeof(RStep) * st.size(), cudaMemcpyHostToDevice));
+    CKP(upload(P->d_sh_l, l)); CKP(upload(P->d_sh_atom, atom)); CKP(upload(P->d_sh_np, np));
+    CKP(upload(P->d_sh_po, po)); CKP(upload(P->d_sh_ao, ao)); CKP(upload(P->d_shloc, shloc));
+    CKP(upload(P->d_exps, ex)); CKP(upload(P->d_coefs, co)); CKP(upload(P->d_coords, xyz));
+    CKP(upload(P->d_mat_off, P->h_mat_off)); CKP(upload(P->d_mat_n, P->h_mat_n));
+    CKP(upload(P->d_aobase, P->h_aobase)); CKP(upload(P->d_pbase, P->h_pairbase));
+    CKP(upload(P->d_ps1, ps1)); CKP(upload(P->d_ps2, ps2)); CKP(upload(P->d_pnp, pnp));
+    CKP(upload(P->d_ppoff, ppoff)); CKP(upload(P->d_pao1, pao1)); CKP(upload(P->d_pao2, pao2));
+    CKP(upload(P->d_phoff, phoff)); CKP(upload(P->d_peoff, peoff)); CKP(upload(P->d_pcls, pcls));
+    CKP(upload(P->d_pmol, pmol)); CKP(upload(P->d_rsteps, st));
     CKP(cudaMemset(P->d_status, 0, sizeof(int)));
     k_normalize<<<grid1(ns, 64), 64>>>(ns, P->d_sh_l, P->d_sh_np, P->d_sh_po, P->d_exps, P->d_coefs, P->d_cn);
     k_compfac<<<grid1(ns, 64), 64>>>(ns, P->d_sh_l, P->d_sh_ao, P->d_f);
@@ -907,6 +1137,28 @@ fail:
   return rc;
 }
 
+extern "C" int eri_plan(const eri_basis_t* basis, const double* coords, const eri_opts_t* opts, eri_plan_t** out) {
+  if (!basis || !coords || !out) return ERI_EINVAL;
+  return plan_create(1, &basis, &coords, opts, out);
+}
+
+extern "C" int eri_plan_batch(int32_t nmol, const eri_basis_t* const* bases, const double* const* coords,
+                              const eri_opts_t* opts, eri_plan_t** out) {
+  return plan_create(nmol, bases, coords, opts, out);
+}
+
+extern "C" int eri_plan_layout(eri_plan_t* plan, int32_t* nmol, int64_t* mat_off, int32_t* nbf, int32_t* atom_off) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P) return ERI_EINVAL;
+  if (nmol) *nmol = P->nmol;
+  for (int m = 0; m <= P->nmol; ++m) {
+    if (mat_off) mat_off[m] = P->h_mat_off[m];
+    if (atom_off) atom_off[m] = P->h_atombase[m];
+    if (nbf && m < P->nmol) nbf[m] = P->h_mat_n[m];
+  }
+  return ERI_OK;
+}
+
 extern "C" int eri_plan_set_coords(eri_plan_t* plan, const double* coords_dev, int32_t freeze_lists, void* stream) {
   eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
   if (!P || !coords_dev) return ERI_EINVAL;
@@ -914,6 +1166,141 @@ extern "C" int eri_plan_set_coords(eri_plan_t* plan, const double* coords_dev, i
   CK(cudaSetDevice(P->device));
   CK(cudaMemcpyAsync(P->d_coords, coords_dev, sizeof(double) * 3 * P->natom, cudaMemcpyDeviceToDevice, s));
   return P->geometry(s, freeze_lists == 0);
+}
+
+// One J/K build on stream s, lists as they stand.  With `concurrent` the class
+// launches are spread over the plan's side streams (fork / join by events) in
+// decreasing order of estimated work; otherwise they run in order on s.
+static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, int precision, cudaStream_t s,
+                      bool concurrent) {
+  const int64_t nn = P->nmat;
+  const MolMats mm = molmats(P);
+  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, P->d_Dp);
+  CK(cudaGetLastError());
+  const bool jengine = J && !K && P->opts.j_engine;
+  if (jengine) {
+    // J alone: Hermite density -> J-engine -> Hermite J to Cartesian (Eq. j_formula)
+    CK(cudaMemsetAsync(P->d_Jherm, 0, sizeof(double) * (size_t)P->nherm_tot, s));
+    k_hermite_density<<<grid1(P->npair, 64), 64, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_pnp, P->d_ppoff,
+                                                          P->d_phoff, P->d_sh_l, P->d_pao1, P->d_pao2, P->d_pmol, mm,
+                                                          P->d_sig, P->pairdata(), P->d_Dp, P->d_Dherm);
+    CK(cudaGetLastError());
+    JArgs ja;
+    ja.pd = P->pairdata(); ja.sp = P->spinfo(); ja.bt = P->boystabs();
+    ja.rsteps = P->d_rsteps; ja.Dherm = P->d_Dherm; ja.Jherm = P->d_Jherm;
+    if (concurrent) {
+      CK(cudaEventRecord(P->fork_ev, s));
+      for (int b = 0; b < eri_plan_impl::kBranches; ++b) CK(cudaStreamWaitEvent(P->branch[b], P->fork_ev, 0));
+    }
+    int nl = 0;
+    for (int X = 0; X < NPAIRCLASS; ++X)
+      for (int Y = 0; Y < NPAIRCLASS; ++Y) {
+        ja.wl = P->jlist(X, Y);
+        if (ja.wl.total == 0) continue;
+        const cudaStream_t ls = concurrent ? P->branch[nl++ % eri_plan_impl::kBranches] : s;
+        const int lab = kClassL1[X] + kClassL2[X], lcd = kClassL1[Y] + kClassL2[Y];
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (lab) {
+          case 0: e = launch_j_lab0(lcd, 0, ja, ls, P->nsm); break;
+          case 1: e = launch_j_lab1(lcd, 0, ja, ls, P->nsm); break;
+          case 2: e = launch_j_lab2(lcd, 0, ja, ls, P->nsm); break;
+          case 3: e = launch_j_lab3(lcd, 0, ja, ls, P->nsm); break;
+          case 4: e = launch_j_lab4(lcd, 0, ja, ls, P->nsm); break;
+          case 5: e = launch_j_lab5(lcd, 0, ja, ls, P->nsm); break;
+          case 6: e = launch_j_lab6(lcd, 0, ja, ls, P->nsm); break;
+        }
+        CK(e);
+      }
+    if (concurrent)
+      for (int b = 0; b < eri_plan_impl::kBranches; ++b) {
+        CK(cudaEventRecord(P->join_ev[b], P->branch[b]));
+        CK(cudaStreamWaitEvent(s, P->join_ev[b], 0));
+      }
+    CK(cudaMemsetAsync(J, 0, sizeof(double) * nn, s));
+    k_post_j<<<grid1((int64_t)P->npair * 100, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_pnp, P->d_ppoff,
+                                                                 P->d_phoff, P->d_sh_l, P->d_pao1, P->d_pao2,
+                                                                 P->d_pmol, mm, P->d_sig, P->pairdata(), P->d_Jherm,
+                                                                 P->d_f, J);
+    CK(cudaGetLastError());
+  } else {
+    // J and/or K from contracted Cartesian ERIs over canonical quartets
+    if (K) CK(cudaMemsetAsync(P->d_Kh, 0, sizeof(double) * nn, s));
+    if (J) CK(cudaMemsetAsync(P->d_Jh, 0, sizeof(double) * nn, s));
+    CK(cudaMemsetAsync(P->d_counters, 0, sizeof(unsigned long long) * NPAIRCLASS * NPAIRCLASS * 6, s));
+    const bool mixed = precision == ERI_MIXED;
+    if (mixed) {
+      k_dmax<<<grid1(P->npair, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_sh_l, P->d_pao1, P->d_pao2,
+                                                  P->d_pmol, P->d_mat_off, P->d_mat_n, P->d_Dp, P->d_dmax);
+      CK(cudaGetLastError());
+    }
+    JKArgs ja;
+    KArgs& ka = ja.k;
+    ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
+    ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Kh = K ? P->d_Kh : nullptr;
+    ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
+    ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
+    ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
+    ja.Jh = J ? P->d_Jh : nullptr;
+    P->last_mixed = mixed;
+    P->last_do_j = J != nullptr;
+    P->last_do_k = K != nullptr;
+    // launches in decreasing order of estimated work (primitive quartets x class cost)
+    struct L { int X, Y, tier; double cost; };
+    std::vector<L> order;
+    for (int X = 0; X < NPAIRCLASS; ++X)
+      for (int Y = 0; Y <= X; ++Y) {
+        const int64_t tot = P->h_ktot[X * NPAIRCLASS + Y];
+        if (tot == 0) continue;
+        const double c = class_flops(X, Y, (double)tot, (double)P->h_kprim[X * NPAIRCLASS + Y], 0.0, J != nullptr,
+                                     K != nullptr);
+        for (int tier = 0; tier < (mixed ? 2 : 1); ++tier) order.push_back({X, Y, tier, c});
+      }
+    if (concurrent) {
+      std::stable_sort(order.begin(), order.end(), [](const L& a, const L& b) { return a.cost > b.cost; });
+      CK(cudaEventRecord(P->fork_ev, s));
+      for (int b = 0; b < eri_plan_impl::kBranches; ++b) CK(cudaStreamWaitEvent(P->branch[b], P->fork_ev, 0));
+    }
+    double load[eri_plan_impl::kBranches] = {};
+    for (const L& l : order) {
+      ka.wl = P->klist(l.X, l.Y);
+      ka.wl.tile = P->tile_for(l.X, l.Y, l.tier);
+      ka.same_class = l.X == l.Y;
+      ka.tier_want = l.tier;
+      ka.counter = P->d_counters + ((l.X * NPAIRCLASS + l.Y) * 2 + l.tier) * 3;
+      cudaStream_t ls = s;
+      if (concurrent) {  // least-loaded branch
+        int b = (int)(std::min_element(load, load + eri_plan_impl::kBranches) - load);
+        load[b] += l.cost;
+        ls = P->branch[b];
+      }
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      const bool prof = P->opts.profile && !concurrent;
+      if (prof) {
+        CK(P->prof_event_pair(&e0, &e1));
+        CK(cudaEventRecord(e0, ls));
+      }
+      CK(launch_jk_class(l.X, l.Y, l.tier, ja, ls, P->nsm));
+      if (prof) {
+        CK(cudaEventRecord(e1, ls));
+        P->prof_log.push_back({l.X, l.Y, l.tier, P->prof_ev_used - 2});
+      }
+    }
+    if (concurrent)
+      for (int b = 0; b < eri_plan_impl::kBranches; ++b) {
+        CK(cudaEventRecord(P->join_ev[b], P->branch[b]));
+        CK(cudaStreamWaitEvent(s, P->join_ev[b], 0));
+      }
+    P->prof_builds += P->opts.profile ? 1 : 0;
+    if (K) {
+      k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, P->d_Kh, P->d_f, K);
+      CK(cudaGetLastError());
+    }
+    if (J) {
+      k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, P->d_Jh, P->d_f, J);
+      CK(cudaGetLastError());
+    }
+  }
+  return ERI_OK;
 }
 
 extern "C" int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double* K, double thresh, int32_t precision,
@@ -927,99 +1314,170 @@ extern "C" int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double
     int rc = P->build_lists(thresh, s);
     if (rc != ERI_OK) return rc;
   }
-  const int n = P->nbf;
-  const int64_t nn = (int64_t)n * n;
-  k_scale_d<<<grid1(nn, 256), 256, 0, s>>>(n, D, P->d_f, P->d_Dp);
-  CK(cudaGetLastError());
-  double fj = 0.0, fk = 0.0;
-  const bool jengine = J && !K && P->opts.j_engine;
-  if (jengine) {
-    // J alone: Hermite density -> J-engine -> Hermite J to Cartesian (Eq. j_formula)
-    CK(cudaMemsetAsync(P->d_Jherm, 0, sizeof(double) * (size_t)P->nherm_tot, s));
-    k_hermite_density<<<grid1(P->npair, 64), 64, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_pnp, P->d_ppoff,
-                                                          P->d_phoff, P->d_sh_l, P->d_sh_ao, P->d_sig, P->pairdata(),
-                                                          P->d_Dp, n, P->d_Dherm);
-    CK(cudaGetLastError());
-    JArgs ja;
-    ja.pd = P->pairdata(); ja.sp = P->spinfo(); ja.bt = P->boystabs();
-    ja.rsteps = P->d_rsteps; ja.Dherm = P->d_Dherm; ja.Jherm = P->d_Jherm;
-    for (int X = 0; X < NPAIRCLASS; ++X)
-      for (int Y = 0; Y < NPAIRCLASS; ++Y) {
-        ja.wl = P->jlist(X, Y);
-        if (ja.wl.total == 0) continue;
-        const int lab = kClassL1[X] + kClassL2[X], lcd = kClassL1[Y] + kClassL2[Y];
-        cudaError_t e = cudaErrorInvalidValue;
-        switch (lab) {
-          case 0: e = launch_j_lab0(lcd, 0, ja, s, P->nsm); break;
-          case 1: e = launch_j_lab1(lcd, 0, ja, s, P->nsm); break;
-          case 2: e = launch_j_lab2(lcd, 0, ja, s, P->nsm); break;
-          case 3: e = launch_j_lab3(lcd, 0, ja, s, P->nsm); break;
-          case 4: e = launch_j_lab4(lcd, 0, ja, s, P->nsm); break;
-          case 5: e = launch_j_lab5(lcd, 0, ja, s, P->nsm); break;
-          case 6: e = launch_j_lab6(lcd, 0, ja, s, P->nsm); break;
-        }
-        CK(e);
+  return build_impl(P, D, J, K, precision, s, false);
+}
+
+extern "C" int eri_build_jk_graph(eri_plan_t* plan, const double* D, double* J, double* K, int32_t precision,
+                                  void* stream) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !D || (!J && !K)) return ERI_EINVAL;
+  if (precision != ERI_FP64 && precision != ERI_MIXED) return ERI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(P->device));
+  if (!P->gexec || P->gkey[0] != D || P->gkey[1] != J || P->gkey[2] != K || P->gprec != precision) {
+    int rc = P->ensure_streams();
+    if (rc != ERI_OK) return rc;
+    if (P->gexec) {
+      CK(cudaStreamSynchronize(s));
+      CK(cudaGraphExecDestroy(P->gexec));
+      P->gexec = nullptr;
+    }
+    // capture one build on the plan's own stream, then instantiate
+    CK(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+    rc = build_impl(P, D, J, K, precision, P->cap_stream, true);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &g);
+    if (rc == ERI_OK && ce != cudaSuccess) rc = eri_fail(ce);
+    if (rc == ERI_OK) {
+      const cudaError_t ie = cudaGraphInstantiate(&P->gexec, g, 0);
+      if (ie != cudaSuccess) {
+        P->gexec = nullptr;
+        rc = eri_fail(ie);
       }
-    CK(cudaMemsetAsync(J, 0, sizeof(double) * nn, s));
-    k_post_j<<<grid1((int64_t)P->npair * 100, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_pnp, P->d_ppoff,
-                                                                 P->d_phoff, P->d_sh_l, P->d_sh_ao, P->d_sig,
-                                                                 P->pairdata(), P->d_Jherm, P->d_f, n, J);
-    CK(cudaGetLastError());
-  } else {
-    // J and/or K from contracted Cartesian ERIs over canonical quartets
-    if (K) CK(cudaMemsetAsync(P->d_Kh, 0, sizeof(double) * nn, s));
-    if (J) CK(cudaMemsetAsync(P->d_Jh, 0, sizeof(double) * nn, s));
-    CK(cudaMemsetAsync(P->d_counters, 0, sizeof(unsigned long long) * NPAIRCLASS * NPAIRCLASS * 6, s));
-    const bool mixed = precision == ERI_MIXED;
-    if (mixed) {
-      k_dmax<<<grid1((int64_t)P->nshell * P->nshell, 256), 256, 0, s>>>(P->nshell, P->d_sh_l, P->d_sh_ao, P->d_Dp, n,
-                                                                         P->d_dmax);
-      CK(cudaGetLastError());
     }
-    JKArgs ja;
-    KArgs& ka = ja.k;
-    ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
-    ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Kh = K ? P->d_Kh : nullptr;
-    ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
-    ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
-    ka.nshell = P->nshell;
-    ka.nbf = n;
-    ja.Jh = J ? P->d_Jh : nullptr;
-    P->last_mixed = mixed;
-    P->last_do_j = J != nullptr;
-    P->last_do_k = K != nullptr;
-    for (int X = 0; X < NPAIRCLASS; ++X)
-      for (int Y = 0; Y <= X; ++Y) {
-        ka.wl = P->klist(X, Y);
-        ka.same_class = X == Y;
-        if (ka.wl.total == 0) continue;
-        for (int tier = 0; tier < (mixed ? 2 : 1); ++tier) {
-          ka.tier_want = tier;
-          ka.counter = P->d_counters + ((X * NPAIRCLASS + Y) * 2 + tier) * 3;
-          cudaEvent_t e0 = nullptr, e1 = nullptr;
-          if (P->opts.profile) {
-            CK(P->prof_event_pair(&e0, &e1));
-            CK(cudaEventRecord(e0, s));
-          }
-          CK(launch_jk_class(X, Y, tier, ja, s, P->nsm));
-          if (P->opts.profile) {
-            CK(cudaEventRecord(e1, s));
-            P->prof_log.push_back({X, Y, tier, P->prof_ev_used - 2});
-          }
-        }
-      }
-    P->prof_builds += P->opts.profile ? 1 : 0;
-    if (K) {
-      k_post_k<<<grid1(nn, 256), 256, 0, s>>>(n, P->d_Kh, P->d_f, K);
-      CK(cudaGetLastError());
+    if (g) cudaGraphDestroy(g);
+    if (rc != ERI_OK) {
+      cudaGetLastError();
+      return rc;
     }
-    if (J) {
-      k_post_k<<<grid1(nn, 256), 256, 0, s>>>(n, P->d_Jh, P->d_f, J);
-      CK(cudaGetLastError());
-    }
+    P->gkey[0] = D;
+    P->gkey[1] = J;
+    P->gkey[2] = K;
+    P->gprec = precision;
   }
-  P->last_flops_j = fj;
-  P->last_flops_k = fk;
+  CK(cudaGraphLaunch(P->gexec, s));
+  return ERI_OK;
+}
+
+// Autotuner: for every (bra class, ket class, tier) launch of this plan, time
+// each candidate work-tile length on three windows of the launch's own work
+// list (at 1/6, 1/2 and 5/6 of it, so that a mixed-precision tier sees its
+// share of quartets) and keep the fastest.  A window is sized so that the
+// default tile takes about trial_ms; each candidate is timed twice (minimum).
+// The trials write into the plan's scratch accumulators only.
+extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision, double trial_ms, void* stream) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !D || !(trial_ms > 0.0)) return ERI_EINVAL;
+  if (precision != ERI_FP64 && precision != ERI_MIXED) return ERI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(P->device));
+  const bool mixed = precision == ERI_MIXED;
+  const MolMats mm = molmats(P);
+  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, P->d_Dp);
+  if (mixed)
+    k_dmax<<<grid1(P->npair, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_sh_l, P->d_pao1, P->d_pao2,
+                                                P->d_pmol, P->d_mat_off, P->d_mat_n, P->d_Dp, P->d_dmax);
+  CK(cudaGetLastError());
+  JKArgs ja;
+  KArgs& ka = ja.k;
+  ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
+  ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Kh = P->d_Kh;
+  ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
+  ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
+  ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
+  ka.counter = nullptr;
+  ja.Jh = P->d_Jh;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = ERI_OK;
+  // time the three windows of `win` items each with tile t; returns ms (< 0 on error)
+  auto trial = [&](int X, int Y, int tier, int t, int64_t win) -> double {
+    const int64_t tot = P->h_ktot[X * NPAIRCLASS + Y];
+    double best = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (cudaEventRecord(e0, s) != cudaSuccess) return -1.0;
+      for (int w = 0; w < 3; ++w) {
+        const int64_t c = tot * (2 * w + 1) / 6;
+        const int64_t f = std::max<int64_t>(0, std::min<int64_t>(c - win / 2, tot - win));
+        ka.wl = P->klist(X, Y);
+        ka.wl.first = f;
+        ka.wl.total = std::min<int64_t>(tot, f + win);
+        ka.wl.tile = t;
+        ka.same_class = X == Y;
+        ka.tier_want = tier;
+        if (launch_jk_class(X, Y, tier, ja, s, P->nsm) != cudaSuccess) return -1.0;
+      }
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0;
+      best = std::min(best, (double)ms);
+    }
+    return best;
+  };
+  static const int kThreadTiles[] = {1, 2, 4, 8};
+  static const int kWarpTiles[] = {1, 2, 4, 8, 16};
+  for (int X = 0; X < NPAIRCLASS && rc == ERI_OK; ++X)
+    for (int Y = 0; Y <= X && rc == ERI_OK; ++Y) {
+      const int64_t tot = P->h_ktot[X * NPAIRCLASS + Y];
+      if (tot == 0) continue;
+      for (int tier = 0; tier < (mixed ? 2 : 1) && rc == ERI_OK; ++tier) {
+        const int def = default_tile(X, Y, tier);
+        int64_t win = std::min<int64_t>(tot, 3 * 32768);
+        double t0 = trial(X, Y, tier, def, win / 3);
+        if (t0 < 0.0) { rc = ERI_ECUDA; break; }
+        if (t0 < 0.5 * trial_ms && win < tot) {
+          win = std::min<int64_t>(tot, (int64_t)((double)win * trial_ms / std::max(t0, 1e-3)));
+          t0 = trial(X, Y, tier, def, win / 3 + 1);
+          if (t0 < 0.0) { rc = ERI_ECUDA; break; }
+        }
+        const bool thr = use_thread_kernel(kClassL1[X], kClassL2[X], kClassL1[Y], kClassL2[Y], tier == 1);
+        const int* cand = thr ? kThreadTiles : kWarpTiles;
+        const int nc = thr ? 4 : 5;
+        int best = def;
+        double bt = t0;
+        for (int i = 0; i < nc; ++i) {
+          if (cand[i] == def) continue;
+          const double t = trial(X, Y, tier, cand[i], win / 3 + 1);
+          if (t < 0.0) { rc = ERI_ECUDA; break; }
+          if (t < 0.97 * bt) { bt = t; best = cand[i]; }
+        }
+        P->tile_k[(X * NPAIRCLASS + Y) * 2 + tier] = best;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (P->gexec) {  // captured builds carry the old tiles
+    cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(P->gexec);
+    P->gexec = nullptr;
+  }
+  return rc;
+}
+
+extern "C" int eri_get_tiles(eri_plan_t* plan, int32_t* tiles) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !tiles) return ERI_EINVAL;
+  for (int X = 0; X < NPAIRCLASS; ++X)
+    for (int Y = 0; Y < NPAIRCLASS; ++Y)
+      for (int t = 0; t < 2; ++t) {
+        const int k = (X * NPAIRCLASS + Y) * 2 + t;
+        tiles[k] = Y <= X ? P->tile_for(X, Y, t) : 0;
+      }
+  return ERI_OK;
+}
+
+extern "C" int eri_set_tiles(eri_plan_t* plan, const int32_t* tiles) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !tiles) return ERI_EINVAL;
+  for (int k = 0; k < NPAIRCLASS * NPAIRCLASS * 2; ++k)
+    if (tiles[k] < 0 || tiles[k] > 1024) return ERI_EINVAL;
+  for (int k = 0; k < NPAIRCLASS * NPAIRCLASS * 2; ++k) P->tile_k[k] = tiles[k];
+  if (P->gexec) {
+    cudaDeviceSynchronize();
+    cudaGraphExecDestroy(P->gexec);
+    P->gexec = nullptr;
+  }
   return ERI_OK;
 }
 
@@ -1029,9 +1487,9 @@ extern "C" int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double
 int eri_build_jk_scratch(eri_plan_t* plan, const double* D, double* J, double* K, double* Dp, double* Kh, double* Jh,
                          cudaStream_t s) {
   eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
-  const int n = P->nbf;
-  const int64_t nn = (int64_t)n * n;
-  k_scale_d<<<grid1(nn, 256), 256, 0, s>>>(n, D, P->d_f, Dp);
+  const int64_t nn = P->nmat;
+  const MolMats mm = molmats(P);
+  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, Dp);
   CK(cudaGetLastError());
   if (K) CK(cudaMemsetAsync(Kh, 0, sizeof(double) * nn, s));
   if (J) CK(cudaMemsetAsync(Jh, 0, sizeof(double) * nn, s));
@@ -1040,31 +1498,32 @@ int eri_build_jk_scratch(eri_plan_t* plan, const double* D, double* J, double* K
   ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
   ka.rsteps = P->d_rsteps; ka.Dp = Dp; ka.Kh = K ? Kh : nullptr;
   ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
+  ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
   ka.tau = 0.0f; ka.pmax32 = 0.0f; ka.mixed = 0; ka.tier_want = 0; ka.counter = nullptr;
-  ka.nshell = P->nshell;
-  ka.nbf = n;
   ja.Jh = J ? Jh : nullptr;
   for (int X = 0; X < NPAIRCLASS; ++X)
     for (int Y = 0; Y <= X; ++Y) {
       ka.wl = P->klist(X, Y);
+      ka.wl.tile = P->tile_for(X, Y, 0);
       ka.same_class = X == Y;
       if (ka.wl.total == 0) continue;
       CK(launch_jk_class(X, Y, 0, ja, s, P->nsm));
     }
   if (K) {
-    k_post_k<<<grid1(nn, 256), 256, 0, s>>>(n, Kh, P->d_f, K);
+    k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, Kh, P->d_f, K);
     CK(cudaGetLastError());
   }
   if (J) {
-    k_post_k<<<grid1(nn, 256), 256, 0, s>>>(n, Jh, P->d_f, J);
+    k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, Jh, P->d_f, J);
     CK(cudaGetLastError());
   }
   return ERI_OK;
 }
 
-int eri_plan_nbf_device(eri_plan_t* plan, int* nbf, int* device) {
+int eri_plan_nbf_device(eri_plan_t* plan, int* nbf, int* device, int* nmol) {
   eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
   *nbf = P->nbf;
+  *nmol = P->nmol;
   *device = P->device;
   return ERI_OK;
 }
@@ -1074,7 +1533,7 @@ extern "C" int eri_energy(eri_plan_t* plan, const double* D, const double* J, co
   eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
   if (!P || !D || !E_out) return ERI_EINVAL;
   CK(cudaSetDevice(P->device));
-  k_energy<<<1, 1024, 0, (cudaStream_t)stream>>>((int64_t)P->nbf * P->nbf, D, J, K, E_out);
+  k_energy<<<P->nmol, 1024, 0, (cudaStream_t)stream>>>(molmats(P), D, J, K, E_out);
   CK(cudaGetLastError());
   return ERI_OK;
 }
@@ -1101,15 +1560,13 @@ extern "C" int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int3
   if (!P || !D || !dEdR) return ERI_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(P->device));
-  const int n = P->nbf;
-  const int64_t nn = (int64_t)n * n;
-  k_scale_d<<<grid1(nn, 256), 256, 0, s>>>(n, D, P->d_f, P->d_Dp);
+  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(molmats(P), D, P->d_f, P->d_Dp);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(dEdR, 0, sizeof(double) * 3 * P->natom, s));
   if (!want_j && !want_k) return ERI_OK;
   GradArgs ga;
   ga.pd = P->pairdata(); ga.sp = P->spinfo(); ga.bt = P->boystabs(); ga.rsteps = P->d_rsteps; ga.Dp = P->d_Dp;
-  ga.ea = P->d_ea; ga.sh_atom = P->d_sh_atom; ga.grad = dEdR; ga.nbf = n;
+  ga.ea = P->d_ea; ga.sh_atom = P->d_sh_atom; ga.grad = dEdR;
   ga.cj = want_j ? 1.0 : 0.0;
   ga.ck = want_k ? 1.0 : 0.0;
   for (int X = 0; X < NPAIRCLASS; ++X)

@@ -10,6 +10,17 @@ struct eri_plan_impl {
   eri_opts_t opts;
   int device = 0, nsm = 1;
   int nshell = 0, natom = 0, nbf = 0, npair = 0, nprimpair = 0, nsig = 0;
+  // molecules: a plan holds nmol independent molecules; pairs never cross
+  // molecules and D / J / K are packed one nbf_m x nbf_m block per molecule
+  int nmol = 1, max_nbf = 0;
+  int64_t nmat = 0;  // packed matrix elements, sum nbf_m^2
+  std::vector<int64_t> h_mat_off;  // [nmol + 1]
+  std::vector<int> h_mat_n, h_aobase, h_atombase, h_pairbase;  // h_aobase / h_atombase / h_pairbase: [nmol + 1]
+  std::vector<int> h_ccm;          // significant pairs per (molecule, class)
+  std::vector<int> h_segloc;       // offset of (molecule, class) segment inside the class list
+  int64_t* d_mat_off = nullptr;
+  int *d_mat_n = nullptr, *d_aobase = nullptr, *d_pbase = nullptr, *d_pmol = nullptr, *d_shloc = nullptr;
+  int *d_ccm = nullptr, *d_segloc = nullptr;
   int64_t nherm_tot = 0;
   double thresh = 1e-12;
   double last_flops_j = 0.0, last_flops_k = 0.0;
@@ -56,6 +67,22 @@ struct eri_plan_impl {
   int prof_builds = 0, prof_ev_used = 0;
   cudaError_t prof_event_pair(cudaEvent_t* a, cudaEvent_t* b);
 
+  // CUDA graph of one build (eri_build_jk_graph): captured on cap_stream, with
+  // the class launches forked onto kBranches side streams so that independent
+  // classes overlap (their tails, and small launches, fill idle SMs)
+  static constexpr int kBranches = 4;
+  cudaStream_t cap_stream = nullptr;
+  cudaStream_t branch[kBranches] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kBranches] = {};
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[3] = {};
+  int gprec = -1;
+  int ensure_streams();
+  // work-tile length (items per worker tile) per (bra class, ket class, tier),
+  // set by eri_autotune or eri_set_tiles; 0 = the built-in default
+  int tile_k[eri::NPAIRCLASS * eri::NPAIRCLASS * 2] = {};
+  int tile_for(int X, int Y, int tier) const;
+
   int alloc_pairs();
   int geometry(cudaStream_t s, bool rebuild_q);
   int build_lists(double th, cudaStream_t s);
@@ -64,5 +91,6 @@ struct eri_plan_impl {
   eri::ShellPairInfo spinfo() const;
   eri::WorkList klist(int X, int Y) const;
   eri::WorkList jlist(int X, int Y) const;
+  dim3 mat_grid(int block) const;
   void release();
 };

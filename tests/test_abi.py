@@ -80,3 +80,32 @@ def test_null_arguments(eri):
     assert L.eri_plan(None, None, None, None) == -1
     assert L.eri_build_jk(None, None, None, None, -1.0, 0, None) == -1
     assert L.eri_plan_destroy(None) == 0
+
+
+def test_plan_batch_rejects_bad_input(eri):
+    """eri_plan_batch validates every molecule (and nmol) on the host."""
+    L = eri.lib()
+    good, k1 = _basis_struct(eri, [(0, 0, 1, 0), (1, 1, 1, 1)], [1.0, 0.5], [1.0, 1.0], 2)
+    bad, k2 = _basis_struct(eri, [(0, 0, 1, 0), (1, 4, 1, 1)], [1.0, 0.5], [1.0, 1.0], 2)
+    c = np.zeros((2, 3))
+    c[1, 0] = 1.5
+    cp = c.ctypes.data_as(C.POINTER(C.c_double))
+    h = C.c_void_p()
+    for nmol in (0, -3, 70000):
+        bp = (C.POINTER(eri.BasisT) * 1)(C.pointer(good))
+        cc = (C.POINTER(C.c_double) * 1)(cp)
+        assert L.eri_plan_batch(nmol, bp, cc, None, C.byref(h)) == -1
+    bp = (C.POINTER(eri.BasisT) * 2)(C.pointer(good), C.pointer(bad))
+    cc = (C.POINTER(C.c_double) * 2)(cp, cp)
+    assert L.eri_plan_batch(2, bp, cc, None, C.byref(h)) == -4
+    assert L.eri_plan_batch(2, None, cc, None, C.byref(h)) == -1
+    assert not h.value
+    assert L.eri_plan_layout(None, None, None, None, None) == -1
+
+
+def test_tuner_and_graph_null_arguments(eri):
+    L = eri.lib()
+    assert L.eri_autotune(None, None, 0, 1.0, None) == -1
+    assert L.eri_get_tiles(None, None) == -1
+    assert L.eri_set_tiles(None, None) == -1
+    assert L.eri_build_jk_graph(None, None, None, None, 0, None) == -1
