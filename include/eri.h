@@ -176,6 +176,22 @@ int eri_build_jk_graph(eri_plan_t* plan, const double* D, double* J, double* K, 
 int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision, double trial_ms, void* stream);
 
 /*
+ * Split the work over nshard GPUs (one plan per GPU, same basis and geometry):
+ * from now on this plan's builds (eri_build_jk, eri_build_jk_graph and the
+ * J-engine) and gradients take only the work tiles t of every class launch with
+ * t % nshard == shard, and return the PARTIAL J, K or dE/dR of that share.  The
+ * shares of shard = 0..nshard-1 cover every quartet exactly once, so a sum
+ * all-reduce of the partial J / K / dEdR over the GPUs gives the full result
+ * (the exchange step; the library does not communicate).  Tiles are a few
+ * quartets long and interleaved, so each share gets an even mix of classes,
+ * screening magnitudes and precision tiers.  A tile is `tile` consecutive items
+ * of the class-pair list for the warp kernels and 32 x tile for the thread
+ * kernel (eri_get_tiles).  (0, 1) restores the whole build.
+ * Errors: ERI_EINVAL (nshard < 1 or shard outside 0..nshard-1).
+ */
+int eri_plan_set_shard(eri_plan_t* plan, int32_t shard, int32_t nshard);
+
+/*
  * Read or set the plan's tile table (host int32 [10][10][2] indexed
  * [bra class][ket class][tier], entries with ket class > bra class unused;
  * 0 in eri_set_tiles = built-in default, valid values 0..1024).  Use them to

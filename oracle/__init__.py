@@ -53,6 +53,7 @@ def lib():
         L.or_lists.argtypes = [C.c_void_p, C.c_double, f, i, i]
         L.or_jk.argtypes = [C.c_void_p, d, C.c_double, f, C.c_int, d, d]
         L.or_energy.argtypes = [C.c_int, d, d, d, d, d]
+        L.or_jk_quartets.argtypes = [C.c_void_p, d, C.c_int, i, d, d]
         L.or_j_block.argtypes = [C.c_void_p, d, C.c_double, f, C.c_int, C.c_int, d]
         L.or_k_block.argtypes = [C.c_void_p, d, C.c_double, f, C.c_int, C.c_int, d]
         L.or_grad.argtypes = [C.c_void_p, d, C.c_double, f, C.c_int, C.c_int, d]
@@ -179,6 +180,14 @@ class Oracle:
         J = np.zeros((self.nbf, self.nbf))
         K = np.zeros((self.nbf, self.nbf))
         lib().or_jk(self.h, _d(D), float(thresh), _f(Q), int(mode), _d(J), _d(K))
+        return J, K
+
+    def jk_quartets(self, D, abcd, J=None, K=None):
+        """Add the J / K contributions of explicit canonical quartets abcd[n, 4]."""
+        J = np.zeros((self.nbf, self.nbf)) if J is None else J
+        K = np.zeros((self.nbf, self.nbf)) if K is None else K
+        a = np.ascontiguousarray(abcd, np.int32).reshape(-1, 4)
+        lib().or_jk_quartets(self.h, _d(np.ascontiguousarray(D, np.float64)), int(a.shape[0]), _i(a), _d(J), _d(K))
         return J, K
 
     def energy(self, D, J, K):

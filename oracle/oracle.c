@@ -717,6 +717,54 @@ void or_jk(void* h, const double* Dm, double thresh, const float* Q, int mode, d
   }
 }
 
+/*
+ * J and K contributions of an explicit list of canonical quartets
+ * abcd[4q..4q+3] = (a, b, c, d), a>=b, c>=d, pair(ab)>=pair(cd), each scattered
+ * into the eight index permutations of Eq. 8_fold_symmetry with the weight
+ * w = 1/2^[a=b] 1/2^[c=d] 1/2^[ab=cd] (as mode 1 of or_jk), no screening.
+ * J and K are accumulated (+=), so partial lists (one per GPU share of a split
+ * build) add up to the whole.  Serial.
+ */
+void or_jk_quartets(void* h, const double* Dm, int nq, const int* abcd, double* J, double* K) {
+  or_ctx* c = (or_ctx*)h;
+  int n = c->nbf;
+  double* X = (double*)malloc(sizeof(double) * 10000);
+  for (int q = 0; q < nq; ++q) {
+    int a = abcd[4 * q], b = abcd[4 * q + 1], cc = abcd[4 * q + 2], d = abcd[4 * q + 3];
+    or_eri_block(h, a, b, cc, d, X);
+    int na = ncart(c->l[a]), nb = ncart(c->l[b]), nc = ncart(c->l[cc]), nd = ncart(c->l[d]);
+    int oa = c->aoff[a], ob = c->aoff[b], oc = c->aoff[cc], od = c->aoff[d];
+    double w = 1.0;
+    if (a == b) w *= 0.5;
+    if (cc == d) w *= 0.5;
+    if (pair_index(a, b) == pair_index(cc, d)) w *= 0.5;
+    for (int i = 0; i < na; ++i)
+      for (int j = 0; j < nb; ++j)
+        for (int k = 0; k < nc; ++k)
+          for (int l = 0; l < nd; ++l) {
+            double x = w * X[((i * nb + j) * nc + k) * nd + l];
+            int m_ = oa + i, n_ = ob + j, l_ = oc + k, s_ = od + l;
+            if (J) {
+              J[(size_t)m_ * n + n_] += x * (Dm[(size_t)l_ * n + s_] + Dm[(size_t)s_ * n + l_]);
+              J[(size_t)n_ * n + m_] += x * (Dm[(size_t)l_ * n + s_] + Dm[(size_t)s_ * n + l_]);
+              J[(size_t)l_ * n + s_] += x * (Dm[(size_t)m_ * n + n_] + Dm[(size_t)n_ * n + m_]);
+              J[(size_t)s_ * n + l_] += x * (Dm[(size_t)m_ * n + n_] + Dm[(size_t)n_ * n + m_]);
+            }
+            if (K) {
+              K[(size_t)m_ * n + l_] += x * Dm[(size_t)n_ * n + s_];
+              K[(size_t)n_ * n + l_] += x * Dm[(size_t)m_ * n + s_];
+              K[(size_t)m_ * n + s_] += x * Dm[(size_t)n_ * n + l_];
+              K[(size_t)n_ * n + s_] += x * Dm[(size_t)m_ * n + l_];
+              K[(size_t)l_ * n + m_] += x * Dm[(size_t)s_ * n + n_];
+              K[(size_t)s_ * n + m_] += x * Dm[(size_t)l_ * n + n_];
+              K[(size_t)l_ * n + n_] += x * Dm[(size_t)s_ * n + m_];
+              K[(size_t)s_ * n + n_] += x * Dm[(size_t)l_ * n + m_];
+            }
+          }
+  }
+  free(X);
+}
+
 /* E_J = 1/2 sum D J, E_K = -1/4 sum D K (SI Eq. si_E_J_K), long double sums */
 void or_energy(int n, const double* Dm, const double* J, const double* K, double* EJ, double* EK) {
   long double sj = 0.0L, sk = 0.0L;

@@ -72,6 +72,7 @@ def lib():
         L.eri_build_jk_graph.argtypes = [vp, vp, vp, vp, i32, vp]
         L.eri_autotune.argtypes = [vp, vp, i32, C.c_double, vp]
         L.eri_get_tiles.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.eri_plan_set_shard.argtypes = [vp, i32, i32]
         L.eri_set_tiles.argtypes = [vp, C.POINTER(C.c_int32)]
         L.eri_energy.argtypes = [vp, vp, vp, vp, vp, vp]
         L.eri_jk_grad.argtypes = [vp, vp, vp, i32, i32, vp]
@@ -250,6 +251,11 @@ class Plan:
                 json.dump(db, f)
             os.replace(tmp, cache)
         return t
+
+    def set_shard(self, shard, nshard):
+        """Compute only this GPU's share of every build / gradient (partial sums;
+        all-reduce them over the GPUs).  (0, 1) = the whole build."""
+        _check(lib().eri_plan_set_shard(self.h, int(shard), int(nshard)), "eri_plan_set_shard")
 
     def tiles(self):
         t = np.zeros(200, np.int32)

@@ -130,6 +130,7 @@ struct WorkList {
   int64_t total;
   int64_t first;           // items [first, total) are processed (0 except in tuning trials)
   int tile;                // consecutive items per worker tile (warp kernels: per warp; thread kernel: per lane)
+  int shard, nshard;       // this launch takes the tiles t with t % nshard == shard (work split over GPUs)
 };
 
 // Boys F_0..F_M at T.  Below BOYS_TMAX: Taylor expansion of F_M around the

@@ -348,8 +348,8 @@ __global__ void __launch_bounds__(128) jk_thread_kernel(JKArgs A) {
   // a warp shares a tile of 32 * tile consecutive items, lane l takes items l, l + 32, ...
   const int64_t span = 32 * (int64_t)a.wl.tile, ntiles = (total - a.wl.first + span - 1) / span;
   const int lane = threadIdx.x & 31;
-  for (int64_t tl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tl < ntiles;
-       tl += stride >> 5) {
+  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * a.wl.nshard + a.wl.shard;
+       tl < ntiles; tl += (stride >> 5) * a.wl.nshard) {
   const int64_t i0 = a.wl.first + tl * span + lane, i1 = a.wl.first + tl * span + span < total
                                                            ? a.wl.first + tl * span + span : total;
   if (i0 >= i1) continue;

@@ -41,6 +41,10 @@ struct BShape {
   static constexpr int G = G0 >= 1 ? (G0 > 16 ? 16 : G0) : 1;
   static constexpr int CHMAX = (BUDGET - FIXED - G * PER_G) / PER_C;
   static constexpr int CH = CHMAX >= NCD ? NCD : (CHMAX < 1 ? 1 : CHMAX);
+  // FP32 register path for step C: lane j-slot P = lane + 32 j holds W[cd][P]
+  // for every ket pair cd in registers, the cd loop unrolled at compile time
+  static constexpr int NPS = (HAB + 31) / 32;
+  static constexpr bool REGW = sizeof(T) == 4 && CH == NCD && NCD * NPS <= 64;
   static constexpr int SM_BOX = 0, SM_PING = SM_BOX + G * BOX, SM_SC = SM_PING + G * 2 * NPING,
                        SM_EK = SM_SC + G * NSC, SM_EB = SM_EK + G * 3 * NEK, SM_W = SM_EB + 3 * NEB,
                        SM_X = SM_W + CH * HABP, SM_TOTAL = SM_X + NAB * CH;
@@ -102,6 +106,9 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
     tab_lex[i] = (t + u <= LAB) ? lex_base(LAB, t, u) : 0;
   }
   __syncthreads();
+  int pslot[S::NPS];  // box offset of this lane's bra Hermite indices P = lane + 32 j
+#pragma unroll
+  for (int j = 0; j < S::NPS; ++j) pslot[j] = lane + 32 * j < HAB ? (tab_p[lane + 32 * j] & 0xffff) : 0;
   T* sm = reinterpret_cast<T*>(smraw + S::table_bytes()) + (size_t)wib * S::SM_TOTAL;
   T* boxes = sm + S::SM_BOX;
   T* pings = sm + S::SM_PING;
@@ -114,7 +121,8 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
   const int64_t total = a.wl.total;
   unsigned long long done = 0, doneq = 0, doneb = 0;
   const int64_t tile = a.wl.tile, ntiles = (total - a.wl.first + tile - 1) / tile;
-  for (int64_t tl = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; tl < ntiles; tl += nwarps) {
+  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * a.wl.nshard + a.wl.shard; tl < ntiles;
+       tl += nwarps * a.wl.nshard) {
   const int64_t i0 = a.wl.first + tl * tile, i1 = i0 + tile < total ? i0 + tile : total;
   BraCursor cur(a.wl, i0);
   for (int64_t item = i0; item < i1; ++item) {
@@ -148,7 +156,13 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
       for (int x = lane; x < NAB * CH; x += 32) Xs[x] = T(0);
       for (int pb = 0; pb < npb; ++pb) {
         for (int x = lane; x < 3 * NEB; x += 32) Eb[x] = ldE<T>(a.pd, eb0 + pb * 3 * NEB + x);
-        for (int x = lane; x < CH * HABP; x += 32) Ws[x] = T(0);
+        T wreg[S::REGW ? S::NPS * NCD : 1];
+        if constexpr (S::REGW) {
+#pragma unroll
+          for (int x = 0; x < S::NPS * NCD; ++x) wreg[x] = T(0);
+        } else {
+          for (int x = lane; x < CH * HABP; x += 32) Ws[x] = T(0);
+        }
         const int ipb = offb + pb;
         const T bp_p = pdv<T>(a.pd.p, a.pd.pf, ipb), bp_pref = pdv<T>(a.pd.pref, a.pd.preff, ipb);
         const T bPx = pdv<T>(a.pd.P, a.pd.Pf, ipb), bPy = pdv<T>(a.pd.P, a.pd.Pf, a.pd.n + ipb),
@@ -232,7 +246,50 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
             }
           }
           __syncwarp();
-          // step C: ket transform, items (ci, P)
+          // step C: ket transform
+          if constexpr (S::REGW) {
+            // lane-owned P, every cd unrolled: R read at a per-lane base plus
+            // compile-time offsets, E' broadcast, W accumulated in registers
+            for (int g = 0; g < ng; ++g) {
+              const T* ek = Ek + g * 3 * NEK;
+              const T* rbox = boxes + g * BOX;
+#pragma unroll
+              for (int kx = LC; kx >= 0; --kx)
+#pragma unroll
+                for (int ky = LC - kx; ky >= 0; --ky)
+#pragma unroll
+                  for (int lx = LD; lx >= 0; --lx)
+#pragma unroll
+                    for (int ly = LD - lx; ly >= 0; --ly) {
+                      const int kz = LC - kx - ky, lz = LD - lx - ly;
+                      const int icd = cidx(LC, ky, kz) * ND + cidx(LD, ly, lz);
+                      const T* ex = ek + (kx * (LD + 1) + lx) * (LCD + 1);
+                      const T* ey = ek + NEK + (ky * (LD + 1) + ly) * (LCD + 1);
+                      const T* ez = ek + 2 * NEK + (kz * (LD + 1) + lz) * (LCD + 1);
+#pragma unroll
+                      for (int j = 0; j < S::NPS; ++j) {
+                        if (j * 32 + 32 <= HAB || lane + 32 * j < HAB) {
+                          const T* r = rbox + pslot[j];
+                          T acc = T(0);
+#pragma unroll
+                          for (int sx = 0; sx <= kx + lx; ++sx) {
+                            T accy = T(0);
+#pragma unroll
+                            for (int sy = 0; sy <= ky + ly; ++sy) {
+                              T accz = T(0);
+#pragma unroll
+                              for (int sz = 0; sz <= kz + lz; ++sz)
+                                accz = fma(ez[sz], r[(sx * B + sy) * B + sz], accz);
+                              accy = fma(ey[sy], accz, accy);
+                            }
+                            acc = fma(ex[sx], accy, acc);
+                          }
+                          wreg[j * NCD + icd] += acc;
+                        }
+                      }
+                    }
+            }
+          } else {
           for (int it = lane; it < nci * HAB; it += 32) {
             const int ci = it / HAB, P = it - ci * HAB;
             const int c0w = tab_cd[2 * (c0 + ci)], c1w = tab_cd[2 * (c0 + ci) + 1];
@@ -257,6 +314,17 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
             }
             Ws[ci * HABP + (pw >> 16)] += acc;
           }
+          }
+          __syncwarp();
+        }
+        if constexpr (S::REGW) {
+#pragma unroll
+          for (int j = 0; j < S::NPS; ++j)
+            if (lane + 32 * j < HAB) {
+              const int slot = tab_p[lane + 32 * j] >> 16;
+#pragma unroll
+              for (int icd = 0; icd < NCD; ++icd) Ws[icd * HABP + slot] = wreg[j * NCD + icd];
+            }
           __syncwarp();
         }
         // step D: bra transform, items (ab, ci)

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(128) grad_warp_kernel(GradArgs a) {
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t total = a.wl.total;
   const int64_t tile = a.wl.tile, ntiles = (total - a.wl.first + tile - 1) / tile;
-  for (int64_t tl = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; tl < ntiles; tl += nwarps) {
+  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * a.wl.nshard + a.wl.shard; tl < ntiles;
+       tl += nwarps * a.wl.nshard) {
   const int64_t i0 = a.wl.first + tl * tile, i1 = i0 + tile < total ? i0 + tile : total;
   BraCursor cur(a.wl, i0);
   for (int64_t item = i0; item < i1; ++item) {

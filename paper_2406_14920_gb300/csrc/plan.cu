@@ -793,6 +793,8 @@ WorkList eri_plan_impl::klist(int X, int Y) const {
   WorkList w;
   w.first = 0;
   w.tile = 1;
+  w.shard = shard;
+  w.nshard = nshard;
   w.bra = d_sorted + h_coff[X];
   w.ket = d_sorted + h_coff[Y];
   w.kseg = d_segloc + Y;
@@ -806,6 +808,8 @@ WorkList eri_plan_impl::jlist(int X, int Y) const {
   WorkList w;
   w.first = 0;
   w.tile = 4;
+  w.shard = shard;
+  w.nshard = nshard;
   w.bra = d_sorted + h_coff[X];
   w.ket = d_sorted + h_coff[Y];
   w.kseg = d_segloc + Y;
@@ -1453,6 +1457,20 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
     P->gexec = nullptr;
   }
   return rc;
+}
+
+extern "C" int eri_plan_set_shard(eri_plan_t* plan, int32_t shard, int32_t nshard) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || nshard < 1 || shard < 0 || shard >= nshard) return ERI_EINVAL;
+  if (P->gexec && (shard != P->shard || nshard != P->nshard)) {  // captured builds carry the old share
+    CK(cudaSetDevice(P->device));
+    CK(cudaDeviceSynchronize());
+    CK(cudaGraphExecDestroy(P->gexec));
+    P->gexec = nullptr;
+  }
+  P->shard = shard;
+  P->nshard = nshard;
+  return ERI_OK;
 }
 
 extern "C" int eri_get_tiles(eri_plan_t* plan, int32_t* tiles) {

@@ -82,6 +82,9 @@ struct eri_plan_impl {
   // set by eri_autotune or eri_set_tiles; 0 = the built-in default
   int tile_k[eri::NPAIRCLASS * eri::NPAIRCLASS * 2] = {};
   int tile_for(int X, int Y, int tier) const;
+  // share of the work this plan computes (eri_plan_set_shard): tiles t of every
+  // class launch with t % nshard == shard; results are this share's partial sums
+  int shard = 0, nshard = 1;
 
   int alloc_pairs();
   int geometry(cudaStream_t s, bool rebuild_q);
