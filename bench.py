@@ -5,16 +5,20 @@ One step = one eri_build_jk (J and K) of the 60-atom / 900-basis-function
 workload (40 light atoms 2s1p, 20 heavy atoms 4s3p2d1f, seed 1001) with the
 Schwarz threshold 1e-12; D is already resident in HBM when the timed region
 starts.  The headline value is significant canonical shell quartets per second
-of the mixed-precision path (FP64 tier above tau = 1e-5, FP32 below).  The FP64
-path is timed on the same workload for the mixed-vs-FP64 comparison, and the
-energy error of the mixed path is measured against it.
+of the mixed-precision path (FP64 tier above tau, FP32 below), with work tiles
+picked by the library's autotuner before timing.  The same build replayed as a
+CUDA graph, the FP64 path, and an end-to-end step from pinned host memory are
+timed beside it; the energy error of the mixed path is measured against FP64.
+A batched leg times many molecules of the 64-molecule set in one plan (one
+CUDA-graph build per step) against one FP64 plan and build per molecule.
 
 --impl reference runs the oracle (plain FP64 CPU code) on seeded samples of the
 same quartet list, on the host cores, as the reference arm.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
-torch.distributed.run, every rank builds its own copy of the workload (weak
-scaling: independent problems, no collective on the data path).
+torch.distributed.run, the build is split over the GPUs (interleaved work
+tiles per GPU, eri_plan_set_shard) and the partial J and K are summed by one
+NCCL all-reduce inside every timed step (strong scaling of one build).
 """
 from __future__ import annotations
 
@@ -213,9 +217,30 @@ def run_ours(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    def timed(precision, steps, warmup):
+    def reduce_jk():
+        # the exchange step of a split build: sum all-reduce of the partial J and K
+        if world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(J)
+            dist.all_reduce(K)
+
+    # energies of both paths (untimed, whole build on every rank) for the accuracy claim
+    plan.build_jk(Dd, J, K, precision=eri.ERI_FP64)
+    e64 = plan.energy(Dd, J, K).cpu().numpy().copy()
+    plan.build_jk(Dd, J, K, precision=eri.ERI_MIXED)
+    emx = plan.energy(Dd, J, K).cpu().numpy().copy()
+    nq32 = plan.stats()["quartets_k_fp32"]
+    # work-tile autotuner (untimed set-up)
+    t0 = time.perf_counter()
+    plan.autotune(Dd, precision=eri.ERI_MIXED, trial_ms=args.tune_ms)
+    tune_s = time.perf_counter() - t0
+    if world > 1:
+        plan.set_shard(rank, world)
+
+    def timed(build, steps, warmup):
         for _ in range(warmup):
-            plan.build_jk(Dd, J, K, precision=precision)
+            build()
+            reduce_jk()
         torch.cuda.synchronize()
         plan.profile()  # drop warm-up records
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -224,25 +249,20 @@ def run_ours(args, rank, world, local_rank):
         for e0, e1 in ev:
             flush.fill_(1.0)
             e0.record(stream)
-            plan.build_jk(Dd, J, K, precision=precision)
+            build()
+            reduce_jk()
             e1.record(stream)
         torch.cuda.synchronize()
         barrier()
         ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
         return ms, plan.profile()
 
-    # energies of both paths (untimed) for the accuracy claim
-    plan.build_jk(Dd, J, K, precision=eri.ERI_FP64)
-    e64 = plan.energy(Dd, J, K).cpu().numpy().copy()
-    plan.build_jk(Dd, J, K, precision=eri.ERI_MIXED)
-    emx = plan.energy(Dd, J, K).cpu().numpy().copy()
-    nq32 = plan.stats()["quartets_k_fp32"]
-
     clocks = ClockSampler(local_rank)
     clocks.start()
-    ms_mixed, prof = timed(eri.ERI_MIXED, args.steps, args.warmup)
+    ms_mixed, prof = timed(lambda: plan.build_jk(Dd, J, K, precision=eri.ERI_MIXED), args.steps, args.warmup)
     clk = clocks.stop()
-    ms64, prof64 = timed(eri.ERI_FP64, args.fp64_steps, args.fp64_warmup)
+    ms_graph, _ = timed(lambda: plan.build_jk_graph(Dd, J, K, precision=eri.ERI_MIXED), args.steps, 2)
+    ms64, prof64 = timed(lambda: plan.build_jk(Dd, J, K, precision=eri.ERI_FP64), args.fp64_steps, args.fp64_warmup)
 
     # end to end through the public API: pinned host D in, J and K back to pinned host
     Dh = torch.from_numpy(D).pin_memory()
@@ -257,6 +277,7 @@ def run_ours(args, rank, world, local_rank):
         e0.record(stream)
         Dtmp.copy_(Dh, non_blocking=True)
         plan.build_jk(Dtmp, J, K, precision=eri.ERI_MIXED)
+        reduce_jk()
         Jh.copy_(J, non_blocking=True)
         Kh.copy_(K, non_blocking=True)
         e1.record(stream)
@@ -266,11 +287,11 @@ def run_ours(args, rank, world, local_rank):
     plan.profile()
 
     # max over ranks
-    vals = torch.tensor([ms_mixed, ms64, ms_e2e], dtype=torch.float64, device=dev)
+    vals = torch.tensor([ms_mixed, ms64, ms_e2e, ms_graph], dtype=torch.float64, device=dev)
     if world > 1:
         import torch.distributed as dist
         dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_mixed, ms64, ms_e2e = [float(v) for v in vals.cpu()]
+    ms_mixed, ms64, ms_e2e, ms_graph = [float(v) for v in vals.cpu()]
 
     # roofline of the dominant kernel (largest device-time share in the mixed step)
     dom = max(prof, key=lambda r: r["ms"])
@@ -299,15 +320,20 @@ def run_ours(args, rank, world, local_rank):
     launches_per_step = len(prof) + 4  # class launches + D scaling, D block maxima, two symmetrisations
 
     out = {
-        "metric": METRIC, "value": world * nq * args.steps / (ms_mixed * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": nq * args.steps / (ms_mixed * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed tiers)",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+        "dtype": "f64+f32 (mixed tiers)", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "nbf": n, "schwarz_thresh": THRESH, "mixed_tau": args.tau,
                    "quartets_per_step": nq, "fp32_quartets_per_step": nq32,
                    "l2": "flushed before every timed step (256 MiB device write)",
-                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
-        "fp64": {"ms_per_step": ms64 / args.fp64_steps, "value": world * nq * args.fp64_steps / (ms64 * 1e-3),
+                   "path": "eri_build_jk (class launches in order on one stream, per-launch events)",
+                   "tiles": f"autotuned ({tune_s:.1f} s, trial {args.tune_ms} ms)",
+                   "parallelism": (f"{world} GPUs: interleaved work tiles per GPU + sum all-reduce of J and K"
+                                   if world > 1 else "1 GPU")},
+        "graph": {"ms_per_step": ms_graph / args.steps, "value": nq * args.steps / (ms_graph * 1e-3),
+                  "path": "eri_build_jk_graph (one CUDA graph per build, class launches on 4 branches)"},
+        "fp64": {"ms_per_step": ms64 / args.fp64_steps, "value": nq * args.fp64_steps / (ms64 * 1e-3),
                  "steps": args.fp64_steps, "warmup": args.fp64_warmup},
         "speedup_mixed_vs_fp64": (ms64 / args.fp64_steps) / (ms_mixed / args.steps),
         "energy": {"E_J_fp64": float(e64[0]), "E_K_fp64": float(e64[1]),
@@ -318,19 +344,80 @@ def run_ours(args, rank, world, local_rank):
         "profile_top": profile_top,
         "fp64_profile_top": fp64_profile_top,
         "roofline": roofline,
-        "e2e": {"value": world * nq * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
+        "e2e": {"value": nq * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 16 * n * n},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    plan.close()
+    if rank == 0 and world == 1 and args.batch_mols > 0:
+        out["batch"] = run_batch(args, dev, flush)
     if rank == 0 and not args.no_cpu_baseline:
-        quartets = sample_quartets(plan.lists(), basis, 400000, seed=1234)
+        p2 = eri.Plan(basis, thresh=THRESH, device=local_rank)
+        quartets = sample_quartets(p2.lists(), basis, 400000, seed=1234)
+        p2.close()
         rate, ns, dt, cores = oracle_rate(basis, quartets, args.cpu_seconds)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{ns} seeded uniformly sampled significant canonical shell quartets of "
                                          f"this workload, contracted ERI blocks in FP64 ({dt:.1f} s)"}
-    plan.close()
     return out
+
+
+def run_batch(args, dev, flush):
+    """Batched leg: molecules of the 64-molecule set in one plan, mixed precision,
+    one CUDA-graph build per step, plus one batched gradient; against one FP64
+    plan and build per molecule (and one mixed plan per molecule)."""
+    import torch
+    import paper_2406_14920_gb300 as eri
+    import workloads as W
+    mols = W.workload(4)
+    order = sorted(range(len(mols)), key=lambda i: mols[i][0].nbf)[:args.batch_mols]
+    sel = [mols[i] for i in order]
+    plan = eri.Plan([b for b, _ in sel], thresh=THRESH, precision=eri.ERI_MIXED, mixed_tau=args.tau, device=dev.index)
+    Dp = plan.pack([torch.from_numpy(D) for _, D in sel]).to(dev)
+    J, K = torch.empty_like(Dp), torch.empty_like(Dp)
+    nq = plan.stats()["quartets_k"]
+    plan.autotune(Dp, precision=eri.ERI_MIXED, trial_ms=args.tune_ms)
+    stream = torch.cuda.current_stream(dev)
+
+    def tm(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms / steps
+
+    ms_b = tm(lambda: plan.build_jk_graph(Dp, J, K), args.batch_steps, 3)
+    Eb = plan.energy(Dp, J, K).cpu().numpy().reshape(-1, 2)
+    ms_g = tm(lambda: plan.grad(Dp), 1, 1)
+    plan.close()
+    ms64, ms_mx, errs = 0.0, 0.0, []
+    for m, (b, D) in enumerate(sel):
+        p = eri.Plan(b, thresh=THRESH, precision=eri.ERI_FP64, device=dev.index)
+        Dt = torch.from_numpy(D).to(dev)
+        J1, K1 = torch.empty_like(Dt), torch.empty_like(Dt)
+        ms64 += tm(lambda: p.build_jk(Dt, J1, K1, precision=eri.ERI_FP64), 1, 1)
+        # energy error of the batched mixed build against this molecule's FP64 build
+        errs.append(float(np.abs(Eb[m] - p.energy(Dt, J1, K1).cpu().numpy()).max()))
+        ms_mx += tm(lambda: p.build_jk(Dt, J1, K1, precision=eri.ERI_MIXED), 1, 1)
+        p.close()
+    return {"molecules": len(sel), "nbf": [b.nbf for b, _ in sel], "quartets_per_step": nq,
+            "sample": f"the {len(sel)} smallest of the 64 seeded molecules (workload seed 1004)",
+            "batched_mixed_graph": {"ms_per_step": ms_b, "value": nq / (ms_b * 1e-3), "unit": UNIT,
+                                    "steps": args.batch_steps},
+            "batched_gradient_ms": ms_g,
+            "per_molecule_fp64": {"ms_per_step": ms64, "value": nq / (ms64 * 1e-3), "unit": UNIT},
+            "per_molecule_mixed": {"ms_per_step": ms_mx, "value": nq / (ms_mx * 1e-3), "unit": UNIT},
+            "speedup_vs_per_molecule_fp64": ms64 / ms_b,
+            "max_abs_dE_vs_fp64": max(errs)}
 
 
 # ---------------------------------------------------------------------------
@@ -394,6 +481,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tau", type=float, default=TAU, help="FP32/FP64 tier threshold of the mixed path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-ms", type=float, default=2.0, help="autotuner trial length per candidate")
+    ap.add_argument("--batch-mols", type=int, default=12,
+                    help="molecules of the 64-molecule set in the batched leg (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--ncu-case", action="store_true",
                     help="small case for ncu section captures: the first 20 atoms of the workload, two mixed builds")
     args = ap.parse_args()

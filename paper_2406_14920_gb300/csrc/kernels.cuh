@@ -16,6 +16,7 @@ struct KArgs {
   BoysTabs bt;
   const RStep* rsteps;
   const double* Dp;   // density with component norms folded in (packed per molecule)
+  const float* Dpf;   // the same in FP32, read by the FP32 tier (no conversions on the FP64 pipe)
   double* Kh;         // half-K accumulator (packed per molecule)
   // precision tiers (mixed mode): a quartet is FP64 (tier 0) when
   // Q_ab Q_cd max|D'| >= tau over the six D blocks it touches, or when one of
@@ -53,6 +54,11 @@ __device__ __forceinline__ int quartet_tier(const KArgs& a, int mol, int pb_id, 
                     __ldg(a.prefmaxp + pb_id) * __ldg(a.prefmaxp + pk_id) > 1.0e18f;
   return (b >= a.tau || wide) ? 0 : 1;
 }
+
+// D' in the launch's precision
+template <typename T> __device__ __forceinline__ const T* dens(const KArgs& a);
+template <> __device__ __forceinline__ const double* dens<double>(const KArgs& a) { return a.Dp; }
+template <> __device__ __forceinline__ const float* dens<float>(const KArgs& a) { return a.Dpf; }
 
 struct JArgs {
   PairData pd;

@@ -266,7 +266,7 @@ template <int LA, int LB, int LC, int LD, typename T>
 __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w, int ao1, int ao2, int ao3, int ao4,
                                                int64_t base, int n) {
   using S = AShape<LA, LB, LC, LD>;
-  const double* Dp = A.k.Dp + base;
+  const T* Dp = dens<T>(A.k) + base;
   double* Kh = A.k.Kh ? A.k.Kh + base : nullptr;
   double* Jh = A.Jh ? A.Jh + base : nullptr;
   if (Kh) {
@@ -279,7 +279,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
         for (int ib = 0; ib < S::NB; ++ib)
 #pragma unroll
           for (int id = 0; id < S::ND; ++id)
-            s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], ldT<T>(Dp + (size_t)(ao2 + ib) * n + ao4 + id), s);
+            s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], __ldg(Dp + (size_t)(ao2 + ib) * n + ao4 + id), s);
         atomic_add_d(Kh + (size_t)(ao1 + ia) * n + ao3 + ic, (double)(w * s));
       }
 #pragma unroll
@@ -289,7 +289,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
         for (int ib = 0; ib < S::NB; ++ib)
 #pragma unroll
           for (int ic = 0; ic < S::NC; ++ic)
-            s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], ldT<T>(Dp + (size_t)(ao2 + ib) * n + ao3 + ic), s);
+            s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], __ldg(Dp + (size_t)(ao2 + ib) * n + ao3 + ic), s);
         atomic_add_d(Kh + (size_t)(ao1 + ia) * n + ao4 + id, (double)(w * s));
       }
     }
@@ -302,7 +302,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
         for (int ia = 0; ia < S::NA; ++ia)
 #pragma unroll
           for (int id = 0; id < S::ND; ++id)
-            s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], ldT<T>(Dp + (size_t)(ao1 + ia) * n + ao4 + id), s);
+            s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], __ldg(Dp + (size_t)(ao1 + ia) * n + ao4 + id), s);
         atomic_add_d(Kh + (size_t)(ao2 + ib) * n + ao3 + ic, (double)(w * s));
       }
 #pragma unroll
@@ -312,7 +312,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
         for (int ia = 0; ia < S::NA; ++ia)
 #pragma unroll
           for (int ic = 0; ic < S::NC; ++ic)
-            s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], ldT<T>(Dp + (size_t)(ao1 + ia) * n + ao3 + ic), s);
+            s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], __ldg(Dp + (size_t)(ao1 + ia) * n + ao3 + ic), s);
         atomic_add_d(Kh + (size_t)(ao2 + ib) * n + ao4 + id, (double)(w * s));
       }
     }
@@ -324,7 +324,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
       T s = T(0);
 #pragma unroll
       for (int icd = 0; icd < S::NCD; ++icd)
-        s = fma(X[iab * S::NCD + icd], ldT<T>(Dp + (size_t)(ao3 + icd / S::ND) * n + ao4 + icd % S::ND), s);
+        s = fma(X[iab * S::NCD + icd], __ldg(Dp + (size_t)(ao3 + icd / S::ND) * n + ao4 + icd % S::ND), s);
       atomic_add_d(Jh + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB, (double)(w2 * s));
     }
 #pragma unroll
@@ -332,7 +332,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
       T s = T(0);
 #pragma unroll
       for (int iab = 0; iab < S::NAB; ++iab)
-        s = fma(X[iab * S::NCD + icd], ldT<T>(Dp + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB), s);
+        s = fma(X[iab * S::NCD + icd], __ldg(Dp + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB), s);
       atomic_add_d(Jh + (size_t)(ao3 + icd / S::ND) * n + ao4 + icd % S::ND, (double)(w2 * s));
     }
   }

@@ -21,6 +21,15 @@
 #pragma once
 #include "kernels_a.cuh"
 
+// shared memory per warp (KB) of the warp kernel, per precision: FP64 keeps
+// 8 warps per SM (two resident 4-warp blocks), FP32 about 16-20
+#ifndef ERI_WARP_SMEM64_KB
+#define ERI_WARP_SMEM64_KB 22
+#endif
+#ifndef ERI_WARP_SMEM32_KB
+#define ERI_WARP_SMEM32_KB 12
+#endif
+
 namespace eri {
 
 template <int LA, int LB, int LC, int LD, typename T>
@@ -31,9 +40,9 @@ struct BShape {
   static constexpr int B = L + 1, BOX = B * B * B, NPING = L > 0 ? nherm(L - 1) : 1;
   static constexpr int NEB = (LA + 1) * (LB + 1) * (LAB + 1), NEK = (LC + 1) * (LD + 1) * (LCD + 1);
   static constexpr int NSC = L + 5;  // F'_0..F'_L, PQx, PQy, PQz, c
-  // shared memory per warp: FP64 needs only one warp per SM sub-partition to fill
-  // its pipe, FP32 needs many warps to hide latency
-  static constexpr int BUDGET = sizeof(T) == 8 ? (44 * 1024) / 8 : (12 * 1024) / 4;  // elements of T per warp
+  // shared memory per warp (elements of T): G ket primitives per batch and CH
+  // ket pairs per chunk are sized to fit it
+  static constexpr int BUDGET = sizeof(T) == 8 ? (ERI_WARP_SMEM64_KB * 1024) / 8 : (ERI_WARP_SMEM32_KB * 1024) / 4;
   static constexpr int FIXED = 3 * NEB;
   static constexpr int PER_G = BOX + 2 * NPING + NSC + 3 * NEK;
   static constexpr int PER_C = HABP + NAB;
@@ -147,7 +156,7 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
     if (pb_id == pk_id) w *= T(0.5);
     const int64_t mbase = __ldg(a.sp.mat_off + mol);
     const int n = __ldg(a.sp.mat_n + mol);
-    const double* Dp = a.Dp + mbase;
+    const T* Dp = dens<T>(a) + mbase;
     double* Kh = a.Kh ? a.Kh + mbase : nullptr;
     double* Jh = A.Jh ? A.Jh + mbase : nullptr;
 
@@ -365,9 +374,9 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
             const int ci = c * ND + d - c0;
             if (ci < 0 || ci >= nci) continue;
             if (isA) {
-              for (int b = 0; b < NB; ++b) s = fma(Xs[(r * NB + b) * CH + ci], ldT<T>(Dp + (size_t)(ao2 + b) * n + ao4 + d), s);
+              for (int b = 0; b < NB; ++b) s = fma(Xs[(r * NB + b) * CH + ci], __ldg(Dp + (size_t)(ao2 + b) * n + ao4 + d), s);
             } else {
-              for (int x = 0; x < NA; ++x) s = fma(Xs[(x * NB + r) * CH + ci], ldT<T>(Dp + (size_t)(ao1 + x) * n + ao4 + d), s);
+              for (int x = 0; x < NA; ++x) s = fma(Xs[(x * NB + r) * CH + ci], __ldg(Dp + (size_t)(ao1 + x) * n + ao4 + d), s);
             }
           }
           const int row = isA ? ao1 + r : ao2 + r;
@@ -383,9 +392,9 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
             const int ci = c * ND + d - c0;
             if (ci < 0 || ci >= nci) continue;
             if (isA) {
-              for (int b = 0; b < NB; ++b) s = fma(Xs[(r * NB + b) * CH + ci], ldT<T>(Dp + (size_t)(ao2 + b) * n + ao3 + c), s);
+              for (int b = 0; b < NB; ++b) s = fma(Xs[(r * NB + b) * CH + ci], __ldg(Dp + (size_t)(ao2 + b) * n + ao3 + c), s);
             } else {
-              for (int x = 0; x < NA; ++x) s = fma(Xs[(x * NB + r) * CH + ci], ldT<T>(Dp + (size_t)(ao1 + x) * n + ao3 + c), s);
+              for (int x = 0; x < NA; ++x) s = fma(Xs[(x * NB + r) * CH + ci], __ldg(Dp + (size_t)(ao1 + x) * n + ao3 + c), s);
             }
           }
           const int row = isA ? ao1 + r : ao2 + r;
@@ -398,14 +407,14 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
           T s = T(0);
           for (int ci = 0; ci < nci; ++ci) {
             const int cd = c0 + ci;
-            s = fma(Xs[iab * CH + ci], ldT<T>(Dp + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND), s);
+            s = fma(Xs[iab * CH + ci], __ldg(Dp + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND), s);
           }
           atomic_add_d(Jh + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB, (double)(w2 * s));
         }
         for (int ci = lane; ci < nci; ci += 32) {  // Jh_cd += 2w sum_ab X D_ab
           T s = T(0);
           for (int iab = 0; iab < NAB; ++iab)
-            s = fma(Xs[iab * CH + ci], ldT<T>(Dp + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB), s);
+            s = fma(Xs[iab * CH + ci], __ldg(Dp + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB), s);
           const int cd = c0 + ci;
           atomic_add_d(Jh + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND, (double)(w2 * s));
         }

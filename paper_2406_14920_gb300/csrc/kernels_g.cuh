@@ -94,7 +94,7 @@ struct GShape {
   static constexpr int NTB = LAB + 2;
   static constexpr int NEB = (LA + 1) * (LB + 1) * NTB, NEK = (LC + 1) * (LD + 1) * (LCD + 1);
   static constexpr int NSC = L1 + 5;
-  static constexpr int BUDGET = (44 * 1024) / 8;
+  static constexpr int BUDGET = (ERI_WARP_SMEM64_KB * 1024) / 8;
   static constexpr int FIXED = 9 * NEB;  // E, GA, GB per direction
   static constexpr int PER_G = BOX + 2 * NPING + NSC + 3 * NEK;
   static constexpr int PER_C = HAB1P;

@@ -486,13 +486,15 @@ struct MolMats {
 
 // D' = D f f (component norms folded in); grid (x, molecule)
 __global__ void k_scale_d(MolMats mm, const double* __restrict__ D, const double* __restrict__ f,
-                          double* __restrict__ Dp) {
+                          double* __restrict__ Dp, float* __restrict__ Dpf) {
   const int m = blockIdx.y, n = mm.n[m];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)n * n) return;
   const int64_t o = mm.off[m] + i;
   const int a0 = mm.aobase[m];
-  Dp[o] = D[o] * f[a0 + i / n] * f[a0 + i % n];
+  const double v = D[o] * f[a0 + i / n] * f[a0 + i % n];
+  Dp[o] = v;
+  if (Dpf) Dpf[o] = (float)v;
 }
 
 // Hermite density per primitive pair (Eq. j_formula, first sub-step):
@@ -825,7 +827,7 @@ void eri_plan_impl::release() {
                   d_PBf, d_preff, d_Q, d_qmax, d_sig, d_ccount, d_coff, d_sorted, d_pos, d_counts, d_koff, d_joff,
                   d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Jh, d_Dherm,
                   d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp, d_ea,
-                  d_mat_off, d_mat_n, d_aobase, d_pbase, d_pmol, d_shloc, d_ccm, d_segloc};
+                  d_mat_off, d_mat_n, d_aobase, d_pbase, d_pmol, d_shloc, d_ccm, d_segloc, d_Dpf};
   for (auto& e : prof_events) cudaEventDestroy(e);
   prof_events.clear();
   if (gexec) cudaGraphExecDestroy(gexec);
@@ -1108,7 +1110,8 @@ static int plan_create(int nmol, const eri_basis_t* const* bases, const double* 
     CKP(dalloc(&P->d_dmax, npair));
     CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3));
     CKP(dalloc(&P->d_rsteps, st.size()));
-    CKP(dalloc(&P->d_Dp, (size_t)P->nmat)); CKP(dalloc(&P->d_Kh, (size_t)P->nmat));
+    CKP(dalloc(&P->d_Dp, (size_t)P->nmat)); CKP(dalloc(&P->d_Dpf, (size_t)P->nmat));
+    CKP(dalloc(&P->d_Kh, (size_t)P->nmat));
     CKP(dalloc(&P->d_Jh, (size_t)P->nmat));
     CKP(dalloc(&P->d_Dherm, nherm_tot)); CKP(dalloc(&P->d_Jherm, nherm_tot));
     CKP(dalloc(&P->d_status, 1));
@@ -1179,7 +1182,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
                       bool concurrent) {
   const int64_t nn = P->nmat;
   const MolMats mm = molmats(P);
-  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, P->d_Dp);
+  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, P->d_Dp, P->d_Dpf);
   CK(cudaGetLastError());
   const bool jengine = J && !K && P->opts.j_engine;
   if (jengine) {
@@ -1240,7 +1243,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
     JKArgs ja;
     KArgs& ka = ja.k;
     ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
-    ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Kh = K ? P->d_Kh : nullptr;
+    ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Dpf = P->d_Dpf; ka.Kh = K ? P->d_Kh : nullptr;
     ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
     ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
     ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
@@ -1377,7 +1380,7 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
   CK(cudaSetDevice(P->device));
   const bool mixed = precision == ERI_MIXED;
   const MolMats mm = molmats(P);
-  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, P->d_Dp);
+  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, P->d_Dp, P->d_Dpf);
   if (mixed)
     k_dmax<<<grid1(P->npair, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_sh_l, P->d_pao1, P->d_pao2,
                                                 P->d_pmol, P->d_mat_off, P->d_mat_n, P->d_Dp, P->d_dmax);
@@ -1385,7 +1388,7 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
   JKArgs ja;
   KArgs& ka = ja.k;
   ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
-  ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Kh = P->d_Kh;
+  ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Dpf = P->d_Dpf; ka.Kh = P->d_Kh;
   ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
   ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
   ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
@@ -1507,14 +1510,14 @@ int eri_build_jk_scratch(eri_plan_t* plan, const double* D, double* J, double* K
   eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
   const int64_t nn = P->nmat;
   const MolMats mm = molmats(P);
-  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, Dp);
+  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, Dp, nullptr);
   CK(cudaGetLastError());
   if (K) CK(cudaMemsetAsync(Kh, 0, sizeof(double) * nn, s));
   if (J) CK(cudaMemsetAsync(Jh, 0, sizeof(double) * nn, s));
   JKArgs ja;
   KArgs& ka = ja.k;
   ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
-  ka.rsteps = P->d_rsteps; ka.Dp = Dp; ka.Kh = K ? Kh : nullptr;
+  ka.rsteps = P->d_rsteps; ka.Dp = Dp; ka.Dpf = nullptr; ka.Kh = K ? Kh : nullptr;
   ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
   ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
   ka.tau = 0.0f; ka.pmax32 = 0.0f; ka.mixed = 0; ka.tier_want = 0; ka.counter = nullptr;
@@ -1578,7 +1581,7 @@ extern "C" int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int3
   if (!P || !D || !dEdR) return ERI_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(P->device));
-  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(molmats(P), D, P->d_f, P->d_Dp);
+  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(molmats(P), D, P->d_f, P->d_Dp, nullptr);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(dEdR, 0, sizeof(double) * 3 * P->natom, s));
   if (!want_j && !want_k) return ERI_OK;

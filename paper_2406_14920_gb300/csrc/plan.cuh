@@ -54,6 +54,7 @@ struct eri_plan_impl {
   float* d_Ef = nullptr;
   eri::RStep* d_rsteps = nullptr;
   // per-build workspace
+  float* d_Dpf = nullptr;  // D' in FP32 for the FP32 tier
   double *d_Dp = nullptr, *d_Kh = nullptr, *d_Jh = nullptr, *d_Dherm = nullptr, *d_Jherm = nullptr;
   int* d_status = nullptr;
   float *d_pmaxp = nullptr, *d_dmax = nullptr, *d_prefmaxp = nullptr;
