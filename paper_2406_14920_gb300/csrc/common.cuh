@@ -10,6 +10,8 @@
 //   - ERI assembly Eq. eri_formula (two transforms: ket then bra).
 #pragma once
 #include <cstdint>
+#include <type_traits>
+#include <utility>
 #include <cuda_runtime.h>
 
 namespace eri {
@@ -46,6 +48,80 @@ __host__ __device__ constexpr void cart_xyz(int l, int k, int& x, int& y, int& z
 }
 
 // position of component (l-y-z, y, z) inside shell l (loop-free)
+// Compile-time loop: f(std::integral_constant<int, i>) for i = 0 .. N-1.  Every
+// index is a constant expression inside f (usable in `if constexpr` and as a
+// register-array index), independent of the compiler's unrolling heuristics.
+template <typename F, int... I>
+__device__ __forceinline__ void sfor_seq(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void sfor(F&& f) {
+  if constexpr (N > 0) sfor_seq(f, std::make_integer_sequence<int, N>{});
+}
+#define ERI_CI(x) decltype(x)::value
+
+// sum_{x <= NX, y <= NY, z <= NZ} cx[x] cy[y] cz[z] v(x, y, z), factored as
+// sum_x cx[x] (sum_y cy[y] (sum_z cz[z] v)).  A direction with N = 0 has the
+// single Hermite coefficient E^{00}_0 = 1 (the exponential factor lives in the
+// pair prefactor), so it contributes no multiplication.  ALT: coefficient of
+// index s carries (-1)^s (the ket sign of Eq. eri_formula).
+template <int NX, int NY, int NZ, bool ALT, typename T, typename V>
+__device__ __forceinline__ T tsum(const T* cx, const T* cy, const T* cz, V&& v) {
+  T acc = T(0);
+  sfor<NX + 1>([&](auto ix) {
+    constexpr int x = ERI_CI(ix);
+    T accy = T(0);
+    sfor<NY + 1>([&](auto iy) {
+      constexpr int y = ERI_CI(iy);
+      T accz = T(0);
+      sfor<NZ + 1>([&](auto iz) {
+        constexpr int z = ERI_CI(iz);
+        const T val = v(std::integral_constant<int, x>{}, std::integral_constant<int, y>{},
+                        std::integral_constant<int, z>{});
+        if constexpr (NZ == 0) accz = val;
+        else if constexpr (ALT && (z & 1)) accz = fma(-cz[z], val, accz);
+        else accz = fma(cz[z], val, accz);
+      });
+      if constexpr (NY == 0) accy = accz;
+      else if constexpr (ALT && (y & 1)) accy = fma(-cy[y], accz, accy);
+      else accy = fma(cy[y], accz, accy);
+    });
+    if constexpr (NX == 0) acc = accy;
+    else if constexpr (ALT && (x & 1)) acc = fma(-cx[x], accy, acc);
+    else acc = fma(cx[x], accy, acc);
+  });
+  return acc;
+}
+
+// f(x, y, z) (integral constants) for every Cartesian component of angular
+// momentum L, in the lexicographic order (x descending, then y descending)
+template <int L, typename F>
+__device__ __forceinline__ void for_cart(F&& f) {
+  sfor<L + 1>([&](auto a) {
+    constexpr int x = L - ERI_CI(a);
+    sfor<L - x + 1>([&](auto b) {
+      constexpr int y = L - x - ERI_CI(b);
+      f(std::integral_constant<int, x>{}, std::integral_constant<int, y>{}, std::integral_constant<int, L - x - y>{});
+    });
+  });
+}
+
+// f(t, u, v) (integral constants) for every Hermite index with t + u + v <= L
+template <int L, typename F>
+__device__ __forceinline__ void for_herm(F&& f) {
+  sfor<L + 1>([&](auto a) {
+    constexpr int t = ERI_CI(a);
+    sfor<L - t + 1>([&](auto b) {
+      constexpr int u = ERI_CI(b);
+      sfor<L - t - u + 1>([&](auto c) {
+        f(std::integral_constant<int, t>{}, std::integral_constant<int, u>{},
+          std::integral_constant<int, ERI_CI(c)>{});
+      });
+    });
+  });
+}
+
 __host__ __device__ constexpr int cidx(int l, int y, int z) {
   return (y + z) * (y + z + 1) / 2 + z + 0 * l;
 }

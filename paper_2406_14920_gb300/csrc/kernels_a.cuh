@@ -57,6 +57,16 @@ __device__ __forceinline__ void load_or_build_e(const PairData& pd, int e0, int 
   }
 }
 
+// Ket transform of one primitive quartet for one ket pair cd (compile-time
+// exponents), one bra Hermite index P = (t, u, v):
+//   sum_Q (-1)^|Q| E_Q^{cd} R_{P+Q}
+template <int L, int KX, int KY, int KZ, int T_, int U_, int V_, typename T>
+__device__ __forceinline__ T ket_term(const T* ex, const T* ey, const T* ez, const T* R) {
+  return tsum<KX, KY, KZ, true>(ex, ey, ez, [&](auto sx, auto sy, auto sz) {
+    return R[herm_index(T_ + ERI_CI(sx), U_ + ERI_CI(sy), V_ + ERI_CI(sz))];
+  });
+}
+
 // Variant for classes whose W (all ket pairs) does not fit in registers: the
 // bra transform runs per primitive quartet, one ket pair cd at a time.
 template <int LA, int LB, int LC, int LD, typename T>
@@ -84,73 +94,33 @@ __device__ __forceinline__ void eri_block_reg_pq(const KArgs& a, int offb, int n
       const T pref = bp.pref * kp.pref * rsqrt_t(ps);
       T R[S::NR];
       r_build_reg<L, T>(F, pref, PQx, PQy, PQz, T(-2) * rho, R);
-#pragma unroll
-      for (int kx = LC; kx >= 0; --kx)
-#pragma unroll
-        for (int ky = LC - kx; ky >= 0; --ky)
-#pragma unroll
-          for (int lx = LD; lx >= 0; --lx)
-#pragma unroll
-            for (int ly = LD - lx; ly >= 0; --ly) {
-              const int kz = LC - kx - ky, lz = LD - lx - ly;
-              const int icd = cidx(LC, ky, kz) * S::ND + cidx(LD, ly, lz);
-              const T* ex = ek + 0 * S::NEK + (kx * (LD + 1) + lx) * (LCD + 1);
-              const T* ey = ek + 1 * S::NEK + (ky * (LD + 1) + ly) * (LCD + 1);
-              const T* ez = ek + 2 * S::NEK + (kz * (LD + 1) + lz) * (LCD + 1);
-              T W[S::HAB];
-#pragma unroll
-              for (int t = LAB; t >= 0; --t)
-#pragma unroll
-                for (int u = LAB - t; u >= 0; --u)
-#pragma unroll
-                  for (int v = LAB - t - u; v >= 0; --v) {
-                    T acc = T(0);
-#pragma unroll
-                    for (int sx = 0; sx <= kx + lx; ++sx) {
-                      T accy = T(0);
-#pragma unroll
-                      for (int sy = 0; sy <= ky + ly; ++sy) {
-                        T accz = T(0);
-#pragma unroll
-                        for (int sz = 0; sz <= kz + lz; ++sz) {
-                          const T r = R[herm_index(t + sx, u + sy, v + sz)];
-                          accz = (sz & 1) ? fma(-ez[sz], r, accz) : fma(ez[sz], r, accz);
-                        }
-                        accy = (sy & 1) ? fma(-ey[sy], accz, accy) : fma(ey[sy], accz, accy);
-                      }
-                      acc = (sx & 1) ? fma(-ex[sx], accy, acc) : fma(ex[sx], accy, acc);
-                    }
-                    W[herm_index(t, u, v)] = acc;
-                  }
-#pragma unroll
-              for (int ix = LA; ix >= 0; --ix)
-#pragma unroll
-                for (int iy = LA - ix; iy >= 0; --iy)
-#pragma unroll
-                  for (int jx = LB; jx >= 0; --jx)
-#pragma unroll
-                    for (int jy = LB - jx; jy >= 0; --jy) {
-                      const int iz = LA - ix - iy, jz = LB - jx - jy;
-                      const int iab = cidx(LA, iy, iz) * S::NB + cidx(LB, jy, jz);
-                      const T* fx = eb + 0 * S::NEB + (ix * (LB + 1) + jx) * (LAB + 1);
-                      const T* fy = eb + 1 * S::NEB + (iy * (LB + 1) + jy) * (LAB + 1);
-                      const T* fz = eb + 2 * S::NEB + (iz * (LB + 1) + jz) * (LAB + 1);
-                      T acc = T(0);
-#pragma unroll
-                      for (int tx = 0; tx <= ix + jx; ++tx) {
-                        T accy = T(0);
-#pragma unroll
-                        for (int ty = 0; ty <= iy + jy; ++ty) {
-                          T accz = T(0);
-#pragma unroll
-                          for (int tz = 0; tz <= iz + jz; ++tz) accz = fma(fz[tz], W[herm_index(tx, ty, tz)], accz);
-                          accy = fma(fy[ty], accz, accy);
-                        }
-                        acc = fma(fx[tx], accy, acc);
-                      }
-                      X[iab * S::NCD + icd] += acc;
-                    }
-            }
+      for_cart<LC>([&](auto kx, auto ky, auto kz) {
+        for_cart<LD>([&](auto lx, auto ly, auto lz) {
+          constexpr int KX = ERI_CI(kx), KY = ERI_CI(ky), KZ = ERI_CI(kz);
+          constexpr int LX = ERI_CI(lx), LY = ERI_CI(ly), LZ = ERI_CI(lz);
+          constexpr int icd = cidx(LC, KY, KZ) * S::ND + cidx(LD, LY, LZ);
+          const T* ex = ek + 0 * S::NEK + (KX * (LD + 1) + LX) * (LCD + 1);
+          const T* ey = ek + 1 * S::NEK + (KY * (LD + 1) + LY) * (LCD + 1);
+          const T* ez = ek + 2 * S::NEK + (KZ * (LD + 1) + LZ) * (LCD + 1);
+          T W[S::HAB];
+          for_herm<LAB>([&](auto t, auto u, auto v) {
+            W[herm_index(ERI_CI(t), ERI_CI(u), ERI_CI(v))] =
+                ket_term<L, KX + LX, KY + LY, KZ + LZ, ERI_CI(t), ERI_CI(u), ERI_CI(v)>(ex, ey, ez, R);
+          });
+          for_cart<LA>([&](auto ix, auto iy, auto iz) {
+            for_cart<LB>([&](auto jx, auto jy, auto jz) {
+              constexpr int IX = ERI_CI(ix), IY = ERI_CI(iy), IZ = ERI_CI(iz);
+              constexpr int JX = ERI_CI(jx), JY = ERI_CI(jy), JZ = ERI_CI(jz);
+              constexpr int iab = cidx(LA, IY, IZ) * S::NB + cidx(LB, JY, JZ);
+              const T* fx = eb + 0 * S::NEB + (IX * (LB + 1) + JX) * (LAB + 1);
+              const T* fy = eb + 1 * S::NEB + (IY * (LB + 1) + JY) * (LAB + 1);
+              const T* fz = eb + 2 * S::NEB + (IZ * (LB + 1) + JZ) * (LAB + 1);
+              X[iab * S::NCD + icd] += tsum<IX + JX, IY + JY, IZ + JZ, false>(
+                  fx, fy, fz, [&](auto tx, auto ty, auto tz) { return W[herm_index(ERI_CI(tx), ERI_CI(ty), ERI_CI(tz))]; });
+            });
+          });
+        });
+      });
     }
   }
 }
@@ -181,81 +151,39 @@ __device__ __forceinline__ void eri_block_reg(const KArgs& a, int offb, int npb,
       const T pref = bp.pref * kp.pref * rsqrt_t(ps);
       T R[S::NR];
       r_build_reg<L, T>(F, pref, PQx, PQy, PQz, T(-2) * rho, R);
-      // component loops are nested exponent loops (x desc, then y desc, i.e. the
-      // lexicographic component order), so every index is compile-time arithmetic
-#pragma unroll
-      for (int kx = LC; kx >= 0; --kx)
-#pragma unroll
-        for (int ky = LC - kx; ky >= 0; --ky)
-#pragma unroll
-          for (int lx = LD; lx >= 0; --lx)
-#pragma unroll
-            for (int ly = LD - lx; ly >= 0; --ly) {
-              const int kz = LC - kx - ky, lz = LD - lx - ly;
-              const int icd = cidx(LC, ky, kz) * S::ND + cidx(LD, ly, lz);
-              const T* ex = ek + 0 * S::NEK + (kx * (LD + 1) + lx) * (LCD + 1);
-              const T* ey = ek + 1 * S::NEK + (ky * (LD + 1) + ly) * (LCD + 1);
-              const T* ez = ek + 2 * S::NEK + (kz * (LD + 1) + lz) * (LCD + 1);
-#pragma unroll
-              for (int t = LAB; t >= 0; --t)
-#pragma unroll
-                for (int u = LAB - t; u >= 0; --u)
-#pragma unroll
-                  for (int v = LAB - t - u; v >= 0; --v) {
-                    T acc = T(0);
-#pragma unroll
-                    for (int sx = 0; sx <= kx + lx; ++sx) {
-                      T accy = T(0);
-#pragma unroll
-                      for (int sy = 0; sy <= ky + ly; ++sy) {
-                        T accz = T(0);
-#pragma unroll
-                        for (int sz = 0; sz <= kz + lz; ++sz) {
-                          const T r = R[herm_index(t + sx, u + sy, v + sz)];
-                          accz = (sz & 1) ? fma(-ez[sz], r, accz) : fma(ez[sz], r, accz);  // (-1)^s
-                        }
-                        accy = (sy & 1) ? fma(-ey[sy], accz, accy) : fma(ey[sy], accz, accy);
-                      }
-                      acc = (sx & 1) ? fma(-ex[sx], accy, acc) : fma(ex[sx], accy, acc);
-                    }
-                    W[icd * S::HAB + herm_index(t, u, v)] += acc;
-                  }
-            }
+      for_cart<LC>([&](auto kx, auto ky, auto kz) {
+        for_cart<LD>([&](auto lx, auto ly, auto lz) {
+          constexpr int KX = ERI_CI(kx), KY = ERI_CI(ky), KZ = ERI_CI(kz);
+          constexpr int LX = ERI_CI(lx), LY = ERI_CI(ly), LZ = ERI_CI(lz);
+          constexpr int icd = cidx(LC, KY, KZ) * S::ND + cidx(LD, LY, LZ);
+          const T* ex = ek + 0 * S::NEK + (KX * (LD + 1) + LX) * (LCD + 1);
+          const T* ey = ek + 1 * S::NEK + (KY * (LD + 1) + LY) * (LCD + 1);
+          const T* ez = ek + 2 * S::NEK + (KZ * (LD + 1) + LZ) * (LCD + 1);
+          for_herm<LAB>([&](auto t, auto u, auto v) {
+            W[icd * S::HAB + herm_index(ERI_CI(t), ERI_CI(u), ERI_CI(v))] +=
+                ket_term<L, KX + LX, KY + LY, KZ + LZ, ERI_CI(t), ERI_CI(u), ERI_CI(v)>(ex, ey, ez, R);
+          });
+        });
+      });
     }
     T eb[3 * S::NEB];
     load_or_build_e<LA, LB, T>(a.pd, eb0 + pb * 3 * S::NEB, offb + pb, eb);
-#pragma unroll
-    for (int icd = 0; icd < S::NCD; ++icd) {
-#pragma unroll
-      for (int ix = LA; ix >= 0; --ix)
-#pragma unroll
-        for (int iy = LA - ix; iy >= 0; --iy)
-#pragma unroll
-          for (int jx = LB; jx >= 0; --jx)
-#pragma unroll
-            for (int jy = LB - jx; jy >= 0; --jy) {
-              const int iz = LA - ix - iy, jz = LB - jx - jy;
-              const int iab = cidx(LA, iy, iz) * S::NB + cidx(LB, jy, jz);
-              const T* fx = eb + 0 * S::NEB + (ix * (LB + 1) + jx) * (LAB + 1);
-              const T* fy = eb + 1 * S::NEB + (iy * (LB + 1) + jy) * (LAB + 1);
-              const T* fz = eb + 2 * S::NEB + (iz * (LB + 1) + jz) * (LAB + 1);
-              T acc = T(0);
-#pragma unroll
-              for (int tx = 0; tx <= ix + jx; ++tx) {
-                T accy = T(0);
-#pragma unroll
-                for (int ty = 0; ty <= iy + jy; ++ty) {
-                  T accz = T(0);
-#pragma unroll
-                  for (int tz = 0; tz <= iz + jz; ++tz)
-                    accz = fma(fz[tz], W[icd * S::HAB + herm_index(tx, ty, tz)], accz);
-                  accy = fma(fy[ty], accz, accy);
-                }
-                acc = fma(fx[tx], accy, acc);
-              }
-              X[iab * S::NCD + icd] += acc;
-            }
-    }
+    sfor<S::NCD>([&](auto icd_) {
+      constexpr int icd = ERI_CI(icd_);
+      for_cart<LA>([&](auto ix, auto iy, auto iz) {
+        for_cart<LB>([&](auto jx, auto jy, auto jz) {
+          constexpr int IX = ERI_CI(ix), IY = ERI_CI(iy), IZ = ERI_CI(iz);
+          constexpr int JX = ERI_CI(jx), JY = ERI_CI(jy), JZ = ERI_CI(jz);
+          constexpr int iab = cidx(LA, IY, IZ) * S::NB + cidx(LB, JY, JZ);
+          const T* fx = eb + 0 * S::NEB + (IX * (LB + 1) + JX) * (LAB + 1);
+          const T* fy = eb + 1 * S::NEB + (IY * (LB + 1) + JY) * (LAB + 1);
+          const T* fz = eb + 2 * S::NEB + (IZ * (LB + 1) + JZ) * (LAB + 1);
+          X[iab * S::NCD + icd] += tsum<IX + JX, IY + JY, IZ + JZ, false>(
+              fx, fy, fz,
+              [&](auto tx, auto ty, auto tz) { return W[icd * S::HAB + herm_index(ERI_CI(tx), ERI_CI(ty), ERI_CI(tz))]; });
+        });
+      });
+    });
   }
 }
 

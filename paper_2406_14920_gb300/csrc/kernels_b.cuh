@@ -29,6 +29,10 @@
 #ifndef ERI_WARP_SMEM32_KB
 #define ERI_WARP_SMEM32_KB 12
 #endif
+// FP64 also takes the lane-owned-P ket transform where W fits in registers
+#ifndef ERI_REGW64
+#define ERI_REGW64 1
+#endif
 
 namespace eri {
 
@@ -53,7 +57,7 @@ struct BShape {
   // FP32 register path for step C: lane j-slot P = lane + 32 j holds W[cd][P]
   // for every ket pair cd in registers, the cd loop unrolled at compile time
   static constexpr int NPS = (HAB + 31) / 32;
-  static constexpr bool REGW = sizeof(T) == 4 && CH == NCD && NCD * NPS <= 64;
+  static constexpr bool REGW = CH == NCD && (sizeof(T) == 4 ? NCD * NPS <= 64 : (ERI_REGW64 && NCD * NPS <= 32));
   static constexpr int SM_BOX = 0, SM_PING = SM_BOX + G * BOX, SM_SC = SM_PING + G * 2 * NPING,
                        SM_EK = SM_SC + G * NSC, SM_EB = SM_EK + G * 3 * NEK, SM_W = SM_EB + 3 * NEB,
                        SM_X = SM_W + CH * HABP, SM_TOTAL = SM_X + NAB * CH;
@@ -262,41 +266,26 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
             for (int g = 0; g < ng; ++g) {
               const T* ek = Ek + g * 3 * NEK;
               const T* rbox = boxes + g * BOX;
-#pragma unroll
-              for (int kx = LC; kx >= 0; --kx)
-#pragma unroll
-                for (int ky = LC - kx; ky >= 0; --ky)
-#pragma unroll
-                  for (int lx = LD; lx >= 0; --lx)
-#pragma unroll
-                    for (int ly = LD - lx; ly >= 0; --ly) {
-                      const int kz = LC - kx - ky, lz = LD - lx - ly;
-                      const int icd = cidx(LC, ky, kz) * ND + cidx(LD, ly, lz);
-                      const T* ex = ek + (kx * (LD + 1) + lx) * (LCD + 1);
-                      const T* ey = ek + NEK + (ky * (LD + 1) + ly) * (LCD + 1);
-                      const T* ez = ek + 2 * NEK + (kz * (LD + 1) + lz) * (LCD + 1);
-#pragma unroll
-                      for (int j = 0; j < S::NPS; ++j) {
-                        if (j * 32 + 32 <= HAB || lane + 32 * j < HAB) {
-                          const T* r = rbox + pslot[j];
-                          T acc = T(0);
-#pragma unroll
-                          for (int sx = 0; sx <= kx + lx; ++sx) {
-                            T accy = T(0);
-#pragma unroll
-                            for (int sy = 0; sy <= ky + ly; ++sy) {
-                              T accz = T(0);
-#pragma unroll
-                              for (int sz = 0; sz <= kz + lz; ++sz)
-                                accz = fma(ez[sz], r[(sx * B + sy) * B + sz], accz);
-                              accy = fma(ey[sy], accz, accy);
-                            }
-                            acc = fma(ex[sx], accy, acc);
-                          }
-                          wreg[j * NCD + icd] += acc;
-                        }
-                      }
+              for_cart<LC>([&](auto kx, auto ky, auto kz) {
+                for_cart<LD>([&](auto lx, auto ly, auto lz) {
+                  constexpr int KX = ERI_CI(kx), KY = ERI_CI(ky), KZ = ERI_CI(kz);
+                  constexpr int LX = ERI_CI(lx), LY = ERI_CI(ly), LZ = ERI_CI(lz);
+                  constexpr int icd = cidx(LC, KY, KZ) * ND + cidx(LD, LY, LZ);
+                  const T* ex = ek + (KX * (LD + 1) + LX) * (LCD + 1);
+                  const T* ey = ek + NEK + (KY * (LD + 1) + LY) * (LCD + 1);
+                  const T* ez = ek + 2 * NEK + (KZ * (LD + 1) + LZ) * (LCD + 1);
+                  sfor<S::NPS>([&](auto j_) {
+                    constexpr int j = ERI_CI(j_);
+                    if (j * 32 + 32 <= HAB || lane + 32 * j < HAB) {
+                      const T* r = rbox + pslot[j];
+                      wreg[j * NCD + icd] += tsum<KX + LX, KY + LY, KZ + LZ, false>(
+                          ex, ey, ez, [&](auto sx, auto sy, auto sz) {
+                            return r[(ERI_CI(sx) * B + ERI_CI(sy)) * B + ERI_CI(sz)];
+                          });
                     }
+                  });
+                });
+              });
             }
           } else {
           for (int it = lane; it < nci * HAB; it += 32) {
