@@ -232,7 +232,7 @@ def run_ours(args, rank, world, local_rank):
     nq32 = plan.stats()["quartets_k_fp32"]
     # work-tile autotuner (untimed set-up)
     t0 = time.perf_counter()
-    plan.autotune(Dd, precision=eri.ERI_MIXED, trial_ms=args.tune_ms)
+    plan.autotune(Dd, precision=eri.ERI_MIXED, trial_ms=args.tune_ms, cache=args.tune_cache)
     tune_s = time.perf_counter() - t0
     if world > 1:
         plan.set_shard(rank, world)
@@ -328,7 +328,8 @@ def run_ours(args, rank, world, local_rank):
                    "quartets_per_step": nq, "fp32_quartets_per_step": nq32,
                    "l2": "flushed before every timed step (256 MiB device write)",
                    "path": "eri_build_jk (class launches in order on one stream, per-launch events)",
-                   "tiles": f"autotuned ({tune_s:.1f} s, trial {args.tune_ms} ms)",
+                   "tiles": (f"autotuned ({tune_s:.1f} s, trial {args.tune_ms} ms)" if not args.tune_cache
+                             else f"autotuner cache {os.path.basename(args.tune_cache)} ({tune_s:.1f} s)"),
                    "parallelism": (f"{world} GPUs: interleaved work tiles per GPU + sum all-reduce of J and K"
                                    if world > 1 else "1 GPU")},
         "graph": {"ms_per_step": ms_graph / args.steps, "value": nq * args.steps / (ms_graph * 1e-3),
@@ -377,7 +378,7 @@ def run_batch(args, dev, flush):
     Dp = plan.pack([torch.from_numpy(D) for _, D in sel]).to(dev)
     J, K = torch.empty_like(Dp), torch.empty_like(Dp)
     nq = plan.stats()["quartets_k"]
-    plan.autotune(Dp, precision=eri.ERI_MIXED, trial_ms=args.tune_ms)
+    plan.autotune(Dp, precision=eri.ERI_MIXED, trial_ms=args.tune_ms, cache=args.tune_cache)
     stream = torch.cuda.current_stream(dev)
 
     def tm(fn, steps, warmup):
@@ -482,6 +483,8 @@ def main():
     ap.add_argument("--tau", type=float, default=TAU, help="FP32/FP64 tier threshold of the mixed path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune-ms", type=float, default=2.0, help="autotuner trial length per candidate")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON tile cache: load the tuned tiles from it if present, else tune and store them")
     ap.add_argument("--batch-mols", type=int, default=12,
                     help="molecules of the 64-molecule set in the batched leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)

@@ -21,13 +21,21 @@
 #pragma once
 #include "kernels_a.cuh"
 
-// shared memory per warp (KB) of the warp kernel, per precision: FP64 keeps
-// 8 warps per SM (two resident 4-warp blocks), FP32 about 16-20
+// base shared memory per warp (KB) of the warp kernel, per precision: FP64
+// keeps 8 warps per SM (two resident 4-warp blocks), FP32 about 16-20
 #ifndef ERI_WARP_SMEM64_KB
 #define ERI_WARP_SMEM64_KB 22
 #endif
 #ifndef ERI_WARP_SMEM32_KB
 #define ERI_WARP_SMEM32_KB 12
+#endif
+// upper limits when a larger ket-primitive batch saves a batch (FP64: two
+// 4-warp blocks still fit in an SM's 228 KB)
+#ifndef ERI_WARP_SMEM64_MAX_KB
+#define ERI_WARP_SMEM64_MAX_KB 27
+#endif
+#ifndef ERI_WARP_SMEM32_MAX_KB
+#define ERI_WARP_SMEM32_MAX_KB 16
 #endif
 // FP64 also takes the lane-owned-P ket transform where W fits in registers
 #ifndef ERI_REGW64
@@ -44,12 +52,23 @@ struct BShape {
   static constexpr int B = L + 1, BOX = B * B * B, NPING = L > 0 ? nherm(L - 1) : 1;
   static constexpr int NEB = (LA + 1) * (LB + 1) * (LAB + 1), NEK = (LC + 1) * (LD + 1) * (LCD + 1);
   static constexpr int NSC = L + 5;  // F'_0..F'_L, PQx, PQy, PQz, c
-  // shared memory per warp (elements of T): G ket primitives per batch and CH
-  // ket pairs per chunk are sized to fit it
-  static constexpr int BUDGET = sizeof(T) == 8 ? (ERI_WARP_SMEM64_KB * 1024) / 8 : (ERI_WARP_SMEM32_KB * 1024) / 4;
+  // Shared memory per warp (elements of T).  Steps A and B cost the same per
+  // batch of G ket primitives whatever G, so G should cover a ket pair's
+  // primitives in as few batches as the memory allows: contracted s/p pairs
+  // commonly have 9 (3 x 3), pairs with a d or f shell 3.  The budget starts at
+  // BASE (occupancy) and grows up to MAX until that batch count is reached.
   static constexpr int FIXED = 3 * NEB;
   static constexpr int PER_G = BOX + 2 * NPING + NSC + 3 * NEK;
   static constexpr int PER_C = HABP + NAB;
+  static constexpr int BASE = sizeof(T) == 8 ? (ERI_WARP_SMEM64_KB * 1024) / 8 : (ERI_WARP_SMEM32_KB * 1024) / 4;
+  static constexpr int MAXB = sizeof(T) == 8 ? (ERI_WARP_SMEM64_MAX_KB * 1024) / 8 : (ERI_WARP_SMEM32_MAX_KB * 1024) / 4;
+  static constexpr int GTARGET = (LC <= 1 && LD <= 1) ? 9 : 3;
+  static constexpr int fit_g(int budget) { return (budget - FIXED - NCD * PER_C) / PER_G; }
+  static constexpr int GMAXB = fit_g(MAXB) < 1 ? 1 : fit_g(MAXB);
+  static constexpr int NBATCH = (GTARGET + GMAXB - 1) / GMAXB;
+  static constexpr int GWANT = (GTARGET + NBATCH - 1) / NBATCH;
+  static constexpr int NEED = FIXED + NCD * PER_C + GWANT * PER_G;
+  static constexpr int BUDGET = NEED <= BASE ? BASE : (NEED <= MAXB ? NEED : MAXB);
   static constexpr int G0 = (BUDGET - FIXED - NCD * PER_C) / PER_G;
   static constexpr int G = G0 >= 1 ? (G0 > 16 ? 16 : G0) : 1;
   static constexpr int CHMAX = (BUDGET - FIXED - G * PER_G) / PER_C;
