@@ -139,7 +139,10 @@ int eri_plan_set_coords(eri_plan_t* plan, const double* coords_dev, int32_t free
  * a batched plan).  D must be symmetric.  J or K may be NULL to
  * skip that matrix (J alone runs only the J-engine).  thresh < 0 keeps the
  * plan's threshold; another value rebuilds the lists first (with a host wait).
- * precision: ERI_FP64 or ERI_MIXED (tier split at the plan's mixed_tau).
+ * precision: ERI_FP64 or ERI_MIXED (tier split at the plan's mixed_tau: a device
+ * pass writes each class pair's FP64-tier and FP32-tier quartets to two compacted
+ * lists, then each tier runs over its own list; the plan holds these lists, up
+ * to 2^23 quartets per tier, allocated by the first mixed build or graph capture).
  * With thresh < 0 and opts.profile = 0 the call only enqueues work on
  * `stream` (no host wait, no allocation), so it may be captured into a CUDA graph.
  */
@@ -166,7 +169,7 @@ int eri_build_jk_graph(eri_plan_t* plan, const double* D, double* J, double* K, 
  * the thread kernel each lane, takes before moving on; the walk steps a cursor
  * through the bra prefix array instead of searching it per quartet).  For every
  * (bra class, ket class, tier) launch of this plan and density, candidate
- * lengths (1, 2, 4, 8, and 16 for warp kernels) are timed with CUDA events on
+ * lengths (1, 2, 4, 8, and 16, 32 for warp kernels) are timed with CUDA events on
  * three windows of the launch's own list, each window sized so the current
  * length takes about trial_ms, and the fastest (by more than 3 %) is kept in
  * the plan.  Synchronises `stream` repeatedly; writes only plan scratch; J and
@@ -186,7 +189,9 @@ int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision, double tr
  * quartets long and interleaved, so each share gets an even mix of classes,
  * screening magnitudes and precision tiers.  A tile is `tile` consecutive items
  * of the class-pair list for the warp kernels and 32 x tile for the thread
- * kernel (eri_get_tiles).  (0, 1) restores the whole build.
+ * kernel (eri_get_tiles); in a mixed-precision build it is 32 items, taken by
+ * the tier split that compacts each tier's quartets.  (0, 1) restores the
+ * whole build.
  * Errors: ERI_EINVAL (nshard < 1 or shard outside 0..nshard-1).
  */
 int eri_plan_set_shard(eri_plan_t* plan, int32_t shard, int32_t nshard);

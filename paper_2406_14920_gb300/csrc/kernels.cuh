@@ -28,10 +28,15 @@ struct KArgs {
   const int* shloc;     // shell index inside its molecule, per (global) shell
   const int* pbase;     // first pair index of each molecule
   float tau, pmax32;
-  int mixed;            // 0: every item in this launch's precision
+  int mixed;            // tier split only (k_tier_split): test every item
   int tier_want;        // 0 or 1: which tier this launch processes
   unsigned long long* counter;  // items processed by this launch's tier (may be null)
   int same_class;
+  // Mixed precision: the launch runs the compacted list of its tier written by
+  // k_tier_split, item i = (bra position items[i].x, ket position items[i].y),
+  // *nitems of them (read on the device).  Null: items are positions in wl.
+  const int2* items;
+  const unsigned int* nitems;
 };
 
 // pair index of shells x, y of molecule `mol` (pairs are stored a >= b, a(a+1)/2 + b)
@@ -85,7 +90,9 @@ __device__ __forceinline__ int find_bra(const int64_t* __restrict__ prefix, int 
 struct BraCursor {
   int ib;
   int64_t bs, be;
-  __device__ __forceinline__ BraCursor(const WorkList& wl, int64_t item) {
+  __device__ __forceinline__ BraCursor() : ib(0), bs(0), be(0) {}
+  __device__ __forceinline__ BraCursor(const WorkList& wl, int64_t item) { seek(wl, item); }
+  __device__ __forceinline__ void seek(const WorkList& wl, int64_t item) {
     ib = find_bra(wl.prefix, wl.nbra, item);
     bs = __ldg(wl.prefix + ib);
     be = __ldg(wl.prefix + ib + 1);

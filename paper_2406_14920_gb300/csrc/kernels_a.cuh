@@ -266,51 +266,68 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
   }
 }
 
+// One quartet (bra position ib, ket position ik of the work list) of a thread-kernel class.
 template <int LA, int LB, int LC, int LD, typename T>
-__global__ void __launch_bounds__(128) jk_thread_kernel(JKArgs A) {
+__device__ __forceinline__ void thread_item(const JKArgs& A, int ib, int ik, unsigned long long& done,
+                                            unsigned long long& doneq, unsigned long long& doneb) {
   using S = AShape<LA, LB, LC, LD>;
   const KArgs& a = A.k;
-  const int64_t total = a.wl.total;
+  const int pb_id = __ldg(a.wl.bra + ib);
+  const int mol = __ldg(a.sp.pmol + pb_id);
+  const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
+  const int s1 = __ldg(a.sp.s1 + pb_id), s2 = __ldg(a.sp.s2 + pb_id);
+  const int s3 = __ldg(a.sp.s1 + pk_id), s4 = __ldg(a.sp.s2 + pk_id);
+  const int npb_ = __ldg(a.sp.np + pb_id), npk_ = __ldg(a.sp.np + pk_id);
+  ++done;
+  doneq += (unsigned long long)npb_ * npk_;
+  doneb += npb_;
+  T w = T(1);
+  if (s1 == s2) w *= T(0.5);
+  if (s3 == s4) w *= T(0.5);
+  if (pb_id == pk_id) w *= T(0.5);
+  T X[S::NAB * S::NCD];
+  if constexpr (S::WACC)
+    eri_block_reg<LA, LB, LC, LD, T>(a, __ldg(a.sp.poff + pb_id), npb_, __ldg(a.sp.eoff + pb_id),
+                                     __ldg(a.sp.poff + pk_id), npk_, __ldg(a.sp.eoff + pk_id), X);
+  else
+    eri_block_reg_pq<LA, LB, LC, LD, T>(a, __ldg(a.sp.poff + pb_id), npb_, __ldg(a.sp.eoff + pb_id),
+                                        __ldg(a.sp.poff + pk_id), npk_, __ldg(a.sp.eoff + pk_id), X);
+  contract_block<LA, LB, LC, LD, T>(A, X, w, __ldg(a.sp.ao1 + pb_id), __ldg(a.sp.ao2 + pb_id),
+                                    __ldg(a.sp.ao1 + pk_id), __ldg(a.sp.ao2 + pk_id), __ldg(a.sp.mat_off + mol),
+                                    __ldg(a.sp.mat_n + mol));
+}
+
+template <int LA, int LB, int LC, int LD, typename T>
+__global__ void __launch_bounds__(128) jk_thread_kernel(JKArgs A) {
+  const KArgs& a = A.k;
+  // items: positions in the work list, or (mixed precision) this tier's compacted list
+  const bool compact = a.items != nullptr;
+  const int64_t total = compact ? (int64_t)__ldg(a.nitems) : a.wl.total;
+  const int64_t first = compact ? 0 : a.wl.first;
+  const int nshard = compact ? 1 : a.wl.nshard, shard = compact ? 0 : a.wl.shard;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long done = 0, doneq = 0, doneb = 0;
   // a warp shares a tile of 32 * tile consecutive items, lane l takes items l, l + 32, ...
-  const int64_t span = 32 * (int64_t)a.wl.tile, ntiles = (total - a.wl.first + span - 1) / span;
+  const int64_t span = 32 * (int64_t)a.wl.tile, ntiles = (total - first + span - 1) / span;
   const int lane = threadIdx.x & 31;
-  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * a.wl.nshard + a.wl.shard;
-       tl < ntiles; tl += (stride >> 5) * a.wl.nshard) {
-  const int64_t i0 = a.wl.first + tl * span + lane, i1 = a.wl.first + tl * span + span < total
-                                                           ? a.wl.first + tl * span + span : total;
-  if (i0 >= i1) continue;
-  BraCursor cur(a.wl, i0);
-  for (int64_t item = i0; item < i1; item += 32) {
-    const int ik = cur.at(a.wl, item);
-    const int ib = cur.ib;
-    const int pb_id = __ldg(a.wl.bra + ib);
-    const int mol = __ldg(a.sp.pmol + pb_id);
-    const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
-    const int s1 = __ldg(a.sp.s1 + pb_id), s2 = __ldg(a.sp.s2 + pb_id);
-    const int s3 = __ldg(a.sp.s1 + pk_id), s4 = __ldg(a.sp.s2 + pk_id);
-    if (a.mixed && quartet_tier(a, mol, pb_id, pk_id, s1, s2, s3, s4) != a.tier_want) continue;
-    const int npb_ = __ldg(a.sp.np + pb_id), npk_ = __ldg(a.sp.np + pk_id);
-    ++done;
-    doneq += (unsigned long long)npb_ * npk_;
-    doneb += npb_;
-    T w = T(1);
-    if (s1 == s2) w *= T(0.5);
-    if (s3 == s4) w *= T(0.5);
-    if (pb_id == pk_id) w *= T(0.5);
-    T X[S::NAB * S::NCD];
-    if constexpr (S::WACC)
-      eri_block_reg<LA, LB, LC, LD, T>(a, __ldg(a.sp.poff + pb_id), __ldg(a.sp.np + pb_id), __ldg(a.sp.eoff + pb_id),
-                                       __ldg(a.sp.poff + pk_id), __ldg(a.sp.np + pk_id), __ldg(a.sp.eoff + pk_id), X);
-    else
-      eri_block_reg_pq<LA, LB, LC, LD, T>(a, __ldg(a.sp.poff + pb_id), __ldg(a.sp.np + pb_id),
-                                          __ldg(a.sp.eoff + pb_id), __ldg(a.sp.poff + pk_id), __ldg(a.sp.np + pk_id),
-                                          __ldg(a.sp.eoff + pk_id), X);
-    contract_block<LA, LB, LC, LD, T>(A, X, w, __ldg(a.sp.ao1 + pb_id), __ldg(a.sp.ao2 + pb_id),
-                                      __ldg(a.sp.ao1 + pk_id), __ldg(a.sp.ao2 + pk_id), __ldg(a.sp.mat_off + mol),
-                                      __ldg(a.sp.mat_n + mol));
-  }
+  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * nshard + shard; tl < ntiles;
+       tl += (stride >> 5) * nshard) {
+    const int64_t t0 = first + tl * span;
+    const int64_t i1 = t0 + span < total ? t0 + span : total;
+    const int64_t i0 = t0 + lane;
+    if (i0 >= i1) continue;
+    if (compact) {
+      for (int64_t item = i0; item < i1; item += 32) {
+        const int2 v = __ldg(a.items + item);
+        thread_item<LA, LB, LC, LD, T>(A, v.x, v.y, done, doneq, doneb);
+      }
+    } else {
+      BraCursor cur(a.wl, i0);
+      for (int64_t item = i0; item < i1; item += 32) {
+        const int ik = cur.at(a.wl, item);
+        thread_item<LA, LB, LC, LD, T>(A, cur.ib, ik, done, doneq, doneb);
+      }
+    }
   }
   if (a.counter && done) {
     atomicAdd(a.counter, done);

@@ -97,8 +97,10 @@ __host__ __device__ constexpr int lex_base(int lmax, int t, int u) {
   return b;
 }
 
+// FP64: two resident blocks per SM are the target (the register budget follows);
+// FP32: left to the compiler
 template <int LA, int LB, int LC, int LD, typename T>
-__global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 1) jk_warp_kernel(JKArgs A) {
   using S = BShape<LA, LB, LC, LD, T>;
   constexpr int LAB = S::LAB, LCD = S::LCD, L = S::L, B = S::B, BOX = S::BOX, NSC = S::NSC;
   constexpr int NA = S::NA, NB = S::NB, ND = S::ND, NAB = S::NAB, NCD = S::NCD, HAB = S::HAB, HABP = S::HABP,
@@ -150,22 +152,42 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
   T* Ws = sm + S::SM_W;
   T* Xs = sm + S::SM_X;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t total = a.wl.total;
+  // items: positions in the work list, or (mixed precision) this tier's compacted list
+  const bool compact = a.items != nullptr;
+  const int64_t total = compact ? (int64_t)__ldg(a.nitems) : a.wl.total;
+  const int64_t first = compact ? 0 : a.wl.first;
+  const int nshard = compact ? 1 : a.wl.nshard, shard = compact ? 0 : a.wl.shard;
   unsigned long long done = 0, doneq = 0, doneb = 0;
-  const int64_t tile = a.wl.tile, ntiles = (total - a.wl.first + tile - 1) / tile;
-  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * a.wl.nshard + a.wl.shard; tl < ntiles;
-       tl += nwarps * a.wl.nshard) {
-  const int64_t i0 = a.wl.first + tl * tile, i1 = i0 + tile < total ? i0 + tile : total;
-  BraCursor cur(a.wl, i0);
-  for (int64_t item = i0; item < i1; ++item) {
-    const int ik = cur.at(a.wl, item);
-    const int ib = cur.ib;
+  const int64_t tile = a.wl.tile, ntiles = (total - first + tile - 1) / tile;
+  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * nshard + shard; tl < ntiles;
+       tl += nwarps * nshard) {
+  const int64_t t0 = first + tl * tile, i1 = t0 + tile < total ? t0 + tile : total;
+  // the lanes locate 32 items at a time; the warp then runs them one by one
+  BraCursor cur;
+  if (!compact) cur.seek(a.wl, t0 + lane < i1 ? t0 + lane : t0);
+  for (int64_t cq = t0; cq < i1; cq += 32) {
+  int my_ib = 0, my_ik = 0;
+  const bool ok = cq + lane < i1;
+  if (ok) {
+    if (compact) {
+      const int2 v = __ldg(a.items + cq + lane);
+      my_ib = v.x;
+      my_ik = v.y;
+    } else {
+      my_ik = cur.at(a.wl, cq + lane);
+      my_ib = cur.ib;
+    }
+  }
+  unsigned pend = __ballot_sync(0xffffffffu, ok);
+  while (pend) {
+    const int src = __ffs(pend) - 1;
+    pend &= pend - 1;
+    const int ib = __shfl_sync(0xffffffffu, my_ib, src), ik = __shfl_sync(0xffffffffu, my_ik, src);
     const int pb_id = __ldg(a.wl.bra + ib);
     const int mol = __ldg(a.sp.pmol + pb_id);
     const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
     const int s1 = __ldg(a.sp.s1 + pb_id), s2 = __ldg(a.sp.s2 + pb_id);
     const int s3 = __ldg(a.sp.s1 + pk_id), s4 = __ldg(a.sp.s2 + pk_id);
-    if (a.mixed && quartet_tier(a, mol, pb_id, pk_id, s1, s2, s3, s4) != a.tier_want) continue;
     const int npb = __ldg(a.sp.np + pb_id), offb = __ldg(a.sp.poff + pb_id), eb0 = __ldg(a.sp.eoff + pb_id);
     const int npk = __ldg(a.sp.np + pk_id), offk = __ldg(a.sp.poff + pk_id), ek0 = __ldg(a.sp.eoff + pk_id);
     ++done;
@@ -429,6 +451,7 @@ __global__ void __launch_bounds__(128) jk_warp_kernel(JKArgs A) {
       }
       __syncwarp();
     }
+  }
   }
   }
   if (a.counter && lane == 0 && done) {

@@ -94,14 +94,25 @@ struct GShape {
   static constexpr int NTB = LAB + 2;
   static constexpr int NEB = (LA + 1) * (LB + 1) * NTB, NEK = (LC + 1) * (LD + 1) * (LCD + 1);
   static constexpr int NSC = L1 + 5;
-  static constexpr int BUDGET = (ERI_WARP_SMEM64_KB * 1024) / 8;
   static constexpr int FIXED = 9 * NEB;  // E, GA, GB per direction
   static constexpr int PER_G = BOX + 2 * NPING + NSC + 3 * NEK;
   static constexpr int PER_C = HAB1P;
+  // ket-primitive batch sized as for the energy kernel (BShape)
+  static constexpr int BASE = (ERI_WARP_SMEM64_KB * 1024) / 8, MAXB = (ERI_WARP_SMEM64_MAX_KB * 1024) / 8;
+  static constexpr int GTARGET = (LC <= 1 && LD <= 1) ? 9 : 3;
+  static constexpr int fit_g(int budget) { return (budget - FIXED - NCD * PER_C) / PER_G; }
+  static constexpr int GMAXB = fit_g(MAXB) < 1 ? 1 : fit_g(MAXB);
+  static constexpr int NBATCH = (GTARGET + GMAXB - 1) / GMAXB;
+  static constexpr int GWANT = (GTARGET + NBATCH - 1) / NBATCH;
+  static constexpr int NEED = FIXED + NCD * PER_C + GWANT * PER_G;
+  static constexpr int BUDGET = NEED <= BASE ? BASE : (NEED <= MAXB ? NEED : MAXB);
   static constexpr int G0 = (BUDGET - FIXED - NCD * PER_C) / PER_G;
   static constexpr int G = G0 >= 1 ? (G0 > 16 ? 16 : G0) : 1;
   static constexpr int CHMAX = (BUDGET - FIXED - G * PER_G) / PER_C;
   static constexpr int CH = CHMAX >= NCD ? NCD : (CHMAX < 1 ? 1 : CHMAX);
+  // register ket transform (as in the energy kernel) where W fits
+  static constexpr int NPS = (HAB1 + 31) / 32;
+  static constexpr bool REGW = ERI_REGW64 && CH == NCD && NCD * NPS <= 32;
   static constexpr int SM_BOX = 0, SM_PING = SM_BOX + G * BOX, SM_SC = SM_PING + G * 2 * NPING,
                        SM_EK = SM_SC + G * NSC, SM_EB = SM_EK + G * 3 * NEK, SM_W = SM_EB + FIXED,
                        SM_TOTAL = SM_W + CH * HAB1P;
@@ -113,7 +124,7 @@ struct GShape {
 };
 
 template <int LA, int LB, int LC, int LD>
-__global__ void __launch_bounds__(128) grad_warp_kernel(GradArgs a) {
+__global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
   using S = GShape<LA, LB, LC, LD>;
   using T = double;
   constexpr int LAB = S::LAB, LCD = S::LCD, L = S::L1, B = S::B, BOX = S::BOX, NSC = S::NSC;
@@ -149,6 +160,9 @@ __global__ void __launch_bounds__(128) grad_warp_kernel(GradArgs a) {
     tab_lex[i] = (t + u <= LAB + 1) ? lex_base(LAB + 1, t, u) : 0;
   }
   __syncthreads();
+  int pslot[S::NPS];  // box offset of this lane's Hermite indices P = lane + 32 j
+#pragma unroll
+  for (int j = 0; j < S::NPS; ++j) pslot[j] = lane + 32 * j < HAB ? (tab_p[lane + 32 * j] & 0xffff) : 0;
   T* sm = reinterpret_cast<T*>(smraw + S::table_bytes()) + (size_t)wib * S::SM_TOTAL;
   T* boxes = sm + S::SM_BOX;
   T* pings = sm + S::SM_PING;
@@ -208,7 +222,13 @@ __global__ void __launch_bounds__(128) grad_warp_kernel(GradArgs a) {
             }
           }
         }
-        for (int x = lane; x < CH * HABP; x += 32) Ws[x] = T(0);
+        T wreg[S::REGW ? S::NPS * NCD : 1];
+        if constexpr (S::REGW) {
+#pragma unroll
+          for (int x = 0; x < S::NPS * NCD; ++x) wreg[x] = T(0);
+        } else {
+          for (int x = lane; x < CH * HABP; x += 32) Ws[x] = T(0);
+        }
         const T bPx = __ldg(a.pd.P + ipb), bPy = __ldg(a.pd.P + a.pd.n + ipb), bPz = __ldg(a.pd.P + 2 * a.pd.n + ipb);
         for (int k0 = 0; k0 < npk; k0 += G) {
           const int ng = npk - k0 < G ? npk - k0 : G;
@@ -262,7 +282,33 @@ __global__ void __launch_bounds__(128) grad_warp_kernel(GradArgs a) {
             __syncwarp();
             cur = 1 - cur;
           }
-          // ket transform, items (ci, P), P over Hermite indices up to LAB+1
+          // ket transform, P over Hermite indices up to LAB+1
+          if constexpr (S::REGW) {
+            for (int g = 0; g < ng; ++g) {
+              const T* ek = Ek + g * 3 * NEK;
+              const T* rbox = boxes + g * BOX;
+              for_cart<LC>([&](auto kx, auto ky, auto kz) {
+                for_cart<LD>([&](auto lx, auto ly, auto lz) {
+                  constexpr int KX = ERI_CI(kx), KY = ERI_CI(ky), KZ = ERI_CI(kz);
+                  constexpr int LX = ERI_CI(lx), LY = ERI_CI(ly), LZ = ERI_CI(lz);
+                  constexpr int icd = cidx(LC, KY, KZ) * ND + cidx(LD, LY, LZ);
+                  const T* ex = ek + (KX * (LD + 1) + LX) * (LCD + 1);
+                  const T* ey = ek + NEK + (KY * (LD + 1) + LY) * (LCD + 1);
+                  const T* ez = ek + 2 * NEK + (KZ * (LD + 1) + LZ) * (LCD + 1);
+                  sfor<S::NPS>([&](auto j_) {
+                    constexpr int j = ERI_CI(j_);
+                    if (j * 32 + 32 <= HAB || lane + 32 * j < HAB) {
+                      const T* r = rbox + pslot[j];
+                      wreg[j * NCD + icd] += tsum<KX + LX, KY + LY, KZ + LZ, false>(
+                          ex, ey, ez, [&](auto sx, auto sy, auto sz) {
+                            return r[(ERI_CI(sx) * B + ERI_CI(sy)) * B + ERI_CI(sz)];
+                          });
+                    }
+                  });
+                });
+              });
+            }
+          } else {
           for (int it = lane; it < nci * HAB; it += 32) {
             const int ci = it / HAB, P = it - ci * HAB;
             const int c0w = tab_cd[2 * (c0 + ci)], c1w = tab_cd[2 * (c0 + ci) + 1];
@@ -287,6 +333,17 @@ __global__ void __launch_bounds__(128) grad_warp_kernel(GradArgs a) {
             }
             Ws[ci * HABP + (pw >> 16)] += acc;
           }
+          }
+          __syncwarp();
+        }
+        if constexpr (S::REGW) {
+#pragma unroll
+          for (int j = 0; j < S::NPS; ++j)
+            if (lane + 32 * j < HAB) {
+              const int slot = tab_p[lane + 32 * j] >> 16;
+#pragma unroll
+              for (int icd = 0; icd < NCD; ++icd) Ws[icd * HABP + slot] = wreg[j * NCD + icd];
+            }
           __syncwarp();
         }
         // bra derivatives and contraction with G, items (ab, ci)

@@ -153,6 +153,40 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
   prefmaxp[ip] = (float)fmin(prmx, 1.0e30);
 }
 
+// Mixed-precision tier split of the items [wl.first, wl.total) of one class
+// pair: one warp per chunk of 32 items (chunks t with t % nshard == shard), each
+// lane locates and tests one item; the FP64-tier and FP32-tier quartets are
+// appended to out0 / out1 (warp-aggregated atomics on cnt[0], cnt[1]).
+__global__ void __launch_bounds__(256) k_tier_split(KArgs a, int2* __restrict__ out0, int2* __restrict__ out1,
+                                                    unsigned int* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t nch = (a.wl.total - a.wl.first + 31) / 32;
+  for (int64_t ch = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * a.wl.nshard + a.wl.shard;
+       ch < nch; ch += nwarps * a.wl.nshard) {
+    const int64_t item = a.wl.first + ch * 32 + lane;
+    int tier = -1, ib = 0, ik = 0;
+    if (item < a.wl.total) {
+      ib = find_bra(a.wl.prefix, a.wl.nbra, item);
+      ik = (int)(item - __ldg(a.wl.prefix + ib));
+      const int pb_id = __ldg(a.wl.bra + ib);
+      const int mol = __ldg(a.sp.pmol + pb_id);
+      const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
+      tier = quartet_tier(a, mol, pb_id, pk_id, __ldg(a.sp.s1 + pb_id), __ldg(a.sp.s2 + pb_id),
+                          __ldg(a.sp.s1 + pk_id), __ldg(a.sp.s2 + pk_id));
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const unsigned m = __ballot_sync(0xffffffffu, tier == t);
+      if (!m) continue;
+      unsigned base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(cnt + t, (unsigned)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (tier == t) (t == 0 ? out0 : out1)[base + __popc(m & ((1u << lane) - 1u))] = make_int2(ib, ik);
+    }
+  }
+}
+
 // max |D'| over the blocks (s1, s2) and (s2, s1) of every shell pair (used by
 // the mixed-precision tier test)
 __global__ void k_dmax(int npair, const int* __restrict__ s1, const int* __restrict__ s2, const int* __restrict__ l,
@@ -838,6 +872,12 @@ void eri_plan_impl::release() {
     branch[b] = nullptr;
     join_ev[b] = nullptr;
   }
+  for (int b = 0; b < kBranches; ++b) {
+    if (tbuf[b]) cudaFree(tbuf[b]);
+    tbuf[b] = nullptr;
+  }
+  if (tcnt) cudaFree(tcnt);
+  tcnt = nullptr;
   if (fork_ev) cudaEventDestroy(fork_ev);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   fork_ev = nullptr;
@@ -860,6 +900,31 @@ int eri_plan_impl::ensure_streams() {
     CK(cudaStreamCreateWithFlags(&branch[b], cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&join_ev[b], cudaEventDisableTiming));
   }
+  return ERI_OK;
+}
+
+// Compacted tier lists of mixed-precision builds: per branch, two lists of
+// tier_cap items (int2 bra / ket positions) and two counters.  tier_cap is the
+// longest class-pair list, at most kTierCap; longer lists are split in windows.
+static const int64_t kTierCap = 1 << 23;
+
+int eri_plan_impl::ensure_tier_bufs(int nb) {
+  int64_t mx = 1;
+  for (int X = 0; X < NPAIRCLASS; ++X)
+    for (int Y = 0; Y <= X; ++Y) mx = std::max(mx, h_ktot[X * NPAIRCLASS + Y]);
+  const int64_t cap = std::min(mx, kTierCap);
+  if (cap > tier_cap) {
+    CK(cudaDeviceSynchronize());
+    for (int b = 0; b < kBranches; ++b) {
+      if (tbuf[b]) cudaFree(tbuf[b]);
+      tbuf[b] = nullptr;
+    }
+    tier_nb = 0;
+    tier_cap = cap;
+  }
+  if (!tcnt) CK(dalloc(&tcnt, 2 * kBranches));
+  for (int b = tier_nb; b < nb; ++b) CK(dalloc(&tbuf[b], 2 * (size_t)tier_cap));
+  tier_nb = std::max(tier_nb, nb);
   return ERI_OK;
 }
 
@@ -905,7 +970,7 @@ static double class_flops(int X, int Y, double nq, double npq, double nbp, bool 
 }
 
 // Default work-tile length: the thread kernel's lanes already take adjacent
-// items; a warp kernel walks 4 consecutive quartets (mostly one bra) per tile.
+// items; a warp kernel takes 4 consecutive quartets (mostly one bra) per tile.
 static int default_tile(int X, int Y, int tier) {
   return use_thread_kernel(kClassL1[X], kClassL2[X], kClassL1[Y], kClassL2[Y], tier == 1) ? 1 : 4;
 }
@@ -1247,50 +1312,93 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
     ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
     ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
     ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
+    ka.items = nullptr; ka.nitems = nullptr;
     ja.Jh = J ? P->d_Jh : nullptr;
     P->last_mixed = mixed;
     P->last_do_j = J != nullptr;
     P->last_do_k = K != nullptr;
-    // launches in decreasing order of estimated work (primitive quartets x class cost)
-    struct L { int X, Y, tier; double cost; };
+    // class pairs in decreasing order of estimated work (primitive quartets x class cost)
+    struct L { int X, Y; double cost; };
     std::vector<L> order;
     for (int X = 0; X < NPAIRCLASS; ++X)
       for (int Y = 0; Y <= X; ++Y) {
         const int64_t tot = P->h_ktot[X * NPAIRCLASS + Y];
         if (tot == 0) continue;
-        const double c = class_flops(X, Y, (double)tot, (double)P->h_kprim[X * NPAIRCLASS + Y], 0.0, J != nullptr,
-                                     K != nullptr);
-        for (int tier = 0; tier < (mixed ? 2 : 1); ++tier) order.push_back({X, Y, tier, c});
+        order.push_back({X, Y, class_flops(X, Y, (double)tot, (double)P->h_kprim[X * NPAIRCLASS + Y], 0.0,
+                                           J != nullptr, K != nullptr)});
       }
+    if (mixed && !concurrent) {
+      const int rc = P->ensure_tier_bufs(1);
+      if (rc != ERI_OK) return rc;
+    }
+    if (mixed && P->tier_nb < (concurrent ? eri_plan_impl::kBranches : 1)) return ERI_EINVAL;
     if (concurrent) {
       std::stable_sort(order.begin(), order.end(), [](const L& a, const L& b) { return a.cost > b.cost; });
       CK(cudaEventRecord(P->fork_ev, s));
       for (int b = 0; b < eri_plan_impl::kBranches; ++b) CK(cudaStreamWaitEvent(P->branch[b], P->fork_ev, 0));
     }
-    double load[eri_plan_impl::kBranches] = {};
-    for (const L& l : order) {
-      ka.wl = P->klist(l.X, l.Y);
-      ka.wl.tile = P->tile_for(l.X, l.Y, l.tier);
-      ka.same_class = l.X == l.Y;
-      ka.tier_want = l.tier;
-      ka.counter = P->d_counters + ((l.X * NPAIRCLASS + l.Y) * 2 + l.tier) * 3;
-      cudaStream_t ls = s;
-      if (concurrent) {  // least-loaded branch
-        int b = (int)(std::min_element(load, load + eri_plan_impl::kBranches) - load);
-        load[b] += l.cost;
-        ls = P->branch[b];
-      }
+    const bool prof = P->opts.profile && !concurrent;
+    auto launch = [&](int X, int Y, int tier, cudaStream_t ls) -> int {
+      ka.tier_want = tier;
+      ka.wl.tile = P->tile_for(X, Y, tier);
+      ka.counter = P->d_counters + ((X * NPAIRCLASS + Y) * 2 + tier) * 3;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
-      const bool prof = P->opts.profile && !concurrent;
       if (prof) {
         CK(P->prof_event_pair(&e0, &e1));
         CK(cudaEventRecord(e0, ls));
       }
-      CK(launch_jk_class(l.X, l.Y, l.tier, ja, ls, P->nsm));
+      CK(launch_jk_class(X, Y, tier, ja, ls, P->nsm));
       if (prof) {
         CK(cudaEventRecord(e1, ls));
-        P->prof_log.push_back({l.X, l.Y, l.tier, P->prof_ev_used - 2});
+        P->prof_log.push_back({X, Y, tier, P->prof_ev_used - 2});
       }
+      return ERI_OK;
+    };
+    double load[eri_plan_impl::kBranches] = {};
+    for (const L& l : order) {
+      cudaStream_t ls = s;
+      int b = 0;
+      if (concurrent) {  // least-loaded branch
+        b = (int)(std::min_element(load, load + eri_plan_impl::kBranches) - load);
+        load[b] += l.cost;
+        ls = P->branch[b];
+      }
+      ka.same_class = l.X == l.Y;
+      if (!mixed) {
+        ka.wl = P->klist(l.X, l.Y);
+        ka.items = nullptr;
+        ka.nitems = nullptr;
+        const int rc = launch(l.X, l.Y, 0, ls);
+        if (rc != ERI_OK) return rc;
+        continue;
+      }
+      // mixed precision: split each window of the list into its two tiers
+      // (compacted on the device), then run each tier over its own list
+      const WorkList full = P->klist(l.X, l.Y);
+      int2* buf = P->tbuf[b];
+      unsigned int* cnt = P->tcnt + 2 * b;
+      for (int64_t f = 0; f < full.total; f += P->tier_cap) {
+        KArgs sa = ka;
+        sa.wl = full;
+        sa.wl.first = f;
+        sa.wl.total = std::min<int64_t>(full.total, f + P->tier_cap);
+        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned int), ls));
+        const int64_t nch = (sa.wl.total - f + 31) / 32;
+        k_tier_split<<<(int)std::max<int64_t>(1, std::min<int64_t>((nch + 7) / 8, (int64_t)P->nsm * 8)), 256, 0,
+                       ls>>>(sa, buf, buf + P->tier_cap, cnt);
+        CK(cudaGetLastError());
+        for (int tier = 0; tier < 2; ++tier) {
+          ka.wl = full;
+          ka.wl.first = 0;
+          ka.wl.total = sa.wl.total - f;  // upper bound of the tier's count (grid sizing)
+          ka.items = buf + (tier ? P->tier_cap : 0);
+          ka.nitems = cnt + tier;
+          const int rc = launch(l.X, l.Y, tier, ls);
+          if (rc != ERI_OK) return rc;
+        }
+      }
+      ka.items = nullptr;
+      ka.nitems = nullptr;
     }
     if (concurrent)
       for (int b = 0; b < eri_plan_impl::kBranches; ++b) {
@@ -1334,6 +1442,10 @@ extern "C" int eri_build_jk_graph(eri_plan_t* plan, const double* D, double* J, 
   if (!P->gexec || P->gkey[0] != D || P->gkey[1] != J || P->gkey[2] != K || P->gprec != precision) {
     int rc = P->ensure_streams();
     if (rc != ERI_OK) return rc;
+    if (precision == ERI_MIXED) {
+      rc = P->ensure_tier_bufs(eri_plan_impl::kBranches);
+      if (rc != ERI_OK) return rc;
+    }
     if (P->gexec) {
       CK(cudaStreamSynchronize(s));
       CK(cudaGraphExecDestroy(P->gexec));
@@ -1398,32 +1510,61 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   int rc = ERI_OK;
-  // time the three windows of `win` items each with tile t; returns ms (< 0 on error)
+  if (mixed) {
+    rc = P->ensure_tier_bufs(1);
+    if (rc != ERI_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
+    }
+  }
+  // time the three windows of `win` items each with tile t; returns ms (< 0 on
+  // error).  Mixed precision: each window is first split into its tiers
+  // (untimed) and the tier's compacted list is timed.
   auto trial = [&](int X, int Y, int tier, int t, int64_t win) -> double {
-    const int64_t tot = P->h_ktot[X * NPAIRCLASS + Y];
+    const WorkList full = P->klist(X, Y);
+    const int64_t tot = full.total;
+    if (mixed) win = std::min<int64_t>(win, P->tier_cap);
     double best = 1e300;
     for (int rep = 0; rep < 2; ++rep) {
-      if (cudaEventRecord(e0, s) != cudaSuccess) return -1.0;
+      double sum = 0.0;
       for (int w = 0; w < 3; ++w) {
         const int64_t c = tot * (2 * w + 1) / 6;
         const int64_t f = std::max<int64_t>(0, std::min<int64_t>(c - win / 2, tot - win));
-        ka.wl = P->klist(X, Y);
+        const int64_t last = std::min<int64_t>(tot, f + win);
+        ka.wl = full;
         ka.wl.first = f;
-        ka.wl.total = std::min<int64_t>(tot, f + win);
+        ka.wl.total = last;
         ka.wl.tile = t;
         ka.same_class = X == Y;
         ka.tier_want = tier;
+        ka.items = nullptr;
+        ka.nitems = nullptr;
+        if (mixed) {
+          if (cudaMemsetAsync(P->tcnt, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) return -1.0;
+          const int64_t nch = (last - f + 31) / 32;
+          k_tier_split<<<(int)std::max<int64_t>(1, std::min<int64_t>((nch + 7) / 8, (int64_t)P->nsm * 8)), 256, 0,
+                         s>>>(ka, P->tbuf[0], P->tbuf[0] + P->tier_cap, P->tcnt);
+          ka.wl.first = 0;
+          ka.wl.total = last - f;
+          ka.items = P->tbuf[0] + (tier ? P->tier_cap : 0);
+          ka.nitems = P->tcnt + tier;
+        }
+        if (cudaEventRecord(e0, s) != cudaSuccess) return -1.0;
         if (launch_jk_class(X, Y, tier, ja, s, P->nsm) != cudaSuccess) return -1.0;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0;
+        sum += ms;
       }
-      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
-      float ms = 0.0f;
-      if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0;
-      best = std::min(best, (double)ms);
+      best = std::min(best, sum);
     }
+    ka.items = nullptr;
+    ka.nitems = nullptr;
     return best;
   };
   static const int kThreadTiles[] = {1, 2, 4, 8};
-  static const int kWarpTiles[] = {1, 2, 4, 8, 16};
+  static const int kWarpTiles[] = {1, 2, 4, 8, 16, 32};
   for (int X = 0; X < NPAIRCLASS && rc == ERI_OK; ++X)
     for (int Y = 0; Y <= X && rc == ERI_OK; ++Y) {
       const int64_t tot = P->h_ktot[X * NPAIRCLASS + Y];
@@ -1440,7 +1581,7 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
         }
         const bool thr = use_thread_kernel(kClassL1[X], kClassL2[X], kClassL1[Y], kClassL2[Y], tier == 1);
         const int* cand = thr ? kThreadTiles : kWarpTiles;
-        const int nc = thr ? 4 : 5;
+        const int nc = thr ? 4 : 6;
         int best = def;
         double bt = t0;
         for (int i = 0; i < nc; ++i) {
@@ -1521,6 +1662,7 @@ int eri_build_jk_scratch(eri_plan_t* plan, const double* D, double* J, double* K
   ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
   ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
   ka.tau = 0.0f; ka.pmax32 = 0.0f; ka.mixed = 0; ka.tier_want = 0; ka.counter = nullptr;
+  ka.items = nullptr; ka.nitems = nullptr;
   ja.Jh = J ? Jh : nullptr;
   for (int X = 0; X < NPAIRCLASS; ++X)
     for (int Y = 0; Y <= X; ++Y) {

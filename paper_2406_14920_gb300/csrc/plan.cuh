@@ -79,6 +79,12 @@ struct eri_plan_impl {
   const void* gkey[3] = {};
   int gprec = -1;
   int ensure_streams();
+  // compacted tier lists of mixed builds (per branch), see ensure_tier_bufs
+  int2* tbuf[kBranches] = {};
+  unsigned int* tcnt = nullptr;
+  int64_t tier_cap = 0;
+  int tier_nb = 0;
+  int ensure_tier_bufs(int nb);
   // work-tile length (items per worker tile) per (bra class, ket class, tier),
   // set by eri_autotune or eri_set_tiles; 0 = the built-in default
   int tile_k[eri::NPAIRCLASS * eri::NPAIRCLASS * 2] = {};
