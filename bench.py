@@ -295,8 +295,10 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (largest device-time share in the mixed step)
     dom = max(prof, key=lambda r: r["ms"])
+    # a class may run in several launches per step (long lists are split in
+    # windows): flops are per step, so per launch = flops / launches-per-step
     per_launch_ms = dom["ms"] / dom["launches"]
-    achieved = dom["flops"] / (per_launch_ms * 1e-3) / 1e12
+    achieved = (dom["flops"] / (dom["launches"] / args.steps)) / (per_launch_ms * 1e-3) / 1e12
     peak = PEAK_TFLOPS[dom["tier"]]
     tot_ms = sum(r["ms"] for r in prof)
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
@@ -312,12 +314,16 @@ def run_ours(args, rank, world, local_rank):
     top = sorted(prof, key=lambda r: -r["ms"])[:8]
     profile_top = [{"class": f"({CLASS_NAMES[r['bra_class']]}|{CLASS_NAMES[r['ket_class']]})",
                     "tier": "fp64" if r["tier"] == 0 else "fp32", "ms_per_step": round(r["ms"] / args.steps, 2),
-                    "tflops": round(r["flops"] / (r["ms"] / r["launches"] * 1e-3) / 1e12, 4)} for r in top]
+                    "tflops": round(r["flops"] / (r["ms"] / args.steps * 1e-3) / 1e12, 4)} for r in top]
     fp64_top = sorted(prof64, key=lambda r: -r["ms"])[:5]
     fp64_profile_top = [{"class": f"({CLASS_NAMES[r['bra_class']]}|{CLASS_NAMES[r['ket_class']]})",
                          "ms_per_step": round(r["ms"] / args.fp64_steps, 2),
-                         "tflops": round(r["flops"] / (r["ms"] / r["launches"] * 1e-3) / 1e12, 4)} for r in fp64_top]
-    launches_per_step = len(prof) + 4  # class launches + D scaling, D block maxima, two symmetrisations
+                         "tflops": round(r["flops"] / (r["ms"] / args.fp64_steps * 1e-3) / 1e12, 4)} for r in fp64_top]
+    # class launches per step, one tier split per class-pair window (mixed), plus
+    # D scaling, D block maxima and the two symmetrisations
+    n_class = sum(r["launches"] for r in prof) // args.steps
+    n_split = sum(r["launches"] for r in prof if r["tier"] == 0) // args.steps
+    launches_per_step = n_class + n_split + 4
 
     out = {
         "metric": METRIC, "value": nq * args.steps / (ms_mixed * 1e-3), "unit": UNIT, "n_gpus": world,
@@ -482,14 +488,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tau", type=float, default=TAU, help="FP32/FP64 tier threshold of the mixed path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tune-ms", type=float, default=2.0, help="autotuner trial length per candidate")
+    ap.add_argument("--tune-ms", type=float, default=10.0, help="autotuner trial length per candidate")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON tile cache: load the tuned tiles from it if present, else tune and store them")
     ap.add_argument("--batch-mols", type=int, default=12,
                     help="molecules of the 64-molecule set in the batched leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--ncu-case", action="store_true",
-                    help="small case for ncu section captures: the first 20 atoms of the workload, two mixed builds")
+                    help="small case for ncu section captures: the first 20 atoms of the workload, two mixed "
+                         "builds and one gradient")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -504,6 +511,7 @@ def main():
         Dt = torch.from_numpy(D2).cuda()
         for _ in range(2):
             plan.build_jk(Dt)
+        plan.grad(Dt)
         torch.cuda.synchronize()
         print(json.dumps({"ncu_case": True, "nbf": b2.nbf, "quartets": plan.stats()["quartets_k"]}))
         return

@@ -170,9 +170,10 @@ int eri_build_jk_graph(eri_plan_t* plan, const double* D, double* J, double* K, 
  * through the bra prefix array instead of searching it per quartet).  For every
  * (bra class, ket class, tier) launch of this plan and density, candidate
  * lengths (1, 2, 4, 8, and 16, 32 for warp kernels) are timed with CUDA events on
- * three windows of the launch's own list, each window sized so the current
- * length takes about trial_ms, and the fastest (by more than 3 %) is kept in
- * the plan.  Synchronises `stream` repeatedly; writes only plan scratch; J and
+ * three windows of the launch's own list (mixed precision: of the tier's
+ * compacted list), the windows sized so the current length takes about trial_ms
+ * and every resident warp gets several tiles; a length replaces the default
+ * only if it is more than 5 % faster twice.  Synchronises `stream` repeatedly; writes only plan scratch; J and
  * K are unchanged.  Later builds (and graphs captured after it) use the tiles.
  * Errors: ERI_EINVAL (trial_ms <= 0, NULL, bad precision), ERI_ECUDA.
  */

@@ -100,7 +100,7 @@ __host__ __device__ constexpr int lex_base(int lmax, int t, int u) {
 // FP64: two resident blocks per SM are the target (the register budget follows);
 // FP32: left to the compiler
 template <int LA, int LB, int LC, int LD, typename T>
-__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 1) jk_warp_kernel(JKArgs A) {
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 0) jk_warp_kernel(JKArgs A) {
   using S = BShape<LA, LB, LC, LD, T>;
   constexpr int LAB = S::LAB, LCD = S::LCD, L = S::L, B = S::B, BOX = S::BOX, NSC = S::NSC;
   constexpr int NA = S::NA, NB = S::NB, ND = S::ND, NAB = S::NAB, NCD = S::NCD, HAB = S::HAB, HABP = S::HABP,

@@ -1571,14 +1571,17 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
       if (tot == 0) continue;
       for (int tier = 0; tier < (mixed ? 2 : 1) && rc == ERI_OK; ++tier) {
         const int def = default_tile(X, Y, tier);
-        int64_t win = std::min<int64_t>(tot, 3 * 32768);
+        // windows long enough that every resident warp gets several tiles (a
+        // short window measures the launch tail, not the tile length)
+        int64_t win = std::min<int64_t>(tot, 3 * (int64_t)P->nsm * 2048);
         double t0 = trial(X, Y, tier, def, win / 3);
         if (t0 < 0.0) { rc = ERI_ECUDA; break; }
-        if (t0 < 0.5 * trial_ms && win < tot) {
+        for (int grow = 0; grow < 2 && t0 < 0.5 * trial_ms && win < tot; ++grow) {
           win = std::min<int64_t>(tot, (int64_t)((double)win * trial_ms / std::max(t0, 1e-3)));
           t0 = trial(X, Y, tier, def, win / 3 + 1);
           if (t0 < 0.0) { rc = ERI_ECUDA; break; }
         }
+        if (rc != ERI_OK) break;
         const bool thr = use_thread_kernel(kClassL1[X], kClassL2[X], kClassL1[Y], kClassL2[Y], tier == 1);
         const int* cand = thr ? kThreadTiles : kWarpTiles;
         const int nc = thr ? 4 : 6;
@@ -1588,7 +1591,12 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
           if (cand[i] == def) continue;
           const double t = trial(X, Y, tier, cand[i], win / 3 + 1);
           if (t < 0.0) { rc = ERI_ECUDA; break; }
-          if (t < 0.97 * bt) { bt = t; best = cand[i]; }
+          if (t < 0.95 * bt) { bt = t; best = cand[i]; }
+        }
+        if (rc == ERI_OK && best != def) {  // confirm against the default once more
+          const double td = trial(X, Y, tier, def, win / 3 + 1), tb = trial(X, Y, tier, best, win / 3 + 1);
+          if (td < 0.0 || tb < 0.0) { rc = ERI_ECUDA; break; }
+          if (!(tb < 0.95 * td)) best = def;
         }
         P->tile_k[(X * NPAIRCLASS + Y) * 2 + tier] = best;
       }
