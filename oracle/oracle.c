@@ -26,7 +26,7 @@
  *   - one-electron overlap (Eq. overlap_definition) and point-charge attraction
  *     (Eq. v1e_definition2), used only to pin the ERIs and normalisation.
  *
- * Readings where the paper is silent (all listed in the design doc as well):
+ * Readings where the paper is silent:
  *   - normalisation: every primitive component gets
  *     N = (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2i-1)!!(2j-1)!!(2k-1)!!), then each
  *     shell's coefficients are scaled once so the contracted (l,0,0) component
