@@ -109,3 +109,11 @@ def test_tuner_and_graph_null_arguments(eri):
     assert L.eri_get_tiles(None, None) == -1
     assert L.eri_set_tiles(None, None) == -1
     assert L.eri_build_jk_graph(None, None, None, None, 0, None) == -1
+
+
+def test_shard_and_layout_null_arguments(eri):
+    L = eri.lib()
+    assert L.eri_plan_set_shard(None, 0, 1) == -1
+    assert L.eri_build_jk_noalloc(None, None, None, None, None) == -1
+    assert L.eri_get_profile(None, None, 0, None) == -1
+    assert L.eri_get_stats(None, None) == -1
