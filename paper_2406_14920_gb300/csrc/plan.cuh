@@ -23,7 +23,6 @@ struct eri_plan_impl {
   int *d_ccm = nullptr, *d_segloc = nullptr;
   int64_t nherm_tot = 0;
   double thresh = 1e-12;
-  double last_flops_j = 0.0, last_flops_k = 0.0;
   // shells
   int *d_sh_l = nullptr, *d_sh_atom = nullptr, *d_sh_np = nullptr, *d_sh_po = nullptr, *d_sh_ao = nullptr;
   double *d_exps = nullptr, *d_coefs = nullptr, *d_cn = nullptr, *d_f = nullptr, *d_coords = nullptr;
