@@ -319,6 +319,17 @@ def run_ours(args, rank, world, local_rank):
     fp64_profile_top = [{"class": f"({CLASS_NAMES[r['bra_class']]}|{CLASS_NAMES[r['ket_class']]})",
                          "ms_per_step": round(r["ms"] / args.fp64_steps, 2),
                          "tflops": round(r["flops"] / (r["ms"] / args.fp64_steps * 1e-3) / 1e12, 4)} for r in fp64_top]
+    # every class launch's achieved fraction of its roofline (ALU peak of its precision)
+    def class_rows(prof_, steps):
+        rows = []
+        for r in sorted(prof_, key=lambda r: -r["ms"]):
+            tf = r["flops"] / (r["ms"] / steps * 1e-3) / 1e12 if r["ms"] > 0 else 0.0
+            rows.append([f"({CLASS_NAMES[r['bra_class']]}|{CLASS_NAMES[r['ket_class']]})",
+                         "fp64" if r["tier"] == 0 else "fp32", round(r["ms"] / steps, 3), round(tf, 4),
+                         round(tf / PEAK_TFLOPS[r["tier"]], 5)])
+        return rows
+    class_roofline = {"columns": ["class", "tier", "ms_per_step", "tflops", "frac"],
+                      "mixed": class_rows(prof, args.steps), "fp64": class_rows(prof64, args.fp64_steps)}
     # class launches per step, one tier split per class-pair window (mixed), plus
     # D scaling, D block maxima and the two symmetrisations
     n_class = sum(r["launches"] for r in prof) // args.steps
@@ -349,6 +360,7 @@ def run_ours(args, rank, world, local_rank):
                                "fp64": sum(r["flops"] for r in prof64) / (sum(r["ms"] for r in prof64) / args.fp64_steps * 1e-3) / 1e12},
         "tier_ms_per_step": tier_ms,
         "profile_top": profile_top,
+        "class_roofline": class_roofline,
         "fp64_profile_top": fp64_profile_top,
         "roofline": roofline,
         "e2e": {"value": nq * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
