@@ -137,7 +137,8 @@ int eri_plan_set_coords(eri_plan_t* plan, const double* coords_dev, int32_t free
  * whose Schwarz bound Q_ab Q_cd >= thresh (Eq. j_definition, Eq. k_definition,
  * Eq. kernel_upperbound).  D, J, K: device, nbf*nbf (packed per molecule for
  * a batched plan).  D must be symmetric.  J or K may be NULL to
- * skip that matrix (J alone runs only the J-engine).  thresh < 0 keeps the
+ * skip that matrix (J alone runs only the J-engine, in FP64 whatever the
+ * precision argument, unless opts.j_engine = 0).  thresh < 0 keeps the
  * plan's threshold; another value rebuilds the lists first (with a host wait).
  * precision: ERI_FP64 or ERI_MIXED (tier split at the plan's mixed_tau: a device
  * pass writes each class pair's FP64-tier and FP32-tier quartets to two compacted
