@@ -57,6 +57,7 @@ cudaError_t launch_jk_t(const JKArgs& a, cudaStream_t s, int nsm) {
   } else {
     using S = BShape<LA, LB, LC, LD, T>;
     constexpr int WPB = 4;
+    static_assert(S::table_bytes() + WPB * S::smem_per_warp() <= 227 * 1024, "warp kernel block exceeds 227 KB");
     auto kern = jk_warp_kernel<LA, LB, LC, LD, T>;
     cudaError_t e = launch_persistent(kern, S::table_bytes() + WPB * S::smem_per_warp(), a.k.wl.total, WPB, nsm, &li);
     if (e != cudaSuccess) return e;
@@ -98,6 +99,7 @@ cudaError_t launch_grad_xy(const GradArgs& a, cudaStream_t s, int nsm) {
   constexpr int LA = ClassL<X>::l1, LB = ClassL<X>::l2, LC = ClassL<Y>::l1, LD = ClassL<Y>::l2;
   using S = GShape<LA, LB, LC, LD>;
   constexpr int WPB = 4;
+  static_assert(S::table_bytes() + WPB * S::smem_per_warp() <= 227 * 1024, "gradient block exceeds 227 KB");
   LaunchInfo li;
   auto kern = grad_warp_kernel<LA, LB, LC, LD>;
   cudaError_t e = launch_persistent(kern, S::table_bytes() + WPB * S::smem_per_warp(), a.wl.total, WPB, nsm, &li);
@@ -128,6 +130,7 @@ cudaError_t launch_j_t(const JArgs& a, cudaStream_t s, int nsm) {
   if (a.wl.total <= 0) return cudaSuccess;
   using S = JShape<LAB, LCD, T>;
   constexpr int WPB = 4;
+  static_assert(WPB * S::smem_per_warp() <= 227 * 1024, "J-engine block exceeds 227 KB");
   LaunchInfo li;
   auto kern = j_warp_kernel<LAB, LCD, T>;
   cudaError_t e = launch_persistent(kern, WPB * S::smem_per_warp(), a.wl.total, WPB, nsm, &li);
