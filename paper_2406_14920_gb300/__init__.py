@@ -146,7 +146,12 @@ class Plan:
             bt, arrs = _basis_t(bs)
             bts[m] = bt
             keep.append(arrs)
+        if len(coords) != len(bases):
+            raise ValueError(f"{len(coords)} coordinate sets for {len(bases)} bases")
         crds = [np.ascontiguousarray(c, np.float64).reshape(-1) for c in coords]
+        for bs, c in zip(bases, crds):
+            if c.size != 3 * bs.natom:
+                raise ValueError(f"coordinates hold {c.size} values, the basis has {bs.natom} atoms (need natom x 3)")
         self._keep = (keep, crds)
         o = OptsT()
         L.eri_default_opts(C.byref(o))

@@ -117,3 +117,14 @@ def test_shard_and_layout_null_arguments(eri):
     assert L.eri_build_jk_noalloc(None, None, None, None, None) == -1
     assert L.eri_get_profile(None, None, 0, None) == -1
     assert L.eri_get_stats(None, None) == -1
+
+
+def test_binding_checks_coordinate_shapes(eri):
+    """The binding refuses coordinates that do not match the basis before any
+    call into the library (which would read natom x 3 doubles)."""
+    import workloads as W
+    b, _ = W.workload(0)
+    with pytest.raises(ValueError):
+        eri.Plan(b, coords=np.zeros((2, 3)))
+    with pytest.raises(ValueError):
+        eri.Plan([b, b], coords=[b.coords])
