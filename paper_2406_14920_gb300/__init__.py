@@ -101,6 +101,21 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
 
 
+def _require(t, numel, what, device=None):
+    """A device argument must be a contiguous float64 CUDA tensor of `numel`
+    elements (on `device` when given): the library reads and writes exactly that
+    many doubles through the raw pointer.  None passes (optional outputs)."""
+    import torch
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{what}: need a contiguous float64 CUDA tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{what}: {t.numel()} elements, need {numel}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{what}: on cuda:{t.device.index}, the plan is on cuda:{device}")
+
+
 def _stream_ptr(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -171,6 +186,8 @@ class Plan:
                               C.byref(h)), "eri_plan")
         self.h = h
         self.precision = int(precision)
+        import torch
+        self.device = torch.cuda.current_device() if device is None else int(device)
         nm = C.c_int32()
         _check(L.eri_plan_layout(h, C.byref(nm), None, None, None), "eri_plan_layout")
         self.nmol = nm.value
@@ -219,6 +236,9 @@ class Plan:
         if want_k and K is None:
             K = torch.empty(shp, dtype=torch.float64, device=D.device)
         prec = self.precision if precision is None else int(precision)
+        _require(D, self.nmat, "D", self.device)
+        _require(J if want_j else None, self.nmat, "J", self.device)
+        _require(K if want_k else None, self.nmat, "K", self.device)
         _check(lib().eri_build_jk(self.h, _ptr(D), _ptr(J if want_j else None), _ptr(K if want_k else None),
                                   float(thresh), prec, _stream_ptr(stream)), "eri_build_jk")
         return (J if want_j else None), (K if want_k else None)
@@ -227,6 +247,8 @@ class Plan:
         """As build_jk into preallocated J / K (either may be None), replayed
         from a CUDA graph captured on the first call with these tensors."""
         prec = self.precision if precision is None else int(precision)
+        for t, w in ((D, "D"), (J, "J"), (K, "K")):
+            _require(t, self.nmat, w, self.device)
         _check(lib().eri_build_jk_graph(self.h, _ptr(D), _ptr(J), _ptr(K), prec, _stream_ptr(stream)),
                "eri_build_jk_graph")
         return J, K
@@ -247,6 +269,7 @@ class Plan:
             if key in db:
                 self.set_tiles(np.asarray(db[key], np.int32))
                 return self.tiles()
+        _require(D, self.nmat, "D", self.device)
         _check(lib().eri_autotune(self.h, _ptr(D), prec, float(trial_ms), _stream_ptr(stream)), "eri_autotune")
         t = self.tiles()
         if cache:
@@ -275,10 +298,14 @@ class Plan:
         import torch
         if out is None:
             out = torch.empty(2 * self.nmol if self.batched else 2, dtype=torch.float64, device=D.device)
+        for t, w in ((D, "D"), (J, "J"), (K, "K")):
+            _require(t, self.nmat, w, self.device)
+        _require(out, 2 * self.nmol, "out", self.device)
         _check(lib().eri_energy(self.h, _ptr(D), _ptr(J), _ptr(K), _ptr(out), _stream_ptr(stream)), "eri_energy")
         return out
 
     def set_coords(self, coords_dev, freeze_lists=False, stream=None):
+        _require(coords_dev, 3 * self.natom, "coords", self.device)
         _check(lib().eri_plan_set_coords(self.h, _ptr(coords_dev), int(bool(freeze_lists)), _stream_ptr(stream)),
                "eri_plan_set_coords")
 
@@ -286,6 +313,8 @@ class Plan:
         import torch
         if out is None:
             out = torch.empty((self.natom, 3), dtype=torch.float64, device=D.device)
+        _require(D, self.nmat, "D", self.device)
+        _require(out, 3 * self.natom, "out", self.device)
         _check(lib().eri_jk_grad(self.h, _ptr(D), _ptr(out), int(want_j), int(want_k), _stream_ptr(stream)),
                "eri_jk_grad")
         return out

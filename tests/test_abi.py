@@ -128,3 +128,13 @@ def test_binding_checks_coordinate_shapes(eri):
         eri.Plan(b, coords=np.zeros((2, 3)))
     with pytest.raises(ValueError):
         eri.Plan([b, b], coords=[b.coords])
+
+
+def test_binding_requires_device_float64_tensors(eri):
+    """Device arguments are checked before their pointers reach the library."""
+    import torch
+    with pytest.raises(ValueError):
+        eri._require(torch.zeros(4, dtype=torch.float64), 4, "D")      # host tensor
+    with pytest.raises(ValueError):
+        eri._require(np.zeros(4), 4, "D")                               # not a tensor
+    eri._require(None, 4, "K")                                          # optional output
