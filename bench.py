@@ -192,6 +192,19 @@ def traffic_for(X, Y, tier):
     return d.get("kernels", {}).get(f"{CLASS_NAMES[X]}|{CLASS_NAMES[Y]}|{tier}")
 
 
+def class_rows(prof, steps):
+    """[class, tier, ms per step, TFLOP/s, fraction of the tier's ALU peak] for
+    every profiled class launch, longest first.  `flops` of a record is per step
+    (all launches of that class in one build); `ms` sums `steps` builds."""
+    rows = []
+    for r in sorted(prof, key=lambda r: -r["ms"]):
+        tf = r["flops"] / (r["ms"] / steps * 1e-3) / 1e12 if r["ms"] > 0 else 0.0
+        rows.append([f"({CLASS_NAMES[r['bra_class']]}|{CLASS_NAMES[r['ket_class']]})",
+                     "fp64" if r["tier"] == 0 else "fp32", round(r["ms"] / steps, 3), round(tf, 4),
+                     round(tf / PEAK_TFLOPS[r["tier"]], 5)])
+    return rows
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -320,14 +333,6 @@ def run_ours(args, rank, world, local_rank):
                          "ms_per_step": round(r["ms"] / args.fp64_steps, 2),
                          "tflops": round(r["flops"] / (r["ms"] / args.fp64_steps * 1e-3) / 1e12, 4)} for r in fp64_top]
     # every class launch's achieved fraction of its roofline (ALU peak of its precision)
-    def class_rows(prof_, steps):
-        rows = []
-        for r in sorted(prof_, key=lambda r: -r["ms"]):
-            tf = r["flops"] / (r["ms"] / steps * 1e-3) / 1e12 if r["ms"] > 0 else 0.0
-            rows.append([f"({CLASS_NAMES[r['bra_class']]}|{CLASS_NAMES[r['ket_class']]})",
-                         "fp64" if r["tier"] == 0 else "fp32", round(r["ms"] / steps, 3), round(tf, 4),
-                         round(tf / PEAK_TFLOPS[r["tier"]], 5)])
-        return rows
     class_roofline = {"columns": ["class", "tier", "ms_per_step", "tflops", "frac"],
                       "mixed": class_rows(prof, args.steps), "fp64": class_rows(prof64, args.fp64_steps)}
     # class launches per step, one tier split per class-pair window (mixed), plus

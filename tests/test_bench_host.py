@@ -19,3 +19,15 @@ def test_sampled_quartets_are_significant_and_canonical():
         assert float(Q[pidx(a, b)]) * float(Q[pidx(c, d)]) >= bench.THRESH
     o = oracle.Oracle(basis)
     assert o.quartet_batch(q[:20]) > 0.0
+
+
+def test_class_rows_rates_and_fractions():
+    """Per-class rows: FLOPs per step over ms per step, against the tier's peak."""
+    prof = [{"bra_class": 7, "ket_class": 1, "tier": 1, "ms": 500.0, "flops": 1e12, "launches": 5},
+            {"bra_class": 2, "ket_class": 2, "tier": 0, "ms": 2000.0, "flops": 2.5e11, "launches": 5}]
+    rows = bench.class_rows(prof, steps=5)
+    assert rows[0][:2] == ["(pp|pp)", "fp64"] and rows[1][:2] == ["(fp|ps)", "fp32"]
+    # (pp|pp): 2.5e11 FLOP per step in 400 ms -> 0.625 TFLOP/s = half of 1.25
+    assert abs(rows[0][3] - 0.625) < 1e-9 and abs(rows[0][4] - 0.5) < 1e-9
+    # (fp|ps): 1e12 FLOP in 100 ms -> 10 TFLOP/s of 80.5
+    assert abs(rows[1][3] - 10.0) < 1e-9 and abs(rows[1][4] - round(10.0 / 80.5, 5)) < 1e-12
