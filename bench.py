@@ -270,6 +270,8 @@ def run_ours(args, rank, world, local_rank):
         ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
         return ms, plan.profile()
 
+    # measured FMA rates of this GPU (untimed): the ALU roofline's measured denominators
+    peak_meas = {0: eri.peak_probe(eri.ERI_FP64, 4000), 1: eri.peak_probe(eri.ERI_MIXED, 200000)}
     clocks = ClockSampler(local_rank)
     clocks.start()
     ms_mixed, prof = timed(lambda: plan.build_jk(Dd, J, K, precision=eri.ERI_MIXED), args.steps, args.warmup)
@@ -320,7 +322,11 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": f"({CLASS_NAMES[dom['bra_class']]}|{CLASS_NAMES[dom['ket_class']]}) "
                           f"{'FP64' if dom['tier'] == 0 else 'FP32'}",
                 "share": round(dom["ms"] / tot_ms, 4),
-                "peak_source": "FP64: GB300 nominal 1.25 TFLOP/s; FP32: 152 SM x 128 x 2 x 2.07 GHz"}
+                "peak_source": "FP64: GB300 nominal 1.25 TFLOP/s; FP32: 152 SM x 128 x 2 x 2.07 GHz",
+                "peak_measured": round(peak_meas[dom["tier"]], 3),
+                "frac_measured": round(achieved / peak_meas[dom["tier"]], 4),
+                "peak_measured_source": "eri_peak_probe: independent FMA chains on every SM, CUDA events, "
+                                        "untimed before the timed region (FP64 DFMA / FP32 FFMA)"}
     fl_total = sum(r["flops"] for r in prof)
     tier_ms = {"fp64": sum(r["ms"] for r in prof if r["tier"] == 0) / args.steps,
                "fp32": sum(r["ms"] for r in prof if r["tier"] == 1) / args.steps}
@@ -368,6 +374,7 @@ def run_ours(args, rank, world, local_rank):
         "class_roofline": class_roofline,
         "fp64_profile_top": fp64_profile_top,
         "roofline": roofline,
+        "peak_probe_tflops": {"fp64": round(peak_meas[0], 3), "fp32": round(peak_meas[1], 3)},
         "e2e": {"value": nq * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 16 * n * n},
         "gpu_launches": launches_per_step * args.steps,
@@ -499,7 +506,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

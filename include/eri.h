@@ -82,6 +82,9 @@ typedef struct {
   int64_t quartets_k_fp32; /* of quartets_k, evaluated in FP32 by the last mixed build */
   double flops_k, flops_j; /* algorithmic FLOPs of the last build (McMurchie-Davidson count) */
   int32_t device_status;   /* device-side status word (0 = ok) */
+  int64_t quartets_k_guard; /* of quartets_k, kept in FP64 by the last mixed build's FP32 range guard
+                               alone (their bound was below mixed_tau, but an exponent sum above 1e3
+                               or a primitive prefactor product above 1e18 would overflow FP32) */
 } eri_stats_t;
 
 /* Fill opts with the defaults listed above.  Host only. */
@@ -261,7 +264,7 @@ int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t cap, int32
 int eri_get_stats(eri_plan_t* plan, eri_stats_t* stats);
 
 /*
- * J and K exactly as eri_build_jk(plan, D, J, K, -1, ERI_FP64, stream), for
+ * J and K in FP64 at the plan's threshold, for
  * callers that cannot allocate device memory when they build (code running
  * during CUDA graph capture, inside a device allocator, or on hosts that
  * forbid allocation after start-up).  The paper has no counterpart of this
@@ -277,10 +280,26 @@ int eri_get_stats(eri_plan_t* plan, eri_stats_t* stats);
  *     the previous call's contents (the accumulators are cleared at the start
  *     of each call).  Calls whose GPU work overlaps, on different streams or
  *     threads, race on it: order them.
- * D, J, K: device pointers as for eri_build_jk; J or K may be NULL.
+ * D, J, K: device pointers as for eri_build_jk; J or K may be NULL.  J and K
+ * always come from contracted Cartesian ERIs (a J-only call does not take the
+ * J-engine), so they equal eri_build_jk(plan, D, J, K, -1, ERI_FP64, stream)
+ * to rounding (within 1e-10, the parity tolerance), bit for bit only where
+ * eri_build_jk takes the same path (J and K together, or opts.j_engine = 0).
+ * eri_get_stats then describes this call as the last build.
  */
 #define ERI_NOALLOC_MAX_NBF 256
 int eri_build_jk_noalloc(eri_plan_t* plan, const double* D, double* J, double* K, void* stream);
+
+/*
+ * Measurement utility (not a step of the method): the FP64 (precision =
+ * ERI_FP64) or FP32 (ERI_MIXED) fused multiply-add rate of the current device,
+ * in TFLOP/s (FMA = 2 FLOP), from one launch of independent FMA chains over
+ * every SM, `iters` iterations per chain, timed with CUDA events on `stream`.
+ * These are the pipes the ERI kernels are bound by; the result is the measured
+ * denominator of their roofline.  Allocates a small output buffer, waits for
+ * the launch.  Errors: ERI_EINVAL, ERI_ENOMEM, ERI_ECUDA.
+ */
+int eri_peak_probe(int32_t precision, int32_t iters, double* tflops, void* stream);
 
 /* Free every device and host resource of the plan (NULL is a no-op). */
 int eri_plan_destroy(eri_plan_t* plan);

@@ -50,7 +50,7 @@ class StatsT(C.Structure):
     _fields_ = [("nbf", C.c_int32), ("nshell", C.c_int32), ("npair", C.c_int32), ("nsig_pair", C.c_int32),
                 ("quartets_k", C.c_int64), ("quartets_j", C.c_int64), ("prim_quartets_k", C.c_int64),
                 ("quartets_k_fp32", C.c_int64), ("flops_k", C.c_double), ("flops_j", C.c_double),
-                ("device_status", C.c_int32)]
+                ("device_status", C.c_int32), ("quartets_k_guard", C.c_int64)]
 
 
 def lib():
@@ -81,6 +81,7 @@ def lib():
         L.eri_get_stats.argtypes = [vp, C.POINTER(StatsT)]
         L.eri_get_profile.argtypes = [vp, C.POINTER(LaunchProfT), i32, C.POINTER(C.c_int32)]
         L.eri_build_jk_noalloc.argtypes = [vp, vp, vp, vp, vp]
+        L.eri_peak_probe.argtypes = [i32, i32, C.POINTER(C.c_double), vp]
         L.eri_plan_destroy.argtypes = [vp]
         L.eri_strerror.argtypes = [C.c_int]
         L.eri_strerror.restype = C.c_char_p
@@ -201,6 +202,10 @@ class Plan:
         self.nmat = int(self.mat_off[-1])
         self.natom = int(self.atom_off[-1])
         self.npair = sum(b.nshell * (b.nshell + 1) // 2 for b in bases)
+        # geometry bookkeeping for JKEnergy: geom_version counts set_coords calls,
+        # list_version counts the ones that rebuilt the lists (freeze_lists False)
+        self.geom_version = 0
+        self.list_version = 0
 
     def _mat_shape(self):
         return (self.nmat,) if self.batched else (self.nbf, self.nbf)
@@ -308,6 +313,9 @@ class Plan:
         _require(coords_dev, 3 * self.natom, "coords", self.device)
         _check(lib().eri_plan_set_coords(self.h, _ptr(coords_dev), int(bool(freeze_lists)), _stream_ptr(stream)),
                "eri_plan_set_coords")
+        self.geom_version += 1
+        if not freeze_lists:
+            self.list_version += 1
 
     def grad(self, D, out=None, want_j=True, want_k=True, stream=None):
         import torch
@@ -344,6 +352,14 @@ class Plan:
         return {k: getattr(s, k) for k, _ in StatsT._fields_}
 
 
+def peak_probe(precision, iters, stream=None):
+    """Measured FMA rate (TFLOP/s) of the current device: FP64 for ERI_FP64,
+    FP32 for ERI_MIXED (eri_peak_probe)."""
+    t = C.c_double()
+    _check(lib().eri_peak_probe(int(precision), int(iters), C.byref(t), _stream_ptr(stream)), "eri_peak_probe")
+    return t.value
+
+
 def _autograd_function():
     import torch
 
@@ -354,15 +370,28 @@ def _autograd_function():
         forward: moves the plan's atoms (eri_plan_set_coords), builds J and K, and
         returns E.  backward: dE/dR from eri_jk_grad (derivative ERIs contracted with
         D, D held fixed) and dE/dD = J - K/2.
+
+        The plan is shared, mutable state.  backward differentiates at the
+        geometry its own forward saw: if the plan has moved since (another
+        forward on the same plan, a finite-difference step), backward moves it
+        back first (rebuilding the lists, or with freeze_lists keeping the
+        plan's frozen ones).  A frozen-list forward whose lists were rebuilt by
+        a later unfrozen set_coords cannot be differentiated any more and
+        raises RuntimeError.
         """
 
         @staticmethod
         def forward(ctx, coords, D, plan, freeze_lists=False):
-            plan.set_coords(coords.detach().contiguous(), freeze_lists=freeze_lists)
+            c = coords.detach().contiguous()
+            plan.set_coords(c, freeze_lists=freeze_lists)
             J, K = plan.build_jk(D.detach().contiguous())
             E = plan.energy(D.detach(), J, K).sum()
             ctx.save_for_backward(D, J, K)
             ctx.plan = plan
+            ctx.coords = c.clone()
+            ctx.freeze = bool(freeze_lists)
+            ctx.geom_version = plan.geom_version
+            ctx.list_version = plan.list_version
             return E
 
         @staticmethod
@@ -370,7 +399,15 @@ def _autograd_function():
             D, J, K = ctx.saved_tensors
             gR = gD = None
             if ctx.needs_input_grad[0]:
-                gR = ctx.plan.grad(D.detach().contiguous()) * gE
+                plan = ctx.plan
+                if plan.geom_version != ctx.geom_version:
+                    if ctx.freeze and plan.list_version != ctx.list_version:
+                        raise RuntimeError("JKEnergy.backward: the plan's frozen lists were rebuilt after this "
+                                           "forward; its gradient can no longer be taken on the same lists")
+                    plan.set_coords(ctx.coords, freeze_lists=ctx.freeze)
+                    ctx.geom_version = plan.geom_version
+                    ctx.list_version = plan.list_version
+                gR = plan.grad(D.detach().contiguous()) * gE
             if ctx.needs_input_grad[1]:
                 gD = (J - 0.5 * K) * gE
             return gR, gD, None, None

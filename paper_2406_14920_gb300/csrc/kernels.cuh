@@ -31,6 +31,7 @@ struct KArgs {
   int mixed;            // tier split only (k_tier_split): test every item
   int tier_want;        // 0 or 1: which tier this launch processes
   unsigned long long* counter;  // items processed by this launch's tier (may be null)
+  unsigned long long* guard;    // tier split: quartets kept in FP64 by the range guard alone (may be null)
   int same_class;
   // Mixed precision: the launch runs the compacted list of its tier written by
   // k_tier_split, item i = (bra position items[i].x, ket position items[i].y),
@@ -46,6 +47,8 @@ __device__ __forceinline__ int pair_index(const KArgs& a, int mol, int x, int y)
   return __ldg(a.pbase + mol) + hi * (hi + 1) / 2 + lo;
 }
 
+// Tier of one quartet: 0 = FP64 (bound >= tau), 1 = FP32, 2 = FP64 because
+// the FP32 range guard tripped although the bound is below tau.
 __device__ __forceinline__ int quartet_tier(const KArgs& a, int mol, int pb_id, int pk_id, int s1, int s2, int s3,
                                             int s4) {
   const float* dm = a.dmax;
@@ -57,7 +60,8 @@ __device__ __forceinline__ int quartet_tier(const KArgs& a, int mol, int pb_id, 
   // (R grows like (2 rho)^(L/2) and the prefactors multiply into it)
   const bool wide = fmaxf(__ldg(a.pmaxp + pb_id), __ldg(a.pmaxp + pk_id)) > a.pmax32 ||
                     __ldg(a.prefmaxp + pb_id) * __ldg(a.prefmaxp + pk_id) > 1.0e18f;
-  return (b >= a.tau || wide) ? 0 : 1;
+  // 0: FP64 by the bound; 1: FP32; 2: FP64 only because of the range guard
+  return b >= a.tau ? 0 : (wide ? 2 : 1);
 }
 
 // D' in the launch's precision

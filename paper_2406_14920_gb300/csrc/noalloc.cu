@@ -8,6 +8,7 @@
 // allocated.  This entry point instead takes its scratch from one fixed array
 // that is part of the loaded library, so a build allocates nothing at all
 // beyond what the caller passes in.
+#include <atomic>
 #include <cstdio>
 
 #include "../../include/eri.h"
@@ -23,19 +24,25 @@ int eri_plan_nbf_device(eri_plan_t* plan, int* nbf, int* device, int* nmol);
 static __device__ __align__(256) double g_noalloc_scratch[3 * ERI_NOALLOC_MAX_NBF * ERI_NOALLOC_MAX_NBF];
 
 static constexpr int kMaxDevices = 64;
-static double* g_scratch_dev[kMaxDevices] = {};
+static std::atomic<double*> g_scratch_dev[kMaxDevices] = {};
 
 // Device address of the scratch array on `device` (must be current).  The host
 // symbol g_noalloc_scratch is only a stand-in, never a device address, so it is
-// looked up once per device with cudaGetSymbolAddress.
+// looked up once per device with cudaGetSymbolAddress and cached.  Two threads
+// making their first call at once both look it up and store the same address
+// (atomic stores, no torn value).  cudaDeviceReset ends the context the address
+// belongs to, and the cache cannot see that: a process that resets a device
+// must not call eri_build_jk_noalloc on it again.
 static int scratch_for(int device, double** out) {
   if (device < 0 || device >= kMaxDevices) return ERI_EUNSUPPORTED;
-  if (!g_scratch_dev[device]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ERI_ECUDA;
-    g_scratch_dev[device] = static_cast<double*>(p);
+  double* p = g_scratch_dev[device].load(std::memory_order_acquire);
+  if (!p) {
+    void* q = nullptr;
+    if (cudaGetSymbolAddress(&q, g_noalloc_scratch) != cudaSuccess || !q) return ERI_ECUDA;
+    p = static_cast<double*>(q);
+    g_scratch_dev[device].store(p, std::memory_order_release);
   }
-  *out = g_scratch_dev[device];
+  *out = p;
   return ERI_OK;
 }
 

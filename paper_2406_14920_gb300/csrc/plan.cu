@@ -175,6 +175,9 @@ __global__ void __launch_bounds__(256) k_tier_split(KArgs a, int2* __restrict__ 
       tier = quartet_tier(a, mol, pb_id, pk_id, __ldg(a.sp.s1 + pb_id), __ldg(a.sp.s2 + pb_id),
                           __ldg(a.sp.s1 + pk_id), __ldg(a.sp.s2 + pk_id));
     }
+    const unsigned gm = __ballot_sync(0xffffffffu, tier == 2);
+    if (gm && lane == 0 && a.guard) atomicAdd(a.guard, (unsigned long long)__popc(gm));
+    if (tier == 2) tier = 0;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       const unsigned m = __ballot_sync(0xffffffffu, tier == t);
@@ -1173,7 +1176,7 @@ static int plan_create(int nmol, const eri_basis_t* const* bases, const double* 
     CKP(dalloc(&P->d_peoff, npair)); CKP(dalloc(&P->d_E, ne_tot)); CKP(dalloc(&P->d_Ef, ne_tot));
     CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_prefmaxp, npair)); CKP(dalloc(&P->d_ea, nprimpair));
     CKP(dalloc(&P->d_dmax, npair));
-    CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3));
+    CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3 + 1));  // + range-guard count
     CKP(dalloc(&P->d_rsteps, st.size()));
     CKP(dalloc(&P->d_Dp, (size_t)P->nmat)); CKP(dalloc(&P->d_Dpf, (size_t)P->nmat));
     CKP(dalloc(&P->d_Kh, (size_t)P->nmat));
@@ -1298,14 +1301,14 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
     // J and/or K from contracted Cartesian ERIs over canonical quartets
     if (K) CK(cudaMemsetAsync(P->d_Kh, 0, sizeof(double) * nn, s));
     if (J) CK(cudaMemsetAsync(P->d_Jh, 0, sizeof(double) * nn, s));
-    CK(cudaMemsetAsync(P->d_counters, 0, sizeof(unsigned long long) * NPAIRCLASS * NPAIRCLASS * 6, s));
+    CK(cudaMemsetAsync(P->d_counters, 0, sizeof(unsigned long long) * (NPAIRCLASS * NPAIRCLASS * 6 + 1), s));
     const bool mixed = precision == ERI_MIXED;
     if (mixed) {
       k_dmax<<<grid1(P->npair, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_sh_l, P->d_pao1, P->d_pao2,
                                                   P->d_pmol, P->d_mat_off, P->d_mat_n, P->d_Dp, P->d_dmax);
       CK(cudaGetLastError());
     }
-    JKArgs ja;
+    JKArgs ja{};
     KArgs& ka = ja.k;
     ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
     ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Dpf = P->d_Dpf; ka.Kh = K ? P->d_Kh : nullptr;
@@ -1313,6 +1316,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
     ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
     ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
     ka.items = nullptr; ka.nitems = nullptr;
+    ka.guard = P->d_counters + NPAIRCLASS * NPAIRCLASS * 6;
     ja.Jh = J ? P->d_Jh : nullptr;
     P->last_mixed = mixed;
     P->last_do_j = J != nullptr;
@@ -1497,7 +1501,7 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
     k_dmax<<<grid1(P->npair, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_sh_l, P->d_pao1, P->d_pao2,
                                                 P->d_pmol, P->d_mat_off, P->d_mat_n, P->d_Dp, P->d_dmax);
   CK(cudaGetLastError());
-  JKArgs ja;
+  JKArgs ja{};
   KArgs& ka = ja.k;
   ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
   ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Dpf = P->d_Dpf; ka.Kh = P->d_Kh;
@@ -1505,6 +1509,7 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
   ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
   ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
   ka.counter = nullptr;
+  ka.guard = nullptr;
   ja.Jh = P->d_Jh;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -1642,12 +1647,13 @@ extern "C" int eri_set_tiles(eri_plan_t* plan, const int32_t* tiles) {
   if (!P || !tiles) return ERI_EINVAL;
   for (int k = 0; k < NPAIRCLASS * NPAIRCLASS * 2; ++k)
     if (tiles[k] < 0 || tiles[k] > 1024) return ERI_EINVAL;
-  for (int k = 0; k < NPAIRCLASS * NPAIRCLASS * 2; ++k) P->tile_k[k] = tiles[k];
-  if (P->gexec) {
-    cudaDeviceSynchronize();
-    cudaGraphExecDestroy(P->gexec);
+  if (P->gexec) {  // a captured graph carries the old tiles: wait for it on the plan's device, then drop it
+    CK(cudaSetDevice(P->device));
+    CK(cudaDeviceSynchronize());
+    CK(cudaGraphExecDestroy(P->gexec));
     P->gexec = nullptr;
   }
+  for (int k = 0; k < NPAIRCLASS * NPAIRCLASS * 2; ++k) P->tile_k[k] = tiles[k];
   return ERI_OK;
 }
 
@@ -1663,15 +1669,18 @@ int eri_build_jk_scratch(eri_plan_t* plan, const double* D, double* J, double* K
   CK(cudaGetLastError());
   if (K) CK(cudaMemsetAsync(Kh, 0, sizeof(double) * nn, s));
   if (J) CK(cudaMemsetAsync(Jh, 0, sizeof(double) * nn, s));
-  JKArgs ja;
+  JKArgs ja{};
   KArgs& ka = ja.k;
   ka.pd = P->pairdata(); ka.sp = P->spinfo(); ka.bt = P->boystabs();
   ka.rsteps = P->d_rsteps; ka.Dp = Dp; ka.Dpf = nullptr; ka.Kh = K ? Kh : nullptr;
   ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
   ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
-  ka.tau = 0.0f; ka.pmax32 = 0.0f; ka.mixed = 0; ka.tier_want = 0; ka.counter = nullptr;
+  ka.tau = 0.0f; ka.pmax32 = 0.0f; ka.mixed = 0; ka.tier_want = 0; ka.counter = nullptr; ka.guard = nullptr;
   ka.items = nullptr; ka.nitems = nullptr;
   ja.Jh = J ? Jh : nullptr;
+  P->last_mixed = false;
+  P->last_do_j = J != nullptr;
+  P->last_do_k = K != nullptr;
   for (int X = 0; X < NPAIRCLASS; ++X)
     for (int Y = 0; Y <= X; ++Y) {
       ka.wl = P->klist(X, Y);
@@ -1781,8 +1790,9 @@ extern "C" int eri_get_stats(eri_plan_t* plan, eri_stats_t* st) {
     }
   }
   {
-    unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6];
+    unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6 + 1];
     CK(cudaMemcpy(c, P->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+    st->quartets_k_guard = P->last_mixed ? (int64_t)c[NPAIRCLASS * NPAIRCLASS * 6] : 0;
     double fl = 0.0;
     for (int X = 0; X < NPAIRCLASS; ++X)
       for (int Y = 0; Y <= X; ++Y)

@@ -1,0 +1,97 @@
+"""Write the oracle's full FP64 J and K of a seeded workload to tests/golden/.
+
+The stored matrices are the reference for the element-by-element full-size
+parity test of the GPU build (tests/test_gpu_fullsize.py).  They come from the
+oracle alone: J_mn = sum_ls (mn|ls) D_ls and K_ml = sum_ns (mn|ls) D_ns
+(Eq. j_definition, Eq. k_definition) over the canonical quartets whose Schwarz
+bound Q_ab Q_cd >= thresh (Eq. kernel_upperbound), every contracted ERI by
+Obara-Saika / Head-Gordon-Pople, energies E_J = 1/2 tr(DJ), E_K = -1/4 tr(DK)
+(SI Eq. si_E_J_K) in long double.  Nothing here touches the CUDA library.
+
+J and K are symmetric for a symmetric D; the file holds the upper triangles of
+(J + J^T)/2 and (K + K^T)/2 (symmetrising moves an element by rounding only)
+plus the oracle's own energies and Schwarz bounds, keyed by a SHA-256 of the
+inputs (shell table, exponents, raw coefficients, coordinates, D, thresh) so a
+test can tell when the workload generator has changed and the file is stale.
+
+Usage:  python tests/golden/make_oracle_jk.py 1      (about 1.5 h on 8 cores)
+"""
+from __future__ import annotations
+
+import hashlib
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+import workloads  # noqa: E402
+
+THRESH = 1e-12
+
+
+def golden_path(wl: int) -> str:
+    return os.path.join(HERE, f"oracle_jk_w{wl}.npz")
+
+
+def input_hash(basis, D, thresh: float) -> str:
+    """SHA-256 over every input the oracle's J/K depend on."""
+    h = hashlib.sha256()
+    for a in (basis.shell_atom, basis.shell_l, basis.shell_nprim, basis.shell_prim_offset):
+        h.update(np.ascontiguousarray(a, np.int32).tobytes())
+    for a in (basis.exps, basis.coefs, basis.coords, D):
+        h.update(np.ascontiguousarray(a, np.float64).tobytes())
+    h.update(np.float64(thresh).tobytes())
+    return h.hexdigest()
+
+
+def upper(M: np.ndarray) -> np.ndarray:
+    S = 0.5 * (M + M.T)
+    return S[np.triu_indices(M.shape[0])]
+
+
+def from_upper(u: np.ndarray, n: int) -> np.ndarray:
+    M = np.zeros((n, n))
+    iu = np.triu_indices(n)
+    M[iu] = u
+    M.T[iu] = u
+    return M
+
+
+def load(wl: int):
+    """(J, K, E_J, E_K, Q, hash) from the stored file, or None if absent."""
+    p = golden_path(wl)
+    if not os.path.exists(p):
+        return None
+    z = np.load(p)
+    n = int(z["nbf"])
+    return (from_upper(z["J_upper"], n), from_upper(z["K_upper"], n), float(z["E_J"]), float(z["E_K"]),
+            z["Q"], str(z["input_sha256"]))
+
+
+def main(wl: int) -> None:
+    basis, D = workloads.workload(wl)
+    o = oracle.Oracle(basis)
+    t0 = time.time()
+    Q = o.schwarz()
+    J, K = o.jk(D, thresh=THRESH, Q=Q, mode=1)
+    ej, ek = o.energy(D, J, K)
+    dt = time.time() - t0
+    asym = max(float(np.abs(J - J.T).max()), float(np.abs(K - K.T).max()))
+    np.savez_compressed(golden_path(wl), nbf=np.int64(basis.nbf), J_upper=upper(J), K_upper=upper(K),
+                        E_J=np.float64(ej), E_K=np.float64(ek), Q=Q, thresh=np.float64(THRESH),
+                        input_sha256=np.str_(input_hash(basis, D, THRESH)),
+                        oracle_seconds=np.float64(dt), oracle_threads=np.int64(oracle.max_threads()),
+                        max_asymmetry=np.float64(asym))
+    print(f"workload {wl}: nbf {basis.nbf}, E_J {ej:.15e}, E_K {ek:.15e}, {dt:.0f} s on "
+          f"{oracle.max_threads()} threads, max |M - M^T| {asym:.2e} -> {golden_path(wl)}")
+
+
+if __name__ == "__main__":
+    main(int(sys.argv[1]) if len(sys.argv) > 1 else 1)

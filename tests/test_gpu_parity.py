@@ -138,3 +138,5 @@ def test_mixed_precision_w0(eri, tau, etol, mtol):
     assert np.abs(K.cpu().numpy() - Kr).max() < mtol
     if tau > 1:
         assert st["quartets_k_fp32"] == st["quartets_k"]
+    else:  # the paper's default bound still sends part of workload 0 to the FP32 tier
+        assert 0 < st["quartets_k_fp32"] < st["quartets_k"], st

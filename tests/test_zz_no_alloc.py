@@ -32,8 +32,8 @@ def eri():
 
 def _noalloc(eri, plan, D, J, K):
     import torch
-    rc = eri.lib().eri_build_jk_noalloc(plan.h, C.c_void_p(D.data_ptr()), C.c_void_p(J.data_ptr()),
-                                        C.c_void_p(K.data_ptr()),
+    ptr = lambda t: C.c_void_p(t.data_ptr() if t is not None else 0)
+    rc = eri.lib().eri_build_jk_noalloc(plan.h, ptr(D), ptr(J), ptr(K),
                                         C.c_void_p(torch.cuda.current_stream().cuda_stream))
     return rc
 
@@ -74,3 +74,27 @@ def test_noalloc_rejects_plans_above_the_limit(eri):
     J = torch.empty_like(Dt)
     K = torch.empty_like(Dt)
     assert _noalloc(eri, plan, Dt, J, K) == -4  # ERI_EUNSUPPORTED
+
+
+def test_noalloc_j_only_and_k_only(eri):
+    """J alone (eri_build_jk takes the J-engine there, this call the Cartesian
+    path: equal to rounding) and K alone, each twice in a row; the stats then
+    describe the allocation-free call."""
+    import torch
+    basis, D = W.workload(0)
+    plan = eri.Plan(basis, thresh=1e-12)
+    Dt = torch.from_numpy(D).cuda()
+    Jr, _ = plan.build_jk(Dt, want_k=False)
+    _, Kr = plan.build_jk(Dt, want_j=False)
+    Jr, Kr = Jr.cpu().numpy(), Kr.cpu().numpy()
+    for call in range(2):
+        J = torch.full_like(Dt, np.nan)
+        assert _noalloc(eri, plan, Dt, J, None) == 0
+        torch.cuda.synchronize()
+        assert np.abs(J.cpu().numpy() - Jr).max() < TOL, call
+        K = torch.full_like(Dt, np.nan)
+        assert _noalloc(eri, plan, Dt, None, K) == 0
+        torch.cuda.synchronize()
+        assert np.abs(K.cpu().numpy() - Kr).max() < TOL, call
+    st = plan.stats()
+    assert st["quartets_k_fp32"] == 0
