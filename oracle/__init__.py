@@ -39,6 +39,8 @@ def lib():
         L.or_prim_overlap.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, d, d, d]
         L.or_prim_nuclear.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, d, d, d, d]
         L.or_prim_eri.argtypes = [C.c_int] * 4 + [C.c_double] * 4 + [d] * 5
+        L.or_prim_eri_erf.argtypes = [C.c_int] * 4 + [C.c_double] * 4 + [d] * 4 + [C.c_double, d]
+        L.or_set_omega.argtypes = [C.c_void_p, C.c_double]
         L.or_create.argtypes = [C.c_int, C.c_int, i, i, i, i, d, d, d]
         L.or_create.restype = C.c_void_p
         L.or_destroy.argtypes = [C.c_void_p]
@@ -108,6 +110,14 @@ def prim_eri(la, lb, lc, ld, a, b, c, d, A, B, Cc, D):
     return out.reshape(ncart(la), ncart(lb), ncart(lc), ncart(ld))
 
 
+def prim_eri_erf(la, lb, lc, ld, a, b, c, d, A, B, Cc, D, omega):
+    """Primitive long-range ERI [ab| erf(omega r)/r |cd] (Eq. eri_longrange_definition)."""
+    out = np.zeros(ncart(la) * ncart(lb) * ncart(lc) * ncart(ld))
+    lib().or_prim_eri_erf(la, lb, lc, ld, a, b, c, d, _d(_v3(A)), _d(_v3(B)), _d(_v3(Cc)), _d(_v3(D)),
+                          float(omega), _d(out))
+    return out.reshape(ncart(la), ncart(lb), ncart(lc), ncart(ld))
+
+
 def max_threads() -> int:
     return int(lib().or_max_threads())
 
@@ -134,6 +144,11 @@ class Oracle:
         if getattr(self, "h", None) and _lib is not None:
             _lib.or_destroy(self.h)
             self.h = None
+
+    def set_omega(self, omega):
+        """Two-electron operator of every later ERI / J / K / gradient call:
+        0 = 1/r, omega > 0 = erf(omega r)/r.  Schwarz bounds stay Coulomb."""
+        lib().or_set_omega(self.h, float(omega))
 
     def set_coords(self, coords):
         c = np.ascontiguousarray(coords, np.float64)

@@ -24,7 +24,11 @@
  *     centres differentiated (SI Sec. 1.4), NOT the bra-only shortcut of
  *     SI Eq. si_dE_J / si_dE_K, so that the shortcut gets checked;
  *   - one-electron overlap (Eq. overlap_definition) and point-charge attraction
- *     (Eq. v1e_definition2), used only to pin the ERIs and normalisation.
+ *     (Eq. v1e_definition2), used only to pin the ERIs and normalisation;
+ *   - the long-range operator erf(omega r)/r (Sec. 2.5,
+ *     Eq. eri_longrange_definition) in place of 1/r in every ERI, J, K and
+ *     gradient (or_set_omega), through the same recurrences with the
+ *     attenuated auxiliary integrals.
  *
  * Readings where the paper is silent:
  *   - normalisation: every primitive component gets
@@ -230,8 +234,8 @@ static void hrr(int la, int lb, const double AB[3], int nouter, int ninner, cons
  *                               + e_i/(2(p+q)) [e-1_i,0|f0]^(m+1)
  * then HRR on the bra and on the ket.  The base case is Eq. eri_base_case.
  */
-void or_prim_eri(int la, int lb, int lc, int ld, double a, double b, double c, double d, const double* A,
-                 const double* B, const double* C, const double* D, double* out) {
+static void prim_eri_op(int la, int lb, int lc, int ld, double a, double b, double c, double d, const double* A,
+                        const double* B, const double* C, const double* D, double omega, double* out) {
   int E = la + lb, F = lc + ld, L = E + F;
   double p = a + b, q = c + d, rho = p * q / (p + q);
   double P[3], Q[3], W[3], PA[3], WP[3], QC[3], WQ[3], AB[3], CD[3];
@@ -251,8 +255,26 @@ void or_prim_eri(int la, int lb, int lc, int ld, double a, double b, double c, d
     pq2 += (P[i] - Q[i]) * (P[i] - Q[i]);
   }
   double Fm[32];
-  or_boys(L, rho * pq2, Fm);
   double pref = 2.0 * pow(OR_PI, 2.5) / (p * q * sqrt(p + q)) * exp(-a * b / p * ab2) * exp(-c * d / q * cd2);
+  if (omega > 0.0) {
+    /* erf(omega r)/r (Eq. eri_longrange_definition): writing the operator as
+     * (2/sqrt(pi)) int_0^omega exp(-t^2 r^2) dt and following the Coulomb
+     * derivation, the u = t/sqrt(rho + t^2) integral of the Boys function stops
+     * at u_max^2 = s = omega^2/(omega^2 + rho), so the auxiliary integrals become
+     *   [00|00]^(m) = pref * s^(m + 1/2) * F_m(s * rho |PQ|^2)
+     * (the prefactor and argument of Eq. eri_longrange_formula); the
+     * recurrences below act on the auxiliaries and do not change. */
+    double sw = omega * omega / (omega * omega + rho);
+    or_boys(L, sw * rho * pq2, Fm);
+    pref *= sqrt(sw);
+    double sm = 1.0;
+    for (int m = 0; m <= L; ++m) {
+      Fm[m] *= sm;
+      sm *= sw;
+    }
+  } else {
+    or_boys(L, rho * pq2, Fm);
+  }
 
   int nE = ncart_cum(E), nF = ncart_cum(F), nm = L + 1;
   double* V = (double*)calloc((size_t)nE * nF * nm, sizeof(double));
@@ -328,6 +350,18 @@ void or_prim_eri(int la, int lb, int lc, int ld, double a, double b, double c, d
   free(U);
 }
 
+/* Primitive Coulomb ERI [ab|cd], out[na][nb][nc][nd] (Eq. eri_definition). */
+void or_prim_eri(int la, int lb, int lc, int ld, double a, double b, double c, double d, const double* A,
+                 const double* B, const double* C, const double* D, double* out) {
+  prim_eri_op(la, lb, lc, ld, a, b, c, d, A, B, C, D, 0.0, out);
+}
+
+/* Primitive long-range ERI [ab| erf(omega r)/r |cd] (Eq. eri_longrange_definition), omega > 0. */
+void or_prim_eri_erf(int la, int lb, int lc, int ld, double a, double b, double c, double d, const double* A,
+                     const double* B, const double* C, const double* D, double omega, double* out) {
+  prim_eri_op(la, lb, lc, ld, a, b, c, d, A, B, C, D, omega, out);
+}
+
 /*
  * Primitive point-charge attraction (a| 1/|r-C| |b), out[na][nb], unit charge,
  * Eq. v1e_definition2, by the Obara-Saika three-centre recurrence:
@@ -391,6 +425,7 @@ typedef struct {
   double* exps;
   double* cn;     /* coefficient of the normalised (l,0,0) component, per primitive */
   double* coords; /* natom*3 */
+  double omega;   /* 0: Coulomb 1/r; > 0: erf(omega r)/r (or_set_omega) */
 } or_ctx;
 
 static double norm_l00(double alpha, int l) {
@@ -459,6 +494,13 @@ void or_set_coords(void* h, const double* coords) {
   or_ctx* c = (or_ctx*)h;
   memcpy(c->coords, coords, sizeof(double) * c->natom * 3);
 }
+
+/* Two-electron operator of every ERI, J, K and gradient below: omega = 0 is the
+ * Coulomb operator 1/r, omega > 0 the long-range erf(omega r)/r of
+ * Eq. eri_longrange_definition.  The Schwarz bounds (or_schwarz) stay those of
+ * 1/r: erfc(omega r)/r is a positive-definite kernel too, so
+ * (ab|erf|ab) <= (ab|ab) and the Coulomb Q bound the attenuated quartets. */
+void or_set_omega(void* h, double omega) { ((or_ctx*)h)->omega = omega > 0.0 ? omega : 0.0; }
 
 int or_nbf(void* h) { return ((or_ctx*)h)->nbf; }
 void or_ao_offsets(void* h, int32_t* out) {
@@ -548,9 +590,8 @@ static void apply_comp_factors(int la, int lb, int lc, int ld, double* out) {
   }
 }
 
-/* contracted, normalised ERI block (ab|cd), out[na][nb][nc][nd] */
-void or_eri_block(void* h, int sa, int sb, int sc, int sd, double* out) {
-  or_ctx* c = (or_ctx*)h;
+/* contracted, normalised ERI block (ab|cd) of the operator selected by omega */
+static void eri_block_op(or_ctx* c, int sa, int sb, int sc, int sd, double omega, double* out) {
   int la = c->l[sa], lb = c->l[sb], lc = c->l[sc], ld = c->l[sd];
   int n = ncart(la) * ncart(lb) * ncart(lc) * ncart(ld);
   double* blk = (double*)malloc(sizeof(double) * n);
@@ -560,13 +601,20 @@ void or_eri_block(void* h, int sa, int sb, int sc, int sd, double* out) {
       for (int kc = 0; kc < c->nprim[sc]; ++kc)
         for (int kd = 0; kd < c->nprim[sd]; ++kd) {
           int pa = c->poff[sa] + ka, pb = c->poff[sb] + kb, pc = c->poff[sc] + kc, pd = c->poff[sd] + kd;
-          or_prim_eri(la, lb, lc, ld, c->exps[pa], c->exps[pb], c->exps[pc], c->exps[pd], ctr(c, sa), ctr(c, sb),
-                      ctr(c, sc), ctr(c, sd), blk);
+          prim_eri_op(la, lb, lc, ld, c->exps[pa], c->exps[pb], c->exps[pc], c->exps[pd], ctr(c, sa), ctr(c, sb),
+                      ctr(c, sc), ctr(c, sd), omega, blk);
           double w = c->cn[pa] * c->cn[pb] * c->cn[pc] * c->cn[pd];
           for (int i = 0; i < n; ++i) out[i] += w * blk[i];
         }
   apply_comp_factors(la, lb, lc, ld, out);
   free(blk);
+}
+
+/* contracted, normalised ERI block (ab|cd), out[na][nb][nc][nd], of the
+ * context's operator (or_set_omega) */
+void or_eri_block(void* h, int sa, int sb, int sc, int sd, double* out) {
+  or_ctx* c = (or_ctx*)h;
+  eri_block_op(c, sa, sb, sc, sd, c->omega, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -593,7 +641,7 @@ void or_schwarz(void* h, float* Q) {
     for (int b = 0; b <= a; ++b) {
       int na = ncart(c->l[a]), nb = ncart(c->l[b]);
       double* blk = (double*)malloc(sizeof(double) * na * nb * na * nb);
-      or_eri_block(h, a, b, a, b, blk);
+      eri_block_op(c, a, b, a, b, 0.0, blk); /* Coulomb Q, whatever the operator */
       double mx = 0.0;
       for (int i = 0; i < na; ++i)
         for (int j = 0; j < nb; ++j) {
@@ -880,9 +928,11 @@ static void eri_deriv_block(or_ctx* c, int s[4], int which, double* out) {
             R[k] = ctr(c, s[k]);
             w *= c->cn[pp[k]];
           }
-          or_prim_eri(lup[0], lup[1], lup[2], lup[3], ex[0], ex[1], ex[2], ex[3], R[0], R[1], R[2], R[3], up);
+          prim_eri_op(lup[0], lup[1], lup[2], lup[3], ex[0], ex[1], ex[2], ex[3], R[0], R[1], R[2], R[3], c->omega,
+                      up);
           if (Ndn > 0)
-            or_prim_eri(ldn[0], ldn[1], ldn[2], ldn[3], ex[0], ex[1], ex[2], ex[3], R[0], R[1], R[2], R[3], dn);
+            prim_eri_op(ldn[0], ldn[1], ldn[2], ldn[3], ex[0], ex[1], ex[2], ex[3], R[0], R[1], R[2], R[3],
+                        c->omega, dn);
           double alpha = ex[which];
           int idx[4];
           for (idx[0] = 0; idx[0] < nn[0]; ++idx[0])

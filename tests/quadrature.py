@@ -2,7 +2,8 @@
 
 Independent of both the oracle and the CUDA path: no recurrence and no Boys
 function.  The Coulomb operator is written as
-    1/r = (2/sqrt(pi)) int_0^inf exp(-t^2 r^2) dt,
+    1/r = (2/sqrt(pi)) int_0^inf exp(-t^2 r^2) dt
+(and the long-range erf(omega r)/r as the same integral up to t = omega),
 which makes every Cartesian direction separate for fixed t.  Each 1-D (or
 coupled 2-D) Gaussian-times-polynomial integral is done exactly by
 Gauss-Hermite quadrature after completing the square (a Cholesky map for the
@@ -91,7 +92,9 @@ def _eri_1d_all(li, lj, lk, ll, a, b, c, d, A, B, Cc, D, t):
     return out
 
 
-def prim_eri(la, lb, lc, ld, a, b, c, d, A, B, Cc, D):
+def prim_eri(la, lb, lc, ld, a, b, c, d, A, B, Cc, D, t_max=np.inf):
+    """Primitive ERI of 1/r, or of erf(omega r)/r = (2/sqrt(pi)) int_0^omega
+    exp(-t^2 r^2) dt with t_max = omega."""
     ca, cb, cc, cd = cart_list(la), cart_list(lb), cart_list(lc), cart_list(ld)
     A, B, Cc, D = (np.asarray(v, float) for v in (A, B, Cc, D))
 
@@ -106,5 +109,5 @@ def prim_eri(la, lb, lc, ld, a, b, c, d, A, B, Cc, D):
                                                * tabs[2][u[2], v[2], w_[2], z[2]])
         return out.ravel()
 
-    val, _ = quad_vec(f, 0.0, np.inf, epsabs=0.0, epsrel=1e-13, limit=400)
+    val, _ = quad_vec(f, 0.0, t_max, epsabs=0.0, epsrel=1e-13, limit=400)
     return (2.0 / np.sqrt(np.pi) * val).reshape(len(ca), len(cb), len(cc), len(cd))
