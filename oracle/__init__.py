@@ -41,6 +41,8 @@ def lib():
         L.or_prim_eri.argtypes = [C.c_int] * 4 + [C.c_double] * 4 + [d] * 5
         L.or_prim_eri_erf.argtypes = [C.c_int] * 4 + [C.c_double] * 4 + [d] * 4 + [C.c_double, d]
         L.or_set_omega.argtypes = [C.c_void_p, C.c_double]
+        L.or_nuclear.argtypes = [C.c_void_p, C.c_int, d, d, d]
+        L.or_nuclear_grad.argtypes = [C.c_void_p, d, C.c_int, d, d, d, d]
         L.or_create.argtypes = [C.c_int, C.c_int, i, i, i, i, d, d, d]
         L.or_create.restype = C.c_void_p
         L.or_destroy.argtypes = [C.c_void_p]
@@ -169,6 +171,24 @@ class Oracle:
         out = np.zeros(ncart(self.l[a]) * ncart(self.l[b]))
         lib().or_nuclear_block(self.h, a, b, _d(_v3(Cc)), _d(out))
         return out.reshape(ncart(self.l[a]), ncart(self.l[b]))
+
+    def nuclear(self, q, Cxyz):
+        """V_mn = sum_C q_C (m|1/|r-C||n) over point charges q[nc] at Cxyz[nc, 3]."""
+        q = np.ascontiguousarray(q, np.float64).reshape(-1)
+        Cc = np.ascontiguousarray(Cxyz, np.float64).reshape(-1, 3)
+        V = np.zeros((self.nbf, self.nbf))
+        lib().or_nuclear(self.h, int(q.shape[0]), _d(q), _d(Cc), _d(V))
+        return V
+
+    def nuclear_grad(self, D, q, Cxyz):
+        """(dE/dR [natom, 3], dE/dC [nc, 3]) of E_V = sum D_mn V_mn, D fixed."""
+        q = np.ascontiguousarray(q, np.float64).reshape(-1)
+        Cc = np.ascontiguousarray(Cxyz, np.float64).reshape(-1, 3)
+        gA = np.zeros((self.basis.natom, 3))
+        gC = np.zeros((q.shape[0], 3))
+        lib().or_nuclear_grad(self.h, _d(np.ascontiguousarray(D, np.float64)), int(q.shape[0]), _d(q), _d(Cc),
+                              _d(gA), _d(gC))
+        return gA, gC
 
     def eri_block(self, a, b, c, d):
         sh = [ncart(self.l[s]) for s in (a, b, c, d)]

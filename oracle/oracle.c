@@ -23,8 +23,12 @@
  *   - E_J and E_K of SI Eq. si_E_J_K and their nuclear gradient with all four
  *     centres differentiated (SI Sec. 1.4), NOT the bra-only shortcut of
  *     SI Eq. si_dE_J / si_dE_K, so that the shortcut gets checked;
- *   - one-electron overlap (Eq. overlap_definition) and point-charge attraction
- *     (Eq. v1e_definition2), used only to pin the ERIs and normalisation;
+ *   - one-electron overlap (Eq. overlap_definition), used to pin the ERIs and
+ *     normalisation;
+ *   - point-charge attraction (Eq. v1e_definition2) by the Obara-Saika
+ *     three-centre recurrence, the matrix V = sum_C q_C (m|1/|r-C||n)
+ *     (Eq. v1e_definition) and the gradient of sum D_mn V_mn with respect to
+ *     the basis centres and the charge positions (SI Sec. 1.3);
  *   - the long-range operator erf(omega r)/r (Sec. 2.5,
  *     Eq. eri_longrange_definition) in place of 1/r in every ERI, J, K and
  *     gradient (or_set_omega), through the same recurrences with the
@@ -881,6 +885,143 @@ void or_k_block(void* h, const double* Dm, double thresh, const float* Q, int a,
     for (int i = 0; i < na * nc; ++i) out[i] += acc[i];
     free(acc);
     free(X);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Point-charge attraction matrix and its gradient (Sec. 2.4)                 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Contracted attraction block of shells (sa, sb) with their angular momenta
+ * shifted by (da, db) in {-1, 0, +1}, summed over the point charges with
+ * weights q, out[ncart(la+da)][ncart(lb+db)].  `wexp` multiplies each
+ * primitive term by 2 x exponent of the raised shell (0: none, 1: shell a,
+ * 2: shell b) for the raising half of the derivative rule.  No component
+ * factors applied (the caller applies the ones of the unshifted functions).
+ */
+static void nuc_block_shift(const or_ctx* c, int sa, int da, int sb, int db, int nc, const double* q,
+                            const double* C, int wexp, double* out) {
+  int la = c->l[sa] + da, lb = c->l[sb] + db, na = ncart(la), nb = ncart(lb);
+  double* blk = (double*)malloc(sizeof(double) * na * nb);
+  for (int i = 0; i < na * nb; ++i) out[i] = 0.0;
+  for (int ka = 0; ka < c->nprim[sa]; ++ka)
+    for (int kb = 0; kb < c->nprim[sb]; ++kb) {
+      int pa = c->poff[sa] + ka, pb = c->poff[sb] + kb;
+      double w = c->cn[pa] * c->cn[pb];
+      if (wexp == 1) w *= 2.0 * c->exps[pa];
+      if (wexp == 2) w *= 2.0 * c->exps[pb];
+      for (int k = 0; k < nc; ++k) {
+        or_prim_nuclear(la, lb, c->exps[pa], c->exps[pb], ctr(c, sa), ctr(c, sb), C + 3 * k, blk);
+        for (int i = 0; i < na * nb; ++i) out[i] += w * q[k] * blk[i];
+      }
+    }
+  free(blk);
+}
+
+/*
+ * V_mn = sum_C q_C (m| 1/|r - C| |n) (Eq. v1e_definition, Eq. v1e_summation_over_C)
+ * over every pair of shells, V nbf x nbf (row-major), charges q[nc] at C[nc*3].
+ */
+void or_nuclear(void* h, int nc, const double* q, const double* C, double* V) {
+  or_ctx* c = (or_ctx*)h;
+  int ns = c->nshell, n = c->nbf;
+#pragma omp parallel for schedule(dynamic)
+  for (int a = 0; a < ns; ++a) {
+    double blk[100];
+    for (int b = 0; b < ns; ++b) {
+      int na = ncart(c->l[a]), nb = ncart(c->l[b]);
+      nuc_block_shift(c, a, 0, b, 0, nc, q, C, 0, blk);
+      for (int i = 0; i < na; ++i) {
+        int ci[3];
+        cart_comp(c->l[a], i, ci);
+        for (int j = 0; j < nb; ++j) {
+          int cj[3];
+          cart_comp(c->l[b], j, cj);
+          V[(size_t)(c->aoff[a] + i) * n + c->aoff[b] + j] =
+              blk[i * nb + j] * comp_factor(ci[0], ci[1], ci[2]) * comp_factor(cj[0], cj[1], cj[2]);
+        }
+      }
+    }
+  }
+}
+
+/*
+ * Gradient of E_V = sum_mn D_mn V_mn (D held fixed): gA[natom*3] with respect
+ * to the basis-function centres, gC[nc*3] with respect to the charge positions.
+ * Centre A of m and B of n are differentiated by the raising/lowering rule
+ * d/dA_t G_i = 2a G_{i+1_t} - i_t G_{i-1_t} at primitive level (each function
+ * keeps its own normalisation).  Each term (m, n, C) depends on A, B and C only
+ * through their differences, so d/dC_t = -(d/dA_t + d/dB_t) term by term
+ * (translational invariance); the finite-difference pins check all three.
+ */
+void or_nuclear_grad(void* h, const double* Dm, int nc, const double* q, const double* C, double* gA, double* gC) {
+  or_ctx* c = (or_ctx*)h;
+  int ns = c->nshell, n = c->nbf, nat = c->natom;
+  for (int i = 0; i < 3 * nat; ++i) gA[i] = 0.0;
+  for (int i = 0; i < 3 * nc; ++i) gC[i] = 0.0;
+#pragma omp parallel
+  {
+    double* tA = (double*)calloc(3 * nat, sizeof(double));
+    double* tC = (double*)calloc(3 * (nc > 0 ? nc : 1), sizeof(double));
+    double up[150], dn[100];
+#pragma omp for schedule(dynamic)
+    for (int a = 0; a < ns; ++a)
+      for (int b = 0; b < ns; ++b)
+        for (int k = 0; k < nc; ++k) {
+          double g[2][3] = {{0, 0, 0}, {0, 0, 0}}; /* d/dA, d/dB of sum_mn D_mn V_mnC */
+          int la = c->l[a], lb = c->l[b], na = ncart(la), nb = ncart(lb);
+          for (int side = 0; side < 2; ++side) {
+            int lx = side == 0 ? la : lb;
+            int nup_a = ncart(la + (side == 0)), nup_b = ncart(lb + (side == 1));
+            nuc_block_shift(c, a, side == 0, b, side == 1, 1, q + k, C + 3 * k, side + 1, up);
+            int ndn_a = 0, ndn_b = 0;
+            if (lx > 0) {
+              nuc_block_shift(c, a, -(side == 0), b, -(side == 1), 1, q + k, C + 3 * k, 0, dn);
+              ndn_a = ncart(la - (side == 0));
+              ndn_b = ncart(lb - (side == 1));
+            }
+            for (int i = 0; i < na; ++i) {
+              int ci[3];
+              cart_comp(la, i, ci);
+              for (int j = 0; j < nb; ++j) {
+                int cj[3];
+                cart_comp(lb, j, cj);
+                double dmn = Dm[(size_t)(c->aoff[a] + i) * n + c->aoff[b] + j] *
+                             comp_factor(ci[0], ci[1], ci[2]) * comp_factor(cj[0], cj[1], cj[2]);
+                int* cw = side == 0 ? ci : cj;
+                for (int t = 0; t < 3; ++t) {
+                  int cu[3] = {cw[0], cw[1], cw[2]};
+                  cu[t] += 1;
+                  double v;
+                  if (side == 0) v = up[cart_in_shell(cu[0], cu[1], cu[2]) * nup_b + j];
+                  else v = up[i * nup_b + cart_in_shell(cu[0], cu[1], cu[2])];
+                  if (cw[t] > 0) {
+                    int cd[3] = {cw[0], cw[1], cw[2]};
+                    cd[t] -= 1;
+                    if (side == 0) v -= cw[t] * dn[cart_in_shell(cd[0], cd[1], cd[2]) * ndn_b + j];
+                    else v -= cw[t] * dn[i * ndn_b + cart_in_shell(cd[0], cd[1], cd[2])];
+                  }
+                  g[side][t] += dmn * v;
+                }
+              }
+            }
+            (void)nup_a;
+            (void)ndn_a;
+          }
+          for (int t = 0; t < 3; ++t) {
+            tA[3 * c->atom[a] + t] += g[0][t];
+            tA[3 * c->atom[b] + t] += g[1][t];
+            tC[3 * k + t] -= g[0][t] + g[1][t];
+          }
+        }
+#pragma omp critical
+    {
+      for (int i = 0; i < 3 * nat; ++i) gA[i] += tA[i];
+      for (int i = 0; i < 3 * nc; ++i) gC[i] += tC[i];
+    }
+    free(tA);
+    free(tC);
   }
 }
 
