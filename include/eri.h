@@ -5,6 +5,8 @@
  * Integrals in the TeraChem Software Package to f Type Orbitals":
  *   basis functions      Sec. 2.1, Eq. contracted_basis, Eq. primtive_basis
  *   ERIs                 Sec. 2.5, Eq. eri_definition, Eq. eri_formula
+ *   long-range ERIs      Sec. 2.5, Eq. eri_longrange_definition, Eq. eri_longrange_formula
+ *   point charges        Sec. 2.4, Eq. v1e_definition, Eq. v1e_formula; SI Sec. 1.3
  *   J and K              Eq. j_definition (J_mn = sum_ls (mn|ls) D_ls),
  *                        Eq. k_definition (K_ml = sum_ns (mn|ls) D_ns)
  *   screening            Eq. cauchy_schwarz_bound, Eq. kernel_upperbound
@@ -72,6 +74,16 @@ typedef struct {
   int32_t j_engine;   /* J-only builds (K == NULL): 1 = Hermite J-engine of Eq. j_formula
                          (default), 0 = contraction of Cartesian ERIs */
   int32_t profile;    /* 1: record CUDA events around every class launch (see eri_get_profile) */
+  const char* tune_cache; /* NULL, or a text file of autotuned tile tables: eri_plan loads the entry for
+                             this device, plan shape (nbf, molecules, shell pairs) and opts.precision if
+                             the file holds one, and eri_autotune stores its result there (replacing
+                             the entry of the same key).  The path is copied. */
+  int32_t deterministic;  /* 1: J/K builds (also the J-engine, graph and allocation-free builds) and
+                             eri_jk_grad accumulate in 64-bit fixed point (scale 2^46, resolution
+                             1.4e-14) with integer atomics, which are order-independent: repeated calls
+                             give bit-identical results.  Accumulated magnitudes must stay below 2^17;
+                             an element above 2^16 sets the device status (see eri_check).  0 (default):
+                             FP64 atomics, results equal to rounding only. */
 } eri_opts_t;
 
 typedef struct {
@@ -178,8 +190,9 @@ int eri_build_jk_graph(eri_plan_t* plan, const double* D, double* J, double* K, 
  * compacted list), the windows sized so the current length takes about trial_ms
  * and every resident warp gets several tiles; a length replaces the default
  * only if it is more than 5 % faster twice.  Synchronises `stream` repeatedly; writes only plan scratch; J and
- * K are unchanged.  Later builds (and graphs captured after it) use the tiles.
- * Errors: ERI_EINVAL (trial_ms <= 0, NULL, bad precision), ERI_ECUDA.
+ * K are unchanged.  Later builds (and graphs captured after it) use the tiles.  With opts.tune_cache set,
+ * the result is stored in that file under this plan's key and precision.
+ * Errors: ERI_EINVAL (trial_ms <= 0, NULL, bad precision, tune_cache not writable), ERI_ECUDA.
  */
 int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision, double trial_ms, void* stream);
 
@@ -200,6 +213,21 @@ int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision, double tr
  * Errors: ERI_EINVAL (nshard < 1 or shard outside 0..nshard-1).
  */
 int eri_plan_set_shard(eri_plan_t* plan, int32_t shard, int32_t nshard);
+
+/*
+ * Two-electron operator of this plan's later builds (eri_build_jk, the graph
+ * build, the J-engine, eri_build_jk_noalloc) and gradients (eri_jk_grad):
+ * omega = 0 (the default) is the Coulomb operator 1/r, omega > 0 the
+ * long-range operator erf(omega r)/r of range-separated functionals (Sec. 2.5,
+ * Eq. eri_longrange_definition).  Its ERIs follow Eq. eri_longrange_formula:
+ * the same McMurchie-Davidson chain with rho -> s rho and the prefactor times
+ * sqrt(s), s = omega^2 / (omega^2 + rho).  The Schwarz bounds, lists and the
+ * mixed-precision tier test stay those of 1/r (a valid upper bound:
+ * erfc(omega r)/r is positive definite, so (ab|erf|ab) <= (ab|ab)).  Host
+ * only; a captured graph build is dropped when omega changes (after a device
+ * wait).  Errors: ERI_EINVAL (NULL, omega < 0, NaN or omega >= 1e30).
+ */
+int eri_plan_set_omega(eri_plan_t* plan, double omega);
 
 /*
  * Read or set the plan's tile table (host int32 [10][10][2] indexed
@@ -260,6 +288,15 @@ typedef struct {
  */
 int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t cap, int32_t* count);
 
+/*
+ * Device-side checks: synchronises the plan's device and returns ERI_EDEVICE
+ * (clearing the status word) if a kernel of this plan reported a problem
+ * since the last check: in deterministic builds, an accumulated element
+ * whose magnitude exceeded 2^16 (half the fixed-point range, so its value may
+ * have wrapped).  ERI_OK otherwise.
+ */
+int eri_check(eri_plan_t* plan);
+
 /* Statistics of the plan and of its last build (host copy; synchronises). */
 int eri_get_stats(eri_plan_t* plan, eri_stats_t* stats);
 
@@ -289,6 +326,35 @@ int eri_get_stats(eri_plan_t* plan, eri_stats_t* stats);
  */
 #define ERI_NOALLOC_MAX_NBF 256
 int eri_build_jk_noalloc(eri_plan_t* plan, const double* D, double* J, double* K, void* stream);
+
+/*
+ * Point-charge attraction matrix (Sec. 2.4, Eq. v1e_definition and
+ * Eq. v1e_summation_over_C; nuclei or QM/MM charges):
+ *   V_mn = sum_C q_C (m| 1/|r - C| |n)
+ * over every shell pair (no screening), by Eq. v1e_formula with the sum over
+ * charges taken in Hermite space per primitive pair.  q: DEVICE, ncharge
+ * doubles (the charges, signed: a nucleus of atomic number Z attracts
+ * electrons with q = -Z in the electronic Hamiltonian); xyz: DEVICE,
+ * ncharge x 3 doubles (bohr); V: DEVICE, nbf x nbf (packed per molecule for a
+ * batched plan; every molecule sees every charge), overwritten.  ncharge = 0
+ * gives V = 0.  The first call on a plan builds its primitive-pair lists (a
+ * host wait); later calls only enqueue work.  Uses plan scratch, so it is
+ * stream-ordered with the plan's builds.
+ * Errors: ERI_EINVAL (NULL, ncharge < 0), ERI_ENOMEM, ERI_ECUDA.
+ */
+int eri_nuclear(eri_plan_t* plan, int32_t ncharge, const double* q, const double* xyz, double* V, void* stream);
+
+/*
+ * Gradient of E_V = sum_mn D_mn V_mn with D held fixed (SI Sec. 1.3,
+ * Eq. si_v1e_derivative_A, _B and _C): dEdR (DEVICE, natom x 3) with respect to
+ * the basis-function centres, dEdC (DEVICE, ncharge x 3, may be NULL) with
+ * respect to the charge positions; both overwritten.  Centre A by the
+ * raising/lowering rule on the Hermite coefficients, C by dR/dC = -R_{P+1},
+ * B by translational invariance of each (pair, charge) term.  D as for
+ * eri_build_jk.  Errors as for eri_nuclear.
+ */
+int eri_nuclear_grad(eri_plan_t* plan, const double* D, int32_t ncharge, const double* q, const double* xyz,
+                     double* dEdR, double* dEdC, void* stream);
 
 /*
  * Measurement utility (not a step of the method): the FP64 (precision =

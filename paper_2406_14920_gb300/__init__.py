@@ -38,7 +38,8 @@ class BasisT(C.Structure):
 
 class OptsT(C.Structure):
     _fields_ = [("thresh", C.c_double), ("precision", C.c_int32), ("mixed_tau", C.c_double),
-                ("device", C.c_int32), ("j_engine", C.c_int32), ("profile", C.c_int32)]
+                ("device", C.c_int32), ("j_engine", C.c_int32), ("profile", C.c_int32),
+                ("tune_cache", C.c_char_p), ("deterministic", C.c_int32)]
 
 
 class LaunchProfT(C.Structure):
@@ -73,15 +74,19 @@ def lib():
         L.eri_autotune.argtypes = [vp, vp, i32, C.c_double, vp]
         L.eri_get_tiles.argtypes = [vp, C.POINTER(C.c_int32)]
         L.eri_plan_set_shard.argtypes = [vp, i32, i32]
+        L.eri_plan_set_omega.argtypes = [vp, C.c_double]
         L.eri_set_tiles.argtypes = [vp, C.POINTER(C.c_int32)]
         L.eri_energy.argtypes = [vp, vp, vp, vp, vp, vp]
         L.eri_jk_grad.argtypes = [vp, vp, vp, i32, i32, vp]
         L.eri_get_lists.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.eri_get_stats.argtypes = [vp, C.POINTER(StatsT)]
+        L.eri_check.argtypes = [vp]
         L.eri_get_profile.argtypes = [vp, C.POINTER(LaunchProfT), i32, C.POINTER(C.c_int32)]
         L.eri_build_jk_noalloc.argtypes = [vp, vp, vp, vp, vp]
         L.eri_peak_probe.argtypes = [i32, i32, C.POINTER(C.c_double), vp]
+        L.eri_nuclear.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.eri_nuclear_grad.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
         L.eri_plan_destroy.argtypes = [vp]
         L.eri_strerror.argtypes = [C.c_int]
         L.eri_strerror.restype = C.c_char_p
@@ -147,7 +152,7 @@ class Plan:
     """
 
     def __init__(self, basis, coords=None, thresh=1e-12, precision=ERI_FP64, mixed_tau=1e-5, device=None,
-                 j_engine=True, profile=False):
+                 j_engine=True, profile=False, tune_cache=None, deterministic=False):
         L = lib()
         self.batched = isinstance(basis, (list, tuple))
         bases = list(basis) if self.batched else [basis]
@@ -177,6 +182,8 @@ class Plan:
         o.device = -1 if device is None else int(device)
         o.j_engine = int(bool(j_engine))
         o.profile = int(bool(profile))
+        o.tune_cache = os.fsencode(tune_cache) if tune_cache else None
+        o.deterministic = int(bool(deterministic))
         h = C.c_void_p()
         if self.batched:
             bp = (C.POINTER(BasisT) * len(bases))(*[C.pointer(bts[m]) for m in range(len(bases))])
@@ -290,6 +297,11 @@ class Plan:
         all-reduce them over the GPUs).  (0, 1) = the whole build."""
         _check(lib().eri_plan_set_shard(self.h, int(shard), int(nshard)), "eri_plan_set_shard")
 
+    def set_omega(self, omega):
+        """Two-electron operator of later builds and gradients: 0 = 1/r,
+        omega > 0 = erf(omega r)/r (eri_plan_set_omega)."""
+        _check(lib().eri_plan_set_omega(self.h, float(omega)), "eri_plan_set_omega")
+
     def tiles(self):
         t = np.zeros(200, np.int32)
         _check(lib().eri_get_tiles(self.h, t.ctypes.data_as(C.POINTER(C.c_int32))), "eri_get_tiles")
@@ -327,6 +339,32 @@ class Plan:
                "eri_jk_grad")
         return out
 
+    def nuclear(self, q, xyz, V=None, stream=None):
+        """V_mn = sum_C q_C (m|1/|r-C||n) for charges q [nc] at xyz [nc, 3]
+        (float64 CUDA tensors); eri_nuclear."""
+        import torch
+        nc = int(q.numel())
+        if V is None:
+            V = torch.empty(self._mat_shape(), dtype=torch.float64, device=xyz.device)
+        _require(q, nc, "q", self.device)
+        _require(xyz, 3 * nc, "xyz", self.device)
+        _require(V, self.nmat, "V", self.device)
+        _check(lib().eri_nuclear(self.h, nc, _ptr(q), _ptr(xyz), _ptr(V), _stream_ptr(stream)), "eri_nuclear")
+        return V
+
+    def nuclear_grad(self, D, q, xyz, want_charges=True, stream=None):
+        """(dE/dR [natom, 3], dE/dC [nc, 3] or None) of E_V = sum D V; eri_nuclear_grad."""
+        import torch
+        nc = int(q.numel())
+        gR = torch.empty((self.natom, 3), dtype=torch.float64, device=D.device)
+        gC = torch.empty((nc, 3), dtype=torch.float64, device=D.device) if want_charges else None
+        _require(D, self.nmat, "D", self.device)
+        _require(q, nc, "q", self.device)
+        _require(xyz, 3 * nc, "xyz", self.device)
+        _check(lib().eri_nuclear_grad(self.h, _ptr(D), nc, _ptr(q), _ptr(xyz), _ptr(gR), _ptr(gC),
+                                      _stream_ptr(stream)), "eri_nuclear_grad")
+        return gR, gC
+
     def lists(self):
         Q = np.zeros(self.npair, np.float32)
         sig = np.zeros(self.npair, np.int32)
@@ -345,6 +383,10 @@ class Plan:
         n = C.c_int32()
         _check(lib().eri_get_profile(self.h, buf, 256, C.byref(n)), "eri_get_profile")
         return [{k: getattr(buf[i], k) for k, _ in LaunchProfT._fields_} for i in range(min(n.value, 256))]
+
+    def check(self):
+        """Raise EriError(ERI_EDEVICE) if a kernel of this plan reported a problem (eri_check)."""
+        _check(lib().eri_check(self.h), "eri_check")
 
     def stats(self):
         s = StatsT()

@@ -1,13 +1,17 @@
 """Build the CUDA library libgb300eri.so in-tree (sm_103a only).
 
 Each csrc/*.cu is compiled to an object in parallel (one nvcc per file), then
-linked into paper_2406_14920_gb300/libgb300eri.so.  Objects go to _build/
-(ignored by git).  Rebuilds only what changed (any header change rebuilds all).
+linked into paper_2406_14920_gb300/libgb300eri.so.  csrc/k_unit.cu is compiled
+once per entry of csrc/units.h (bra class, precision, ket classes, passed as
+-D flags), so the class kernels of one bra class compile in parallel.  Objects
+go to _build/ (ignored by git).  Rebuilds only what changed (any header change
+rebuilds all).
 """
 from __future__ import annotations
 
 import glob
 import os
+import re
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -27,26 +31,40 @@ def _nvcc() -> str:
 
 
 def _headers_mtime() -> float:
-    hs = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    hs = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+          glob.glob(os.path.join(ROOT, "include", "*.h")))
     return max([os.path.getmtime(h) for h in hs] + [0.0])
+
+
+def jk_units() -> list[tuple[int, int, int, int]]:
+    """(bra class, precision, first ket class, last ket class) of every entry of csrc/units.h."""
+    txt = open(os.path.join(CSRC, "units.h")).read()
+    return [tuple(int(v) for v in m) for m in re.findall(r"U\((\d+), (\d+), (\d+), (\d+)\)", txt)]
 
 
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    unit_src = os.path.join(CSRC, "k_unit.cu")
+    jobs_list = [(s, os.path.join(OBJ, os.path.basename(s)[:-3] + ".o"), [])
+                 for s in sorted(glob.glob(os.path.join(CSRC, "*.cu"))) if s != unit_src]
+    for x, p, ylo, yhi in jk_units():
+        jobs_list.append((unit_src, os.path.join(OBJ, f"k_unit_{x}_{p}_{ylo}_{yhi}.o"),
+                          [f"-DERI_UNIT_X={x}", f"-DERI_UNIT_P={p}", f"-DERI_UNIT_YLO={ylo}", f"-DERI_UNIT_YHI={yhi}"]))
     hdr = _headers_mtime()
     todo = []
     objs = []
-    for s in srcs:
-        o = os.path.join(OBJ, os.path.basename(s)[:-3] + ".o")
+    for s, o, defs in jobs_list:
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
-            todo.append((s, o))
+            todo.append((s, o, defs))
+    stale = [f for f in glob.glob(os.path.join(OBJ, "*.o")) if f not in objs]
+    for f in stale:  # objects of removed sources must not be linked
+        os.remove(f)
     nvcc = _nvcc()
 
     def compile_one(so):
-        s, o = so
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o + ".tmp"]
+        s, o, defs = so
+        cmd = [nvcc, *ARCH, *FLAGS, *defs, "-c", s, "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {s}:\n{r.stderr}")
@@ -56,8 +74,9 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
 
     if todo:
         jobs = jobs or min(len(todo), max(1, os.cpu_count() or 1))
-        # heaviest translation units first
-        todo.sort(key=lambda so: -os.path.getsize(so[0]) if "k_bra" not in so[0] else -int(so[0][-4]) - 100)
+        # heaviest translation units first: FP32 class units of high bra classes, then the rest by size
+        todo.sort(key=lambda so: (-1000 - 10 * int(so[1].split("_")[-4]) - 100 * int(so[1].split("_")[-3])
+                                  if "k_unit_" in so[1] else -os.path.getsize(so[0])))
         with ThreadPoolExecutor(jobs) as ex:
             list(ex.map(compile_one, todo))
     if todo or not os.path.exists(SO):

@@ -336,7 +336,27 @@ __device__ __forceinline__ void md_e_1d(T PA, T PB, T o2p, T* E) {
   }
 }
 
-__device__ __forceinline__ double atomic_add_d(double* p, double v) { return atomicAdd(p, v); }
+// Accumulation into a J / K / gradient accumulator.  det = 0: FP64 atomicAdd
+// (the sum depends on the order in which the atomics land).  det = 1
+// (deterministic builds): the accumulator holds a 64-bit two's-complement
+// fixed-point number with scale 2^46 and v is rounded to it; integer addition
+// is associative (exact modulo 2^64), so the final bits do not depend on the
+// order of the additions.  Resolution 2^-46 = 1.4e-14, range |sum| < 2^17.
+constexpr double kFixScale = 70368744177664.0;  // 2^46
+constexpr double kFixInv = 1.0 / 70368744177664.0;
+constexpr double kFixLimit = 65536.0;           // 2^16: |value| above this is reported (half the range)
+__device__ __forceinline__ void acc_add(double* p, double v, int det) {
+  if (det)
+    atomicAdd(reinterpret_cast<unsigned long long*>(p),
+              static_cast<unsigned long long>(__double2ll_rn(v * kFixScale)));
+  else
+    atomicAdd(p, v);
+}
+// value of an accumulator element (det: fixed point -> double)
+__device__ __forceinline__ double acc_value(const double* p, int det) {
+  if (!det) return *p;
+  return (double)(*reinterpret_cast<const long long*>(p)) * kFixInv;
+}
 
 // R^0_{tuv}, t+u+v <= L, in registers (fully unrolled; every index is an
 // arithmetic expression of unrolled loop counters, so it folds to a constant).
@@ -376,6 +396,6 @@ __device__ __forceinline__ void r_build_reg(const T* F, T pref, T X, T Y, T Z, T
 }
 
 // Error codes written by device code into the plan's status word.
-enum : int { DEV_OK = 0, DEV_BOUNDS = 1 };
+enum : int { DEV_OK = 0, DEV_BOUNDS = 1, DEV_RANGE = 2 };  // DEV_RANGE: a deterministic accumulator above 2^16
 
 }  // namespace eri

@@ -3,7 +3,9 @@
 // in parallel.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 #include "kernels_g.cuh"
+#include "units.h"
 
 namespace eri {
 
@@ -66,31 +68,20 @@ cudaError_t launch_jk_t(const JKArgs& a, cudaStream_t s, int nsm) {
   return cudaGetLastError();
 }
 
-template <int X, int Y>
-cudaError_t launch_jk_xy(int prec, const JKArgs& a, cudaStream_t s, int nsm) {
-  if constexpr (Y <= X) {
-    constexpr int LA = ClassL<X>::l1, LB = ClassL<X>::l2, LC = ClassL<Y>::l1, LD = ClassL<Y>::l2;
-    return prec ? launch_jk_t<LA, LB, LC, LD, float>(a, s, nsm) : launch_jk_t<LA, LB, LC, LD, double>(a, s, nsm);
-  } else {
+// Launch of class pair (X, y) in precision P for y in YLO..YHI (compile-time
+// chain of the ket classes of one compilation unit, see units.h)
+template <int X, int P, int YLO, int YHI>
+cudaError_t launch_jk_unit(int y, const JKArgs& a, cudaStream_t s, int nsm) {
+  if constexpr (YLO > YHI || YLO > X) {
     return cudaErrorInvalidValue;
+  } else {
+    if (y == YLO) {
+      constexpr int LA = ClassL<X>::l1, LB = ClassL<X>::l2, LC = ClassL<YLO>::l1, LD = ClassL<YLO>::l2;
+      using T = std::conditional_t<P == 1, float, double>;
+      return launch_jk_t<LA, LB, LC, LD, T>(a, s, nsm);
+    }
+    return launch_jk_unit<X, P, YLO + 1, YHI>(y, a, s, nsm);
   }
-}
-
-template <int X>
-cudaError_t launch_jk_x(int Y, int prec, const JKArgs& a, cudaStream_t s, int nsm) {
-  switch (Y) {
-    case 0: return launch_jk_xy<X, 0>(prec, a, s, nsm);
-    case 1: return launch_jk_xy<X, 1>(prec, a, s, nsm);
-    case 2: return launch_jk_xy<X, 2>(prec, a, s, nsm);
-    case 3: return launch_jk_xy<X, 3>(prec, a, s, nsm);
-    case 4: return launch_jk_xy<X, 4>(prec, a, s, nsm);
-    case 5: return launch_jk_xy<X, 5>(prec, a, s, nsm);
-    case 6: return launch_jk_xy<X, 6>(prec, a, s, nsm);
-    case 7: return launch_jk_xy<X, 7>(prec, a, s, nsm);
-    case 8: return launch_jk_xy<X, 8>(prec, a, s, nsm);
-    case 9: return launch_jk_xy<X, 9>(prec, a, s, nsm);
-  }
-  return cudaErrorInvalidValue;
 }
 
 template <int X, int Y>
@@ -156,17 +147,12 @@ cudaError_t launch_j_lab(int LCD, int prec, const JArgs& a, cudaStream_t s, int 
   return cudaErrorInvalidValue;
 }
 
-// entry points defined in the per-class translation units
-cudaError_t launch_jk_bra0(int, int, const JKArgs&, cudaStream_t, int);
-cudaError_t launch_jk_bra1(int, int, const JKArgs&, cudaStream_t, int);
-cudaError_t launch_jk_bra2(int, int, const JKArgs&, cudaStream_t, int);
-cudaError_t launch_jk_bra3(int, int, const JKArgs&, cudaStream_t, int);
-cudaError_t launch_jk_bra4(int, int, const JKArgs&, cudaStream_t, int);
-cudaError_t launch_jk_bra5(int, int, const JKArgs&, cudaStream_t, int);
-cudaError_t launch_jk_bra6(int, int, const JKArgs&, cudaStream_t, int);
-cudaError_t launch_jk_bra7(int, int, const JKArgs&, cudaStream_t, int);
-cudaError_t launch_jk_bra8(int, int, const JKArgs&, cudaStream_t, int);
-cudaError_t launch_jk_bra9(int, int, const JKArgs&, cudaStream_t, int);
+// J/K entry points: explicitly instantiated once per entry of units.h in its own
+// compilation unit (k_unit.cu), referenced from plan.cu
+#define ERI_JK_UNIT_DECL(X, P, YLO, YHI) \
+  extern template cudaError_t launch_jk_unit<X, P, YLO, YHI>(int, const JKArgs&, cudaStream_t, int);
+ERI_JK_UNITS(ERI_JK_UNIT_DECL)
+#undef ERI_JK_UNIT_DECL
 cudaError_t launch_grad_bra0(int, const GradArgs&, cudaStream_t, int);
 cudaError_t launch_grad_bra1(int, const GradArgs&, cudaStream_t, int);
 cudaError_t launch_grad_bra2(int, const GradArgs&, cudaStream_t, int);

@@ -38,7 +38,23 @@ struct KArgs {
   // *nitems of them (read on the device).  Null: items are positions in wl.
   const int2* items;
   const unsigned int* nitems;
+  double omega2;  // long-range operator erf(omega r)/r: omega^2 (0 = Coulomb 1/r)
+  float omega2f;
+  int det;        // 1: fixed-point accumulators (deterministic builds, acc_add)
 };
+
+// Long-range operator erf(omega r)/r (Sec. 2.5, Eq. eri_longrange_formula):
+// the Hermite integrals keep their form with rho -> s rho and the prefactor
+// times sqrt(s), s = omega^2 / (omega^2 + rho).  omega2 = 0 is the Coulomb
+// operator and leaves rho and pref untouched.  omega2 is uniform over a launch.
+template <typename T>
+__device__ __forceinline__ void attenuate(T omega2, T& rho, T& pref) {
+  if (omega2 > T(0)) {
+    const T s = omega2 / (omega2 + rho);
+    rho *= s;
+    pref *= sqrt(s);
+  }
+}
 
 // pair index of shells x, y of molecule `mol` (pairs are stored a >= b, a(a+1)/2 + b)
 __device__ __forceinline__ int pair_index(const KArgs& a, int mol, int x, int y) {
@@ -77,7 +93,17 @@ struct JArgs {
   const RStep* rsteps;
   const double* Dherm;  // Hermite density per ket primitive pair (sign (-1)^|Q| folded in)
   double* Jherm;        // Hermite J per bra primitive pair (accumulated)
+  double omega2;        // erf(omega r)/r: omega^2 (0 = Coulomb)
+  float omega2f;
+  int det;              // 1: fixed-point Jherm (deterministic builds)
 };
+
+// omega^2 of a launch in its precision
+template <typename T, typename A> __device__ __forceinline__ T om2(const A& a);
+template <> __device__ __forceinline__ double om2<double, KArgs>(const KArgs& a) { return a.omega2; }
+template <> __device__ __forceinline__ float om2<float, KArgs>(const KArgs& a) { return a.omega2f; }
+template <> __device__ __forceinline__ double om2<double, JArgs>(const JArgs& a) { return a.omega2; }
+template <> __device__ __forceinline__ float om2<float, JArgs>(const JArgs& a) { return a.omega2f; }
 
 __device__ __forceinline__ int find_bra(const int64_t* __restrict__ prefix, int n, int64_t item) {
   int lo = 0, hi = n;  // prefix[lo] <= item < prefix[hi]
@@ -239,11 +265,12 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
         Prim<T> kp;
         kp.load(a.pd, offk + pk);
         const T pq = bp.p * kp.p, ps = bp.p + kp.p;
-        const T rho = pq / ps;
+        T rho = pq / ps;
+        T pref = bp.pref * kp.pref * (T(1) / sqrt(ps));
+        attenuate(om2<T>(a), rho, pref);
         const T X = bp.P[0] - kp.P[0], Y = bp.P[1] - kp.P[1], Z = bp.P[2] - kp.P[2];
         T F[L + 1];
         Boys<T>::template eval<L>(rho * (X * X + Y * Y + Z * Z), a.bt, F);
-        const T pref = bp.pref * kp.pref * (T(1) / sqrt(ps));
         r_build_warp<L, T>(F, pref, X, Y, Z, T(-2) * rho, a.rsteps, ping0, ping1, box, lane);
         const double* dq = a.Dherm + hk + (size_t)pk * HCD;
 #pragma unroll
@@ -267,7 +294,7 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
 #pragma unroll
       for (int j = 0; j < S::NPS; ++j) {
         const int P = lane + 32 * j;
-        if (P < HAB) atomic_add_d(a.Jherm + hb + (size_t)pb * HAB + P, (double)acc[j]);
+        if (P < HAB) acc_add(a.Jherm + hb + (size_t)pb * HAB + P, (double)acc[j], a.det);
       }
     }
   }

@@ -23,18 +23,27 @@ struct AShape {
   // ket primitives (fewer FLOPs), or the bra transform per primitive quartet
   static constexpr int REG_WACC = NCD * HAB + NAB * NCD + NR;
   static constexpr int REG_PERPQ = HAB + NAB * NCD + NR;
-  static constexpr bool WACC = REG_WACC <= 140;
+  // W accumulated over the ket primitives where its footprint stays near the
+  // 255-register limit (a few hundred bytes of spill still beat the extra bra
+  // transforms of the per-primitive-quartet variant; measured on GB300)
+  static constexpr bool WACC = REG_WACC <= 260;
 };
 
 // Which classes run one quartet per thread (registers) rather than one per warp.
 // FP64: the tiny classes only (the warp kernel keeps the FP64 pipe busier for the
-// rest).  FP32: every class of L <= 4 whose register footprint fits.
+// rest).  FP32: every class of L <= 7 whose per-primitive-quartet register
+// footprint is at most 460 values.  Measured on GB300 (workload 1, FP32 tier):
+// the register kernel runs these classes 2.2x to 9.6x faster than the
+// shared-memory warp kernel even where ptxas spills up to ~6 KB per thread
+// (spills are lane-interleaved local memory, served by L1), because every
+// index is a compile-time constant and all 32 lanes do useful work; the warp
+// kernel stays for the classes with larger ERI blocks.
 __host__ __device__ constexpr bool use_thread_kernel(int la, int lb, int lc, int ld, bool fp32) {
   const int L = la + lb + lc + ld;
   const int nab = ncart(la) * ncart(lb), ncd = ncart(lc) * ncart(ld);
   if (!fp32) return L <= 3 && nab * ncd <= 27;
   const int hab = nherm(la + lb), nr = nherm(L);
-  return L <= 4 && (hab + nab * ncd + nr) <= 140;
+  return L <= 7 && (hab + nab * ncd + nr) <= 460;
 }
 
 // (ab|cd) for all components of one contracted quartet, summed over primitives:
@@ -87,11 +96,12 @@ __device__ __forceinline__ void eri_block_reg_pq(const KArgs& a, int offb, int n
       T ek[3 * S::NEK];
       load_or_build_e<LC, LD, T>(a.pd, ek0 + pk * 3 * S::NEK, offk + pk, ek);
       const T ps = bp.p + kp.p;
-      const T rho = bp.p * kp.p / ps;
+      T rho = bp.p * kp.p / ps;
+      T pref = bp.pref * kp.pref * rsqrt_t(ps);
+      attenuate(om2<T>(a), rho, pref);
       const T PQx = bp.P[0] - kp.P[0], PQy = bp.P[1] - kp.P[1], PQz = bp.P[2] - kp.P[2];
       T F[L + 1];
       Boys<T>::template eval<L>(rho * (PQx * PQx + PQy * PQy + PQz * PQz), a.bt, F);
-      const T pref = bp.pref * kp.pref * rsqrt_t(ps);
       T R[S::NR];
       r_build_reg<L, T>(F, pref, PQx, PQy, PQz, T(-2) * rho, R);
       for_cart<LC>([&](auto kx, auto ky, auto kz) {
@@ -144,11 +154,12 @@ __device__ __forceinline__ void eri_block_reg(const KArgs& a, int offb, int npb,
       T ek[3 * S::NEK];
       load_or_build_e<LC, LD, T>(a.pd, ek0 + pk * 3 * S::NEK, offk + pk, ek);
       const T ps = bp.p + kp.p;
-      const T rho = bp.p * kp.p / ps;
+      T rho = bp.p * kp.p / ps;
+      T pref = bp.pref * kp.pref * rsqrt_t(ps);
+      attenuate(om2<T>(a), rho, pref);
       const T PQx = bp.P[0] - kp.P[0], PQy = bp.P[1] - kp.P[1], PQz = bp.P[2] - kp.P[2];
       T F[L + 1];
       Boys<T>::template eval<L>(rho * (PQx * PQx + PQy * PQy + PQz * PQz), a.bt, F);
-      const T pref = bp.pref * kp.pref * rsqrt_t(ps);
       T R[S::NR];
       r_build_reg<L, T>(F, pref, PQx, PQy, PQz, T(-2) * rho, R);
       for_cart<LC>([&](auto kx, auto ky, auto kz) {
@@ -208,7 +219,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
           for (int id = 0; id < S::ND; ++id)
             s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], __ldg(Dp + (size_t)(ao2 + ib) * n + ao4 + id), s);
-        atomic_add_d(Kh + (size_t)(ao1 + ia) * n + ao3 + ic, (double)(w * s));
+        acc_add(Kh + (size_t)(ao1 + ia) * n + ao3 + ic, (double)(w * s), A.k.det);
       }
 #pragma unroll
       for (int id = 0; id < S::ND; ++id) {  // Kh_ad += w (ab|cd) D_bc
@@ -218,7 +229,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
           for (int ic = 0; ic < S::NC; ++ic)
             s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], __ldg(Dp + (size_t)(ao2 + ib) * n + ao3 + ic), s);
-        atomic_add_d(Kh + (size_t)(ao1 + ia) * n + ao4 + id, (double)(w * s));
+        acc_add(Kh + (size_t)(ao1 + ia) * n + ao4 + id, (double)(w * s), A.k.det);
       }
     }
 #pragma unroll
@@ -231,7 +242,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
           for (int id = 0; id < S::ND; ++id)
             s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], __ldg(Dp + (size_t)(ao1 + ia) * n + ao4 + id), s);
-        atomic_add_d(Kh + (size_t)(ao2 + ib) * n + ao3 + ic, (double)(w * s));
+        acc_add(Kh + (size_t)(ao2 + ib) * n + ao3 + ic, (double)(w * s), A.k.det);
       }
 #pragma unroll
       for (int id = 0; id < S::ND; ++id) {  // Kh_bd += w (ab|cd) D_ac
@@ -241,7 +252,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
           for (int ic = 0; ic < S::NC; ++ic)
             s = fma(X[(ia * S::NB + ib) * S::NCD + ic * S::ND + id], __ldg(Dp + (size_t)(ao1 + ia) * n + ao3 + ic), s);
-        atomic_add_d(Kh + (size_t)(ao2 + ib) * n + ao4 + id, (double)(w * s));
+        acc_add(Kh + (size_t)(ao2 + ib) * n + ao4 + id, (double)(w * s), A.k.det);
       }
     }
   }
@@ -253,7 +264,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
       for (int icd = 0; icd < S::NCD; ++icd)
         s = fma(X[iab * S::NCD + icd], __ldg(Dp + (size_t)(ao3 + icd / S::ND) * n + ao4 + icd % S::ND), s);
-      atomic_add_d(Jh + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB, (double)(w2 * s));
+      acc_add(Jh + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB, (double)(w2 * s), A.k.det);
     }
 #pragma unroll
     for (int icd = 0; icd < S::NCD; ++icd) {  // Jh_cd += 2w (ab|cd) D_ab
@@ -261,7 +272,7 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
       for (int iab = 0; iab < S::NAB; ++iab)
         s = fma(X[iab * S::NCD + icd], __ldg(Dp + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB), s);
-      atomic_add_d(Jh + (size_t)(ao3 + icd / S::ND) * n + ao4 + icd % S::ND, (double)(w2 * s));
+      acc_add(Jh + (size_t)(ao3 + icd / S::ND) * n + ao4 + icd % S::ND, (double)(w2 * s), A.k.det);
     }
   }
 }

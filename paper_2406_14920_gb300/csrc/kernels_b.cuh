@@ -233,13 +233,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 0) jk_warp_kernel(JK
             const int ipk = offk + k0 + lane;
             const T kp = pdv<T>(a.pd.p, a.pd.pf, ipk);
             const T ps = bp_p + kp;
-            const T rho = bp_p * kp / ps;
+            T rho = bp_p * kp / ps;
+            T pref = bp_pref * pdv<T>(a.pd.pref, a.pd.preff, ipk) * rsqrt_t(ps);
+            attenuate(om2<T>(a), rho, pref);
             const T X = bPx - pdv<T>(a.pd.P, a.pd.Pf, ipk);
             const T Y = bPy - pdv<T>(a.pd.P, a.pd.Pf, a.pd.n + ipk);
             const T Z = bPz - pdv<T>(a.pd.P, a.pd.Pf, 2 * a.pd.n + ipk);
             T F[L + 1];
             Boys<T>::template eval<L>(rho * (X * X + Y * Y + Z * Z), a.bt, F);
-            const T pref = bp_pref * pdv<T>(a.pd.pref, a.pd.preff, ipk) * rsqrt_t(ps);
             T* sc = scal + lane * NSC;
 #pragma unroll
             for (int m = 0; m <= L; ++m) sc[m] = pref * F[m];
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 0) jk_warp_kernel(JK
             }
           }
           const int row = isA ? ao1 + r : ao2 + r;
-          atomic_add_d(Kh + (size_t)row * n + ao3 + c, (double)(w * s));
+          acc_add(Kh + (size_t)row * n + ao3 + c, (double)(w * s), a.det);
         }
         // Kh_ad[a][d] += w sum_{b, c in chunk} X D_bc ; Kh_bd[b][d] += w sum_{a, c} X D_ac
         for (int o = lane; o < (NA + NB) * ND; o += 32) {
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 0) jk_warp_kernel(JK
             }
           }
           const int row = isA ? ao1 + r : ao2 + r;
-          atomic_add_d(Kh + (size_t)row * n + ao4 + d, (double)(w * s));
+          acc_add(Kh + (size_t)row * n + ao4 + d, (double)(w * s), a.det);
         }
       }
       if (Jh) {
@@ -439,14 +440,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 0) jk_warp_kernel(JK
             const int cd = c0 + ci;
             s = fma(Xs[iab * CH + ci], __ldg(Dp + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND), s);
           }
-          atomic_add_d(Jh + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB, (double)(w2 * s));
+          acc_add(Jh + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB, (double)(w2 * s), a.det);
         }
         for (int ci = lane; ci < nci; ci += 32) {  // Jh_cd += 2w sum_ab X D_ab
           T s = T(0);
           for (int iab = 0; iab < NAB; ++iab)
             s = fma(Xs[iab * CH + ci], __ldg(Dp + (size_t)(ao1 + iab / NB) * n + ao2 + iab % NB), s);
           const int cd = c0 + ci;
-          atomic_add_d(Jh + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND, (double)(w2 * s));
+          acc_add(Jh + (size_t)(ao3 + cd / ND) * n + ao4 + cd % ND, (double)(w2 * s), a.det);
         }
       }
       __syncwarp();

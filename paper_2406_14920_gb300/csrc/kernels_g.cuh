@@ -30,6 +30,8 @@ struct GradArgs {
   const int* sh_atom;
   double* grad;        // natom * 3 (all molecules' atoms)
   double cj, ck;       // weights of the Coulomb and exchange parts (1 or 0)
+  double omega2;       // erf(omega r)/r: omega^2 (0 = Coulomb)
+  int det;             // 1: fixed-point gradient accumulator (deterministic builds)
 };
 
 // E^{ij}_t and E^{ij,(1)}_t for one direction, i <= LI, j <= LJ, t <= i+j,
@@ -241,12 +243,13 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
             const int ipk = offk + k0 + lane;
             const T kp = __ldg(a.pd.p + ipk);
             const T ps = bp_p + kp;
-            const T rho = bp_p * kp / ps;
+            T rho = bp_p * kp / ps;
+            T pref = bp_pref * __ldg(a.pd.pref + ipk) * rsqrt(ps);
+            attenuate(a.omega2, rho, pref);  // s depends on exponents only: the derivative rules hold as they are
             const T X = bPx - __ldg(a.pd.P + ipk), Y = bPy - __ldg(a.pd.P + a.pd.n + ipk),
                     Z = bPz - __ldg(a.pd.P + 2 * a.pd.n + ipk);
             T F[L + 1];
             boys_f64<L>(rho * (X * X + Y * Y + Z * Z), a.bt, F);
-            const T pref = bp_pref * __ldg(a.pd.pref + ipk) * rsqrt(ps);
             T* sc = scal + lane * NSC;
 #pragma unroll
             for (int m = 0; m <= L; ++m) sc[m] = pref * F[m];
@@ -414,8 +417,8 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
       const int atA = __ldg(a.sh_atom + s1), atB = __ldg(a.sh_atom + s2);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        atomicAdd(a.grad + atA * 3 + d, w * gA[d]);
-        atomicAdd(a.grad + atB * 3 + d, w * gB[d]);
+        acc_add(a.grad + atA * 3 + d, w * gA[d], a.det);
+        acc_add(a.grad + atB * 3 + d, w * gB[d], a.det);
       }
     }
     __syncwarp();

@@ -208,26 +208,6 @@ __global__ void k_dmax(int npair, const int* __restrict__ s1, const int* __restr
   dmax[ip] = __double2float_ru(mx);
 }
 
-// runtime-l E^{ij}_t (Eq. E_recursion), E[(i*5+j)*9+t], i,j <= 4
-__device__ void md_e_rt(int li, int lj, double PA, double PB, double o2p, double* E) {
-  for (int x = 0; x < 225; ++x) E[x] = 0.0;
-  E[0] = 1.0;
-  for (int i = 0; i < li; ++i)
-    for (int t = 0; t <= i + 1; ++t) {
-      double v = PA * E[(i * 5) * 9 + t];
-      if (t > 0) v += o2p * E[(i * 5) * 9 + t - 1];
-      if (t + 1 <= i) v += (t + 1) * E[(i * 5) * 9 + t + 1];
-      E[((i + 1) * 5) * 9 + t] = v;
-    }
-  for (int i = 0; i <= li; ++i)
-    for (int j = 0; j < lj; ++j)
-      for (int t = 0; t <= i + j + 1; ++t) {
-        double v = PB * E[(i * 5 + j) * 9 + t];
-        if (t > 0) v += o2p * E[(i * 5 + j) * 9 + t - 1];
-        if (t + 1 <= i + j) v += (t + 1) * E[(i * 5 + j) * 9 + t + 1];
-        E[(i * 5 + j + 1) * 9 + t] = v;
-      }
-}
 
 // Hermite coefficients E^{ij}_t (Eq. E_recursion) of every primitive pair, per
 // direction, stored as (i*(l2+1)+j)*(l1+l2+1)+t, i <= l1, j <= l2 (x, then y, then z).
@@ -515,11 +495,6 @@ __global__ void k_prefix(const int* __restrict__ sorted, const int* __restrict__
 
 // Where each molecule's nbf_m x nbf_m block sits in packed D / J / K, and the
 // global AO index of its first function (component factors f are global).
-struct MolMats {
-  const int64_t* off;
-  const int* n;
-  const int* aobase;
-};
 
 // D' = D f f (component norms folded in); grid (x, molecule)
 __global__ void k_scale_d(MolMats mm, const double* __restrict__ D, const double* __restrict__ f,
@@ -579,11 +554,11 @@ __global__ void k_post_j(int npair, const int* __restrict__ s1, const int* __res
                          const int* __restrict__ poff, const int* __restrict__ hoff, const int* __restrict__ sh_l,
                          const int* __restrict__ pao1, const int* __restrict__ pao2, const int* __restrict__ pmol,
                          MolMats mm, const int* __restrict__ sig, PairData pd, const double* __restrict__ Jh,
-                         const double* __restrict__ f, double* __restrict__ J) {
+                         const double* __restrict__ f, double* __restrict__ J, int det, int* __restrict__ status) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= npair * 100) return;
   const int ip = t / 100, c = t % 100;
-  if (!sig[ip]) return;
+  if (sig && !sig[ip]) return;
   const int a = s1[ip], b = s2[ip], la = sh_l[a], lb = sh_l[b];
   const int mu = c / 10, nu = c % 10;
   if (mu >= ncart(la) || nu >= ncart(lb)) return;
@@ -599,9 +574,11 @@ __global__ void k_post_j(int npair, const int* __restrict__ s1, const int* __res
     const double* jh = Jh + hoff[ip] + (size_t)k * H;
     for (int tx = 0; tx <= ix + jx; ++tx)
       for (int ty = 0; ty <= iy + jy; ++ty)
-        for (int tz = 0; tz <= iz + jz; ++tz)
-          v += E[0][(ix * 5 + jx) * 9 + tx] * E[1][(iy * 5 + jy) * 9 + ty] * E[2][(iz * 5 + jz) * 9 + tz] *
-               jh[herm_index(tx, ty, tz)];
+        for (int tz = 0; tz <= iz + jz; ++tz) {
+          const double hv = acc_value(jh + herm_index(tx, ty, tz), det);
+          if (det && fabs(hv) > kFixLimit) atomicOr(status, DEV_RANGE);
+          v += E[0][(ix * 5 + jx) * 9 + tx] * E[1][(iy * 5 + jy) * 9 + ty] * E[2][(iz * 5 + jz) * 9 + tz] * hv;
+        }
   }
   const int m = pmol[ip], nbf = mm.n[m], a0 = mm.aobase[m];
   const int r = pao1[ip] + mu, cc = pao2[ip] + nu;
@@ -612,14 +589,27 @@ __global__ void k_post_j(int npair, const int* __restrict__ s1, const int* __res
 }
 
 // K = (Kh + Kh^T) f f  (Eq. 8_fold_symmetry: the transposes carry permutations 5-8); grid (x, molecule)
+// (deterministic builds: Kh holds fixed point, see acc_add; an element above the
+// reporting limit sets DEV_RANGE in the plan's status word)
 __global__ void k_post_k(MolMats mm, const double* __restrict__ Kh, const double* __restrict__ f,
-                         double* __restrict__ K) {
+                         double* __restrict__ K, int det, int* __restrict__ status) {
   const int m = blockIdx.y, n = mm.n[m];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)n * n) return;
   const int r = (int)(i / n), c = (int)(i % n), a0 = mm.aobase[m];
   const int64_t o = mm.off[m];
-  K[o + i] = (Kh[o + i] + Kh[o + (int64_t)c * n + r]) * f[a0 + r] * f[a0 + c];
+  const double x = acc_value(Kh + o + i, det), y = acc_value(Kh + o + (int64_t)c * n + r, det);
+  if (det && (fabs(x) > kFixLimit || fabs(y) > kFixLimit)) atomicOr(status, DEV_RANGE);
+  K[o + i] = (x + y) * f[a0 + r] * f[a0 + c];
+}
+
+// deterministic gradient: fixed-point accumulators -> doubles, in place
+__global__ void k_fix_to_double(int n, double* __restrict__ x, int* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = acc_value(x + i, 1);
+  if (fabs(v) > kFixLimit) atomicOr(status, DEV_RANGE);
+  x[i] = v;
 }
 
 // E_J = 1/2 sum D J, E_K = -1/4 sum D K per molecule (one block each, fixed
@@ -735,7 +725,12 @@ dim3 eri_plan_impl::mat_grid(int block) const {
   return dim3((unsigned)std::max<int64_t>(1, ((int64_t)max_nbf * max_nbf + block - 1) / block), (unsigned)nmol);
 }
 
-static MolMats molmats(const eri_plan_impl* P) {
+// D' = D f f into the plan's FP64 workspace (also used by nuclear.cu)
+void k_scale_d_launch(const eri_plan_impl* P, const double* D, cudaStream_t s) {
+  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(molmats(P), D, P->d_f, P->d_Dp, nullptr);
+}
+
+MolMats molmats(const eri_plan_impl* P) {
   MolMats m;
   m.off = P->d_mat_off; m.n = P->d_mat_n; m.aobase = P->d_aobase;
   return m;
@@ -864,7 +859,8 @@ void eri_plan_impl::release() {
                   d_PBf, d_preff, d_Q, d_qmax, d_sig, d_ccount, d_coff, d_sorted, d_pos, d_counts, d_koff, d_joff,
                   d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Jh, d_Dherm,
                   d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp, d_ea,
-                  d_mat_off, d_mat_n, d_aobase, d_pbase, d_pmol, d_shloc, d_ccm, d_segloc, d_Dpf};
+                  d_mat_off, d_mat_n, d_aobase, d_pbase, d_pmol, d_shloc, d_ccm, d_segloc, d_Dpf,
+                  d_nuc_list, d_nuc_goff, d_nuc_dens};
   for (auto& e : prof_events) cudaEventDestroy(e);
   prof_events.clear();
   if (gexec) cudaGraphExecDestroy(gexec);
@@ -984,18 +980,10 @@ int eri_plan_impl::tile_for(int X, int Y, int tier) const {
 }
 
 static cudaError_t launch_jk_class(int X, int Y, int prec, const JKArgs& ja, cudaStream_t s, int nsm) {
-  switch (X) {
-    case 0: return launch_jk_bra0(Y, prec, ja, s, nsm);
-    case 1: return launch_jk_bra1(Y, prec, ja, s, nsm);
-    case 2: return launch_jk_bra2(Y, prec, ja, s, nsm);
-    case 3: return launch_jk_bra3(Y, prec, ja, s, nsm);
-    case 4: return launch_jk_bra4(Y, prec, ja, s, nsm);
-    case 5: return launch_jk_bra5(Y, prec, ja, s, nsm);
-    case 6: return launch_jk_bra6(Y, prec, ja, s, nsm);
-    case 7: return launch_jk_bra7(Y, prec, ja, s, nsm);
-    case 8: return launch_jk_bra8(Y, prec, ja, s, nsm);
-    case 9: return launch_jk_bra9(Y, prec, ja, s, nsm);
-  }
+#define ERI_JK_UNIT_CALL(UX, UP, YLO, YHI) \
+  if (X == UX && prec == UP && Y >= YLO && Y <= YHI) return launch_jk_unit<UX, UP, YLO, YHI>(Y, ja, s, nsm);
+  ERI_JK_UNITS(ERI_JK_UNIT_CALL)
+#undef ERI_JK_UNIT_CALL
   return cudaErrorInvalidValue;
 }
 
@@ -1007,6 +995,87 @@ extern "C" int eri_default_opts(eri_opts_t* o) {
   o->device = -1;
   o->j_engine = 1;
   o->profile = 0;
+  o->tune_cache = nullptr;
+  o->deterministic = 0;
+  return ERI_OK;
+}
+
+// Tile cache file (opts.tune_cache): one line per entry,
+//   <key> t_0 ... t_199      key = <device name>|nbf=<n>|nmol=<m>|npair=<p>|prec=<0|1>
+// with spaces in the device name replaced by '_', the tiles in eri_get_tiles order.
+static std::string tune_key(const eri_plan_impl* P, int precision) {
+  cudaDeviceProp prop;
+  std::string name = cudaGetDeviceProperties(&prop, P->device) == cudaSuccess ? prop.name : "unknown";
+  for (char& c : name)
+    if (c == ' ') c = '_';
+  char buf[160];
+  snprintf(buf, sizeof(buf), "|nbf=%d|nmol=%d|npair=%d|prec=%d", P->nbf, P->nmol, P->npair, precision);
+  return name + buf;
+}
+
+static std::vector<std::string> read_lines(const std::string& path) {
+  std::vector<std::string> out;
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return out;
+  std::string cur;
+  int ch;
+  while ((ch = fgetc(f)) != EOF) {
+    if (ch == '\n') {
+      if (!cur.empty()) out.push_back(cur);
+      cur.clear();
+    } else {
+      cur.push_back((char)ch);
+    }
+  }
+  if (!cur.empty()) out.push_back(cur);
+  fclose(f);
+  return out;
+}
+
+// Load the entry for (this plan, precision) into tile_k; a missing file or
+// entry leaves the tiles unchanged.  Malformed entries are ignored.
+static void tune_cache_load(eri_plan_impl* P, int precision) {
+  if (P->tune_cache.empty()) return;
+  const std::string key = tune_key(P, precision) + " ";
+  for (const std::string& ln : read_lines(P->tune_cache)) {
+    if (ln.compare(0, key.size(), key) != 0) continue;
+    int t[NPAIRCLASS * NPAIRCLASS * 2];
+    const char* c = ln.c_str() + key.size();
+    int k = 0;
+    for (; k < NPAIRCLASS * NPAIRCLASS * 2; ++k) {
+      char* e = nullptr;
+      const long v = strtol(c, &e, 10);
+      if (e == c || v < 0 || v > 1024) break;
+      t[k] = (int)v;
+      c = e;
+    }
+    if (k == NPAIRCLASS * NPAIRCLASS * 2) memcpy(P->tile_k, t, sizeof(t));
+  }
+}
+
+// Store tile_k as the entry for (this plan, precision), replacing an older one
+// (write to a temporary file, then rename).  Returns ERI_EINVAL if the file
+// cannot be written.
+static int tune_cache_store(const eri_plan_impl* P, int precision) {
+  if (P->tune_cache.empty()) return ERI_OK;
+  const std::string key = tune_key(P, precision);
+  std::vector<std::string> lines;
+  for (const std::string& ln : read_lines(P->tune_cache))
+    if (ln.compare(0, key.size() + 1, key + " ") != 0) lines.push_back(ln);
+  std::string mine = key;
+  for (int X = 0; X < NPAIRCLASS; ++X)
+    for (int Y = 0; Y < NPAIRCLASS; ++Y)
+      for (int t = 0; t < 2; ++t) mine += " " + std::to_string(Y <= X ? P->tile_for(X, Y, t) : 0);
+  lines.push_back(mine);
+  const std::string tmp = P->tune_cache + ".tmp" + std::to_string((long long)(uintptr_t)P);
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return ERI_EINVAL;
+  for (const std::string& ln : lines) fprintf(f, "%s\n", ln.c_str());
+  const bool ok = fclose(f) == 0;
+  if (!ok || rename(tmp.c_str(), P->tune_cache.c_str()) != 0) {
+    remove(tmp.c_str());
+    return ERI_EINVAL;
+  }
   return ERI_OK;
 }
 
@@ -1056,6 +1125,8 @@ static int plan_create(int nmol, const eri_basis_t* const* bases, const double* 
   eri_plan_impl* P = new (std::nothrow) eri_plan_impl();
   if (!P) return ERI_ENOMEM;
   P->opts = o;
+  if (o.tune_cache) P->tune_cache = o.tune_cache;
+  P->opts.tune_cache = nullptr;  // the caller's string is not kept
   if (o.device >= 0) {
     if (cudaSetDevice(o.device) != cudaSuccess) { delete P; return ERI_ECUDA; }
   }
@@ -1204,6 +1275,7 @@ static int plan_create(int nmol, const eri_basis_t* const* bases, const double* 
     CKP(cudaDeviceSynchronize());
   }
 #undef CKP
+  tune_cache_load(P, o.precision);
   *out = reinterpret_cast<eri_plan_t*>(P);
   return ERI_OK;
 fail:
@@ -1260,9 +1332,11 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
                                                           P->d_phoff, P->d_sh_l, P->d_pao1, P->d_pao2, P->d_pmol, mm,
                                                           P->d_sig, P->pairdata(), P->d_Dp, P->d_Dherm);
     CK(cudaGetLastError());
-    JArgs ja;
+    JArgs ja{};
     ja.pd = P->pairdata(); ja.sp = P->spinfo(); ja.bt = P->boystabs();
     ja.rsteps = P->d_rsteps; ja.Dherm = P->d_Dherm; ja.Jherm = P->d_Jherm;
+    ja.omega2 = P->omega * P->omega; ja.omega2f = (float)ja.omega2;
+    ja.det = P->opts.deterministic ? 1 : 0;
     if (concurrent) {
       CK(cudaEventRecord(P->fork_ev, s));
       for (int b = 0; b < eri_plan_impl::kBranches; ++b) CK(cudaStreamWaitEvent(P->branch[b], P->fork_ev, 0));
@@ -1295,7 +1369,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
     k_post_j<<<grid1((int64_t)P->npair * 100, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_pnp, P->d_ppoff,
                                                                  P->d_phoff, P->d_sh_l, P->d_pao1, P->d_pao2,
                                                                  P->d_pmol, mm, P->d_sig, P->pairdata(), P->d_Jherm,
-                                                                 P->d_f, J);
+                                                                 P->d_f, J, ja.det, P->d_status);
     CK(cudaGetLastError());
   } else {
     // J and/or K from contracted Cartesian ERIs over canonical quartets
@@ -1317,6 +1391,8 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
     ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
     ka.items = nullptr; ka.nitems = nullptr;
     ka.guard = P->d_counters + NPAIRCLASS * NPAIRCLASS * 6;
+    ka.omega2 = P->omega * P->omega; ka.omega2f = (float)ka.omega2;
+    ka.det = P->opts.deterministic ? 1 : 0;
     ja.Jh = J ? P->d_Jh : nullptr;
     P->last_mixed = mixed;
     P->last_do_j = J != nullptr;
@@ -1411,11 +1487,11 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
       }
     P->prof_builds += P->opts.profile ? 1 : 0;
     if (K) {
-      k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, P->d_Kh, P->d_f, K);
+      k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, P->d_Kh, P->d_f, K, ka.det, P->d_status);
       CK(cudaGetLastError());
     }
     if (J) {
-      k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, P->d_Jh, P->d_f, J);
+      k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, P->d_Jh, P->d_f, J, ka.det, P->d_status);
       CK(cudaGetLastError());
     }
   }
@@ -1510,6 +1586,7 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
   ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
   ka.counter = nullptr;
   ka.guard = nullptr;
+  ka.omega2 = P->omega * P->omega; ka.omega2f = (float)ka.omega2;
   ja.Jh = P->d_Jh;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -1613,6 +1690,7 @@ extern "C" int eri_autotune(eri_plan_t* plan, const double* D, int32_t precision
     cudaGraphExecDestroy(P->gexec);
     P->gexec = nullptr;
   }
+  if (rc == ERI_OK) rc = tune_cache_store(P, precision);
   return rc;
 }
 
@@ -1627,6 +1705,19 @@ extern "C" int eri_plan_set_shard(eri_plan_t* plan, int32_t shard, int32_t nshar
   }
   P->shard = shard;
   P->nshard = nshard;
+  return ERI_OK;
+}
+
+extern "C" int eri_plan_set_omega(eri_plan_t* plan, double omega) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !(omega >= 0.0) || !(omega < 1.0e30)) return ERI_EINVAL;
+  if (P->gexec && omega != P->omega) {  // a captured graph carries the old operator
+    CK(cudaSetDevice(P->device));
+    CK(cudaDeviceSynchronize());
+    CK(cudaGraphExecDestroy(P->gexec));
+    P->gexec = nullptr;
+  }
+  P->omega = omega;
   return ERI_OK;
 }
 
@@ -1677,6 +1768,8 @@ int eri_build_jk_scratch(eri_plan_t* plan, const double* D, double* J, double* K
   ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
   ka.tau = 0.0f; ka.pmax32 = 0.0f; ka.mixed = 0; ka.tier_want = 0; ka.counter = nullptr; ka.guard = nullptr;
   ka.items = nullptr; ka.nitems = nullptr;
+  ka.omega2 = P->omega * P->omega; ka.omega2f = (float)ka.omega2;
+  ka.det = P->opts.deterministic ? 1 : 0;
   ja.Jh = J ? Jh : nullptr;
   P->last_mixed = false;
   P->last_do_j = J != nullptr;
@@ -1690,11 +1783,11 @@ int eri_build_jk_scratch(eri_plan_t* plan, const double* D, double* J, double* K
       CK(launch_jk_class(X, Y, 0, ja, s, P->nsm));
     }
   if (K) {
-    k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, Kh, P->d_f, K);
+    k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, Kh, P->d_f, K, ka.det, P->d_status);
     CK(cudaGetLastError());
   }
   if (J) {
-    k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, Jh, P->d_f, J);
+    k_post_k<<<P->mat_grid(256), 256, 0, s>>>(mm, Jh, P->d_f, J, ka.det, P->d_status);
     CK(cudaGetLastError());
   }
   return ERI_OK;
@@ -1744,17 +1837,23 @@ extern "C" int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int3
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(dEdR, 0, sizeof(double) * 3 * P->natom, s));
   if (!want_j && !want_k) return ERI_OK;
-  GradArgs ga;
+  GradArgs ga{};
   ga.pd = P->pairdata(); ga.sp = P->spinfo(); ga.bt = P->boystabs(); ga.rsteps = P->d_rsteps; ga.Dp = P->d_Dp;
   ga.ea = P->d_ea; ga.sh_atom = P->d_sh_atom; ga.grad = dEdR;
   ga.cj = want_j ? 1.0 : 0.0;
   ga.ck = want_k ? 1.0 : 0.0;
+  ga.omega2 = P->omega * P->omega;
+  ga.det = P->opts.deterministic ? 1 : 0;
   for (int X = 0; X < NPAIRCLASS; ++X)
     for (int Y = 0; Y < NPAIRCLASS; ++Y) {
       ga.wl = P->jlist(X, Y);
       if (ga.wl.total == 0) continue;
       CK(launch_grad_class(X, Y, ga, s, P->nsm));
     }
+  if (ga.det) {
+    k_fix_to_double<<<grid1(3 * P->natom, 128), 128, 0, s>>>(3 * P->natom, dEdR, P->d_status);
+    CK(cudaGetLastError());
+  }
   return ERI_OK;
 }
 
@@ -1770,6 +1869,18 @@ extern "C" int eri_get_lists(eri_plan_t* plan, float* Q, int32_t* sig, int32_t* 
   if (sorted) CK(cudaMemcpy(sorted, P->d_sorted, sizeof(int) * P->nsig, cudaMemcpyDeviceToHost));
   if (class_count) memcpy(class_count, P->h_ccount, sizeof(int) * NPAIRCLASS);
   return ERI_OK;
+}
+
+extern "C" int eri_check(eri_plan_t* plan) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P) return ERI_EINVAL;
+  CK(cudaSetDevice(P->device));
+  CK(cudaDeviceSynchronize());
+  int status = 0;
+  CK(cudaMemcpy(&status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status == 0) return ERI_OK;
+  CK(cudaMemset(P->d_status, 0, sizeof(int)));
+  return ERI_EDEVICE;
 }
 
 extern "C" int eri_get_stats(eri_plan_t* plan, eri_stats_t* st) {

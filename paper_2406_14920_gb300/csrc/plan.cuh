@@ -1,6 +1,7 @@
 // Internal plan state behind the opaque eri_plan_t of include/eri.h.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <vector>
 #include <cuda_runtime.h>
 #include "common.cuh"
@@ -23,6 +24,7 @@ struct eri_plan_impl {
   int *d_ccm = nullptr, *d_segloc = nullptr;
   int64_t nherm_tot = 0;
   double thresh = 1e-12;
+  double omega = 0.0;  // two-electron operator: 0 = 1/r, > 0 = erf(omega r)/r (eri_plan_set_omega)
   // shells
   int *d_sh_l = nullptr, *d_sh_atom = nullptr, *d_sh_np = nullptr, *d_sh_po = nullptr, *d_sh_ao = nullptr;
   double *d_exps = nullptr, *d_coefs = nullptr, *d_cn = nullptr, *d_f = nullptr, *d_coords = nullptr;
@@ -87,10 +89,21 @@ struct eri_plan_impl {
   // work-tile length (items per worker tile) per (bra class, ket class, tier),
   // set by eri_autotune or eri_set_tiles; 0 = the built-in default
   int tile_k[eri::NPAIRCLASS * eri::NPAIRCLASS * 2] = {};
+  std::string tune_cache;  // opts.tune_cache (copied): tile tables stored per device, plan shape and precision
   int tile_for(int X, int Y, int tier) const;
   // share of the work this plan computes (eri_plan_set_shard): tiles t of every
   // class launch with t % nshard == shard; results are this share's partial sums
   int shard = 0, nshard = 1;
+
+  // point-charge attraction (nuclear.cu): primitive pairs of every shell pair
+  // grouped by l1 + l2 (entries {prim pair, Hermite offset, density offset,
+  // shell pair}), built at the first call; per-pair offsets and buffer of the
+  // Hermite densities the gradient contracts
+  int4* d_nuc_list = nullptr;
+  int nuc_cnt[2 * eri::LMAX + 1] = {}, nuc_first[2 * eri::LMAX + 2] = {};
+  int* d_nuc_goff = nullptr;
+  double* d_nuc_dens = nullptr;
+  int nuc_built = 0;
 
   int alloc_pairs();
   int geometry(cudaStream_t s, bool rebuild_q);
@@ -103,3 +116,40 @@ struct eri_plan_impl {
   dim3 mat_grid(int block) const;
   void release();
 };
+
+// packed per-molecule matrices: molecule m's nbf_m x nbf_m block at off[m], AO offset aobase[m]
+struct MolMats {
+  const int64_t* off;
+  const int* n;
+  const int* aobase;
+};
+MolMats molmats(const eri_plan_impl* P);
+void k_scale_d_launch(const eri_plan_impl* P, const double* D, cudaStream_t s);  // D' = D f f into P->d_Dp
+
+// runtime-l E^{ij}_t (Eq. E_recursion), E[(i*5+j)*9+t], i,j <= 4
+__device__ __forceinline__ void md_e_rt(int li, int lj, double PA, double PB, double o2p, double* E) {
+  for (int x = 0; x < 225; ++x) E[x] = 0.0;
+  E[0] = 1.0;
+  for (int i = 0; i < li; ++i)
+    for (int t = 0; t <= i + 1; ++t) {
+      double v = PA * E[(i * 5) * 9 + t];
+      if (t > 0) v += o2p * E[(i * 5) * 9 + t - 1];
+      if (t + 1 <= i) v += (t + 1) * E[(i * 5) * 9 + t + 1];
+      E[((i + 1) * 5) * 9 + t] = v;
+    }
+  for (int i = 0; i <= li; ++i)
+    for (int j = 0; j < lj; ++j)
+      for (int t = 0; t <= i + j + 1; ++t) {
+        double v = PB * E[(i * 5 + j) * 9 + t];
+        if (t > 0) v += o2p * E[(i * 5 + j) * 9 + t - 1];
+        if (t + 1 <= i + j) v += (t + 1) * E[(i * 5 + j) * 9 + t + 1];
+        E[(i * 5 + j + 1) * 9 + t] = v;
+      }
+}
+
+// Cartesian J from Hermite J per primitive pair (plan.cu); sig == nullptr takes every pair
+__global__ void k_post_j(int npair, const int* __restrict__ s1, const int* __restrict__ s2, const int* __restrict__ np,
+                         const int* __restrict__ poff, const int* __restrict__ hoff, const int* __restrict__ sh_l,
+                         const int* __restrict__ pao1, const int* __restrict__ pao2, const int* __restrict__ pmol,
+                         MolMats mm, const int* __restrict__ sig, eri::PairData pd, const double* __restrict__ Jh,
+                         const double* __restrict__ f, double* __restrict__ J, int det, int* __restrict__ status);

@@ -116,3 +116,26 @@ def test_autotune_and_cache(eri, tmp_path):
     # a second plan of the same shape loads the cached table instead of tuning
     p2 = eri.Plan(basis, precision=1, mixed_tau=1e-3)
     assert np.array_equal(p2.autotune(Dt, cache=cache), t)
+
+
+def test_c_level_tune_cache(eri, tmp_path):
+    """opts.tune_cache: eri_autotune stores the tuned table under this device,
+    plan shape and precision; a new plan with the same cache loads it; a plan of
+    another shape does not."""
+    import torch
+    basis, D = W.workload(0)
+    path = str(tmp_path / "tiles.txt")
+    p1 = eri.Plan(basis, precision=1, mixed_tau=1e-3, tune_cache=path)
+    Dt = torch.from_numpy(D).cuda()
+    p1.set_tiles(np.full((10, 10, 2), 3, np.int32))  # a table the tuner would not pick by itself
+    t1 = p1.autotune(Dt, precision=1, trial_ms=0.5)
+    lines = open(path).read().splitlines()
+    assert len(lines) == 1 and "|prec=1" in lines[0] and f"|nbf={basis.nbf}|" in lines[0]
+    p2 = eri.Plan(basis, precision=1, mixed_tau=1e-3, tune_cache=path)
+    assert np.array_equal(p2.tiles(), t1)
+    b2, _ = W.small_system(["1s1p1d", "2s1p"], seed=4)
+    p3 = eri.Plan(b2, precision=1, tune_cache=path)
+    assert np.array_equal(p3.tiles(), eri.Plan(b2, precision=1).tiles())
+    # FP64 tuning adds its own entry next to the mixed one
+    p1.autotune(Dt, precision=0, trial_ms=0.5)
+    assert len(open(path).read().splitlines()) == 2
