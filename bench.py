@@ -192,7 +192,16 @@ def traffic_for(X, Y, tier):
     return d.get("kernels", {}).get(f"{CLASS_NAMES[X]}|{CLASS_NAMES[Y]}|{tier}")
 
 
-def class_rows(prof, steps):
+TIER_NAMES = {0: "fp64", 1: "fp32", 2: "grad-fp64", 3: "jengine-fp64"}
+
+
+def tier_peak(tier, peaks=None):
+    """ALU peak of a profile tier: FP32 for tier 1, FP64 for the rest (nominal, or `peaks` if given)."""
+    p = peaks if peaks is not None else PEAK_TFLOPS
+    return p[1] if tier == 1 else p[0]
+
+
+def class_rows(prof, steps, peaks=None):
     """[class, tier, ms per step, TFLOP/s, fraction of the tier's ALU peak] for
     every profiled class launch, longest first.  `flops` of a record is per step
     (all launches of that class in one build); `ms` sums `steps` builds."""
@@ -200,8 +209,8 @@ def class_rows(prof, steps):
     for r in sorted(prof, key=lambda r: -r["ms"]):
         tf = r["flops"] / (r["ms"] / steps * 1e-3) / 1e12 if r["ms"] > 0 else 0.0
         rows.append([f"({CLASS_NAMES[r['bra_class']]}|{CLASS_NAMES[r['ket_class']]})",
-                     "fp64" if r["tier"] == 0 else "fp32", round(r["ms"] / steps, 3), round(tf, 4),
-                     round(tf / PEAK_TFLOPS[r["tier"]], 5)])
+                     TIER_NAMES[r["tier"]], round(r["ms"] / steps, 3), round(tf, 4),
+                     round(tf / tier_peak(r["tier"], peaks), 5)])
     return rows
 
 
@@ -383,6 +392,12 @@ def run_ours(args, rank, world, local_rank):
     plan.close()
     if rank == 0 and world == 1 and args.batch_mols > 0:
         out["batch"] = run_batch(args, dev, flush)
+    if rank == 0 and world == 1 and not args.no_legs:
+        out["jengine"] = run_jengine_leg(args, dev, peak_meas)
+        out["longrange"] = run_longrange_leg(args, dev)
+        out["nuclear"] = run_nuclear_leg(args, dev)
+        if args.grad_steps > 0:
+            out["gradient"] = run_gradient_leg(args, dev, peak_meas)
     if rank == 0 and not args.no_cpu_baseline:
         p2 = eri.Plan(basis, thresh=THRESH, device=local_rank)
         quartets = sample_quartets(p2.lists(), basis, 400000, seed=1234)
@@ -392,6 +407,159 @@ def run_ours(args, rank, world, local_rank):
                                "sample": f"{ns} seeded uniformly sampled significant canonical shell quartets of "
                                          f"this workload, contracted ERI blocks in FP64 ({dt:.1f} s)"}
     return out
+
+
+def _events(stream):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+
+def run_gradient_leg(args, dev, peaks):
+    """Nuclear gradient of E = 1/2 tr(DJ) - 1/4 tr(DK) for the 30-atom, 750-bf
+    system (3s2p1d1f per atom, seed 1003) through the autograd Function:
+    forward (move atoms, FP64 J/K build, energy) and backward (derivative-ERI
+    kernels contracted with D), CUDA events on the plan's stream; the gradient
+    class launches profiled in the library."""
+    import torch
+    import paper_2406_14920_gb300 as eri
+    import workloads as W
+    basis, D = W.workload(3)
+    plan = eri.Plan(basis, thresh=THRESH, precision=eri.ERI_FP64, device=dev.index, profile=True)
+    stream = torch.cuda.current_stream(dev)
+    R = torch.from_numpy(basis.coords).to(dev)
+    Dt = torch.from_numpy(D).to(dev)
+    fwd, bwd, fl, gms = [], [], 0.0, 0.0
+    rows = []
+    for step in range(args.grad_steps + 1):  # the first pass is warm-up (lists, tables, caches)
+        Rg = R.clone().requires_grad_(True)
+        e0, e1, e2 = _events(stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        E = eri.jk_energy(Rg, Dt, plan)
+        e1.record(stream)
+        E.backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        prof = plan.profile()
+        if step == 0:
+            continue
+        fwd.append(e0.elapsed_time(e1))
+        bwd.append(e1.elapsed_time(e2))
+        g = [r for r in prof if r["tier"] == 2]
+        fl += sum(r["flops"] for r in g)
+        gms += sum(r["ms"] for r in g)
+        rows = class_rows(g, 1, peaks)
+    net = float(Rg.grad.sum(dim=0).abs().max())
+    plan.close()
+    n = len(bwd)
+    tf = fl / (gms * 1e-3) / 1e12 if gms > 0 else 0.0
+    return {"workload": "30 atoms 3s2p1d1f (750 bf), seed 1003, Schwarz 1e-12, FP64 quartets and accumulation",
+            "forward_ms": sum(fwd) / n, "backward_ms": sum(bwd) / n, "steps": n,
+            "backward_over_forward": (sum(bwd) / n) / (sum(fwd) / n),
+            "gradient_tflops": round(tf, 4), "frac_fp64_nominal": round(tf / PEAK_TFLOPS[0], 4),
+            "frac_fp64_measured": round(tf / peaks[0], 4), "max_abs_net_force": net,
+            "class_roofline": {"columns": ["class", "tier", "ms_per_step", "tflops", "frac_of_measured_peak"],
+                               "rows": rows[:24]}}
+
+
+def run_jengine_leg(args, dev, peaks):
+    """J-only FP64 build of the bench workload through the J-engine (Eq. j_formula)."""
+    import torch
+    import paper_2406_14920_gb300 as eri
+    import workloads as W
+    basis, D = W.workload(WORKLOAD_ID)
+    plan = eri.Plan(basis, thresh=THRESH, device=dev.index, profile=True)
+    stream = torch.cuda.current_stream(dev)
+    Dt = torch.from_numpy(D).to(dev)
+    J = torch.empty_like(Dt)
+    plan.build_jk(Dt, J, None, want_k=False)
+    torch.cuda.synchronize()
+    plan.profile()
+    e0, e1, _ = _events(stream)
+    e0.record(stream)
+    for _ in range(args.aux_steps):
+        plan.build_jk(Dt, J, None, want_k=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.aux_steps
+    prof = [r for r in plan.profile() if r["tier"] == 3]
+    nq = plan.stats()["quartets_j"]
+    plan.close()
+    fl = sum(r["flops"] for r in prof) / args.aux_steps
+    kms = sum(r["ms"] for r in prof) / args.aux_steps
+    tf = fl / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
+    return {"ms_per_step": ms, "ordered_pair_pairs_per_s": nq / (ms * 1e-3), "steps": args.aux_steps,
+            "tflops": round(tf, 4), "frac_fp64_measured": round(tf / peaks[0], 4),
+            "class_roofline": {"columns": ["class", "tier", "ms_per_step", "tflops", "frac_of_measured_peak"],
+                               "rows": class_rows(prof, args.aux_steps, peaks)[:16]}}
+
+
+def run_longrange_leg(args, dev):
+    """Mixed-precision J+K build of the bench workload with the long-range
+    operator erf(omega r)/r, omega = 0.3 (Sec. 2.5, Eq. eri_longrange_formula)."""
+    import torch
+    import paper_2406_14920_gb300 as eri
+    import workloads as W
+    basis, D = W.workload(WORKLOAD_ID)
+    plan = eri.Plan(basis, thresh=THRESH, precision=eri.ERI_MIXED, mixed_tau=args.tau, device=dev.index,
+                    tune_cache=args.tune_cache)
+    plan.set_omega(0.3)
+    stream = torch.cuda.current_stream(dev)
+    Dt = torch.from_numpy(D).to(dev)
+    J, K = torch.empty_like(Dt), torch.empty_like(Dt)
+    plan.build_jk(Dt, J, K)
+    torch.cuda.synchronize()
+    e0, e1, _ = _events(stream)
+    e0.record(stream)
+    for _ in range(args.aux_steps):
+        plan.build_jk(Dt, J, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.aux_steps
+    E = plan.energy(Dt, J, K).cpu().numpy()
+    nq = plan.stats()["quartets_k"]
+    plan.close()
+    return {"omega": 0.3, "ms_per_step": ms, "value": nq / (ms * 1e-3), "unit": UNIT, "steps": args.aux_steps,
+            "E_J": float(E[0]), "E_K": float(E[1])}
+
+
+def run_nuclear_leg(args, dev):
+    """Point-charge attraction V = sum_C q_C (m|1/|r-C||n) and the gradient of
+    sum D V for the bench workload's basis with its 60 nuclei plus a seeded
+    cloud of 20000 point charges around it (a QM/MM-like field)."""
+    import torch
+    import paper_2406_14920_gb300 as eri
+    import workloads as W
+    basis, D = W.workload(WORKLOAD_ID)
+    rng = np.random.default_rng(77)
+    ncloud = 20000
+    lo, hi = basis.coords.min(axis=0) - 8.0, basis.coords.max(axis=0) + 8.0
+    cloud = rng.uniform(lo, hi, (ncloud, 3))
+    q = np.concatenate([-np.where(np.bincount(basis.shell_atom, minlength=basis.natom) > 3, 6.0, 1.0),
+                        rng.uniform(-0.8, 0.8, ncloud)])
+    C = np.concatenate([basis.coords, cloud])
+    plan = eri.Plan(basis, thresh=THRESH, device=dev.index)
+    stream = torch.cuda.current_stream(dev)
+    qt, Ct, Dt = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (q, C, D))
+    V = plan.nuclear(qt, Ct)
+    plan.nuclear_grad(Dt, qt, Ct)
+    torch.cuda.synchronize()
+    e0, e1, e2 = _events(stream)
+    e0.record(stream)
+    for _ in range(args.aux_steps):
+        plan.nuclear(qt, Ct, V)
+    e1.record(stream)
+    for _ in range(args.aux_steps):
+        gR, gC = plan.nuclear_grad(Dt, qt, Ct)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    npr = basis.shell_nprim.astype(np.int64)
+    npp = int((npr.sum() ** 2 + (npr ** 2).sum()) // 2)  # primitive pairs of the shell pairs a >= b
+    ms_v, ms_g = e0.elapsed_time(e1) / args.aux_steps, e1.elapsed_time(e2) / args.aux_steps
+    plan.close()
+    return {"charges": int(len(q)), "primitive_pairs": npp, "V_ms": ms_v, "gradient_ms": ms_g,
+            "steps": args.aux_steps, "pair_charge_terms_per_s": npp * len(q) / (ms_v * 1e-3),
+            "max_abs_net_force": float((gR.sum(dim=0) + gC.sum(dim=0)).abs().max())}
 
 
 def run_batch(args, dev, flush):
@@ -518,6 +686,10 @@ def main():
     ap.add_argument("--batch-mols", type=int, default=12,
                     help="molecules of the 64-molecule set in the batched leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the J-engine, long-range, point-charge and gradient legs")
+    ap.add_argument("--aux-steps", type=int, default=2, help="timed steps of the J-engine / long-range / V legs")
+    ap.add_argument("--grad-steps", type=int, default=1, help="timed gradient steps (after one warm-up pass)")
     ap.add_argument("--ncu-case", action="store_true",
                     help="small case for ncu section captures: the first 20 atoms of the workload, two mixed "
                          "builds and one gradient")

@@ -84,6 +84,12 @@ typedef struct {
                              give bit-identical results.  Accumulated magnitudes must stay below 2^17;
                              an element above 2^16 sets the device status (see eri_check).  0 (default):
                              FP64 atomics, results equal to rounding only. */
+  int32_t density_screen; /* 1: J+K and K builds also drop every quartet whose density-weighted bound
+                             Q_ab Q_cd max|D'| (float32; max over the six D' blocks the quartet
+                             touches, D' = D with component norms) is below the threshold
+                             (Eq. kernel_upperbound with the density factor; a device pass
+                             compacts the kept quartets per build).  J-only J-engine builds and
+                             gradients are not screened.  0 (default): lists only (Q_ab Q_cd). */
 } eri_opts_t;
 
 typedef struct {
@@ -97,6 +103,7 @@ typedef struct {
   int64_t quartets_k_guard; /* of quartets_k, kept in FP64 by the last mixed build's FP32 range guard
                                alone (their bound was below mixed_tau, but an exponent sum above 1e3
                                or a primitive prefactor product above 1e18 would overflow FP32) */
+  int64_t quartets_k_screened; /* of quartets_k, dropped by the density screen in the last build */
 } eri_stats_t;
 
 /* Fill opts with the defaults listed above.  Host only. */
@@ -272,7 +279,8 @@ int eri_get_lists(eri_plan_t* plan, float* Q, int32_t* sig, int32_t* counts, int
 /* One class launch of the J/K build, as seen by eri_get_profile. */
 typedef struct {
   int32_t bra_class, ket_class; /* pair classes 0..9 = ss ps pp ds dp dd fs fp fd ff */
-  int32_t tier;                 /* 0 = FP64, 1 = FP32 (mixed precision) */
+  int32_t tier;                 /* 0 = FP64 J/K, 1 = FP32 J/K (mixed precision), 2 = gradient (FP64,
+                                   eri_jk_grad), 3 = J-engine (FP64, J-only builds) */
   int32_t launches;             /* profiled launches summed into ms */
   double ms;                    /* total device time of those launches (CUDA events on the build stream) */
   int64_t quartets;             /* canonical shell quartets of the last build's launch */
@@ -281,8 +289,12 @@ typedef struct {
 } eri_launch_prof_t;
 
 /*
- * Per-launch device times of every eri_build_jk since the previous call, for a
- * plan created with opts.profile = 1 (Cartesian J/K path).  Fills up to cap
+ * Per-launch device times of every eri_build_jk and eri_jk_grad since the
+ * previous call, for a plan created with opts.profile = 1 (eager builds; graph
+ * builds are not profiled).  quartets / prim_quartets count the launch's work
+ * items (ordered (bra, ket) pairs for the gradient and the J-engine); flops is
+ * the algorithmic FLOP count of the implemented McMurchie-Davidson chain for
+ * those items.  Fills up to cap
  * entries of out (host), sets *count to the number of (class pair, tier)
  * launches, synchronises, and resets the record.
  */

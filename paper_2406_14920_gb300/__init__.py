@@ -39,7 +39,7 @@ class BasisT(C.Structure):
 class OptsT(C.Structure):
     _fields_ = [("thresh", C.c_double), ("precision", C.c_int32), ("mixed_tau", C.c_double),
                 ("device", C.c_int32), ("j_engine", C.c_int32), ("profile", C.c_int32),
-                ("tune_cache", C.c_char_p), ("deterministic", C.c_int32)]
+                ("tune_cache", C.c_char_p), ("deterministic", C.c_int32), ("density_screen", C.c_int32)]
 
 
 class LaunchProfT(C.Structure):
@@ -51,7 +51,7 @@ class StatsT(C.Structure):
     _fields_ = [("nbf", C.c_int32), ("nshell", C.c_int32), ("npair", C.c_int32), ("nsig_pair", C.c_int32),
                 ("quartets_k", C.c_int64), ("quartets_j", C.c_int64), ("prim_quartets_k", C.c_int64),
                 ("quartets_k_fp32", C.c_int64), ("flops_k", C.c_double), ("flops_j", C.c_double),
-                ("device_status", C.c_int32), ("quartets_k_guard", C.c_int64)]
+                ("device_status", C.c_int32), ("quartets_k_guard", C.c_int64), ("quartets_k_screened", C.c_int64)]
 
 
 def lib():
@@ -152,7 +152,7 @@ class Plan:
     """
 
     def __init__(self, basis, coords=None, thresh=1e-12, precision=ERI_FP64, mixed_tau=1e-5, device=None,
-                 j_engine=True, profile=False, tune_cache=None, deterministic=False):
+                 j_engine=True, profile=False, tune_cache=None, deterministic=False, density_screen=False):
         L = lib()
         self.batched = isinstance(basis, (list, tuple))
         bases = list(basis) if self.batched else [basis]
@@ -184,6 +184,7 @@ class Plan:
         o.profile = int(bool(profile))
         o.tune_cache = os.fsencode(tune_cache) if tune_cache else None
         o.deterministic = int(bool(deterministic))
+        o.density_screen = int(bool(density_screen))
         h = C.c_void_p()
         if self.batched:
             bp = (C.POINTER(BasisT) * len(bases))(*[C.pointer(bts[m]) for m in range(len(bases))])

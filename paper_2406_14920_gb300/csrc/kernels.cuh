@@ -32,6 +32,8 @@ struct KArgs {
   int tier_want;        // 0 or 1: which tier this launch processes
   unsigned long long* counter;  // items processed by this launch's tier (may be null)
   unsigned long long* guard;    // tier split: quartets kept in FP64 by the range guard alone (may be null)
+  unsigned long long* screened; // tier split: quartets dropped by the density screen (may be null)
+  float screen;                 // density screen (Eq. kernel_upperbound): drop Q_ab Q_cd max|D'| < screen; 0 = off
   int same_class;
   // Mixed precision: the launch runs the compacted list of its tier written by
   // k_tier_split, item i = (bra position items[i].x, ket position items[i].y),
@@ -64,7 +66,8 @@ __device__ __forceinline__ int pair_index(const KArgs& a, int mol, int x, int y)
 }
 
 // Tier of one quartet: 0 = FP64 (bound >= tau), 1 = FP32, 2 = FP64 because
-// the FP32 range guard tripped although the bound is below tau.
+// the FP32 range guard tripped although the bound is below tau, 3 = dropped
+// by the density screen (bound below `screen`).
 __device__ __forceinline__ int quartet_tier(const KArgs& a, int mol, int pb_id, int pk_id, int s1, int s2, int s3,
                                             int s4) {
   const float* dm = a.dmax;
@@ -72,6 +75,7 @@ __device__ __forceinline__ int quartet_tier(const KArgs& a, int mol, int pb_id, 
                   fmaxf(fmaxf(__ldg(dm + pair_index(a, mol, s1, s3)), __ldg(dm + pair_index(a, mol, s1, s4))),
                         fmaxf(__ldg(dm + pair_index(a, mol, s2, s3)), __ldg(dm + pair_index(a, mol, s2, s4)))));
   const float b = __ldg(a.Q + pb_id) * __ldg(a.Q + pk_id) * d;
+  if (b < a.screen) return 3;
   // FP32 range guard: tight exponents or large prefactors stay in FP64
   // (R grows like (2 rho)^(L/2) and the prefactors multiply into it)
   const bool wide = fmaxf(__ldg(a.pmaxp + pb_id), __ldg(a.pmaxp + pk_id)) > a.pmax32 ||
@@ -96,6 +100,7 @@ struct JArgs {
   double omega2;        // erf(omega r)/r: omega^2 (0 = Coulomb)
   float omega2f;
   int det;              // 1: fixed-point Jherm (deterministic builds)
+  unsigned long long* counter;  // items, primitive quartets, bra primitives of this launch (may be null)
 };
 
 // omega^2 of a launch in its precision
@@ -241,6 +246,7 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
   }
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t total = a.wl.total;
+  unsigned long long done = 0, doneq = 0, doneb = 0;
   const int64_t tile = a.wl.tile, ntiles = (total - a.wl.first + tile - 1) / tile;
   for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * a.wl.nshard + a.wl.shard; tl < ntiles;
        tl += nwarps * a.wl.nshard) {
@@ -254,6 +260,9 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
     const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
     const int npb = __ldg(a.sp.np + pb_id), offb = __ldg(a.sp.poff + pb_id);
     const int npk = __ldg(a.sp.np + pk_id), offk = __ldg(a.sp.poff + pk_id);
+    ++done;
+    doneq += (unsigned long long)npb * npk;
+    doneb += npb;
     const int hb = __ldg(a.sp.hoff + pb_id), hk = __ldg(a.sp.hoff + pk_id);
     for (int pb = 0; pb < npb; ++pb) {
       Prim<T> bp;
@@ -298,6 +307,11 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
       }
     }
   }
+  }
+  if (a.counter && lane == 0 && done) {
+    atomicAdd(a.counter, done);
+    atomicAdd(a.counter + 1, doneq);
+    atomicAdd(a.counter + 2, doneb);
   }
 }
 

@@ -32,6 +32,7 @@ struct GradArgs {
   double cj, ck;       // weights of the Coulomb and exchange parts (1 or 0)
   double omega2;       // erf(omega r)/r: omega^2 (0 = Coulomb)
   int det;             // 1: fixed-point gradient accumulator (deterministic builds)
+  unsigned long long* counter;  // items, primitive quartets, bra primitives of this launch (may be null)
 };
 
 // E^{ij}_t and E^{ij,(1)}_t for one direction, i <= LI, j <= LJ, t <= i+j,
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
   T* Ws = sm + S::SM_W;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t total = a.wl.total;
+  unsigned long long done = 0, doneq = 0, doneb = 0;
   const int64_t tile = a.wl.tile, ntiles = (total - a.wl.first + tile - 1) / tile;
   for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * a.wl.nshard + a.wl.shard; tl < ntiles;
        tl += nwarps * a.wl.nshard) {
@@ -191,6 +193,9 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
     const int npk = __ldg(a.sp.np + pk_id), offk = __ldg(a.sp.poff + pk_id), ek0 = __ldg(a.sp.eoff + pk_id);
     const int ao1 = __ldg(a.sp.ao1 + pb_id), ao2 = __ldg(a.sp.ao2 + pb_id);
     const int ao3 = __ldg(a.sp.ao1 + pk_id), ao4 = __ldg(a.sp.ao2 + pk_id);
+    ++done;
+    doneq += (unsigned long long)npb * npk;
+    doneb += npb;
     T w = T(1);
     if (s1 == s2) w *= T(0.5);
     if (s3 == s4) w *= T(0.5);
@@ -423,6 +428,11 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
     }
     __syncwarp();
   }
+  }
+  if (a.counter && lane == 0 && done) {
+    atomicAdd(a.counter, done);
+    atomicAdd(a.counter + 1, doneq);
+    atomicAdd(a.counter + 2, doneb);
   }
 }
 

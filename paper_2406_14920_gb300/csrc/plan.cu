@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(256) k_tier_split(KArgs a, int2* __restrict__ 
     }
     const unsigned gm = __ballot_sync(0xffffffffu, tier == 2);
     if (gm && lane == 0 && a.guard) atomicAdd(a.guard, (unsigned long long)__popc(gm));
+    const unsigned sm = __ballot_sync(0xffffffffu, tier == 3);
+    if (sm && lane == 0 && a.screened) atomicAdd(a.screened, (unsigned long long)__popc(sm));
     if (tier == 2) tier = 0;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -860,7 +862,7 @@ void eri_plan_impl::release() {
                   d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Jh, d_Dherm,
                   d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp, d_ea,
                   d_mat_off, d_mat_n, d_aobase, d_pbase, d_pmol, d_shloc, d_ccm, d_segloc, d_Dpf,
-                  d_nuc_list, d_nuc_goff, d_nuc_dens};
+                  d_nuc_list, d_nuc_goff, d_nuc_dens, d_counters2};
   for (auto& e : prof_events) cudaEventDestroy(e);
   prof_events.clear();
   if (gexec) cudaGraphExecDestroy(gexec);
@@ -968,6 +970,42 @@ static double class_flops(int X, int Y, double nq, double npq, double nbp, bool 
   return npq * per_pq + nbp * per_bp + nq * per_q;
 }
 
+// J-engine (Eq. j_formula) per primitive quartet of an ordered (bra, ket) item:
+// Boys 2(L+1)+20, R recursion, J_P += sum_Q R_{P+Q} D_Q: 2 nherm(lab) nherm(lcd).
+static double jengine_flops(int X, int Y, double npq) {
+  const int lab = kClassL1[X] + kClassL2[X], lcd = kClassL1[Y] + kClassL2[Y], L = lab + lcd;
+  double rf = 0.0;
+  for (int m = 0; m < L; ++m) rf += 3.0 * (nherm(L - m) - 1);
+  return npq * (2.0 * (L + 1) + 20.0 + rf + 2.0 * nherm(lab) * nherm(lcd));
+}
+
+// Gradient (bra derivatives, SI Eq. si_dE_J / si_dE_K) per ordered item:
+//   per primitive quartet: Boys 2(L+2)+20, R recursion to L+1, ket transform
+//     2 nherm(lab+1) sum_{cd} prod_t (k_t+l_t+1);
+//   per bra primitive: for every (ab, cd), direction t opened to n_t+1 (raised
+//     Hermite index) and the other two closed: 2 sum_t (n_t+2) prod_{u!=t} (n_u+1)
+//     plus 4 (n_t+2) for the A and B coefficients;
+//   per item: the density factor, 8 FLOPs per (ab, cd).
+static double grad_flops(int X, int Y, double nq, double npq, double nbp) {
+  const int la = kClassL1[X], lb = kClassL2[X], lc = kClassL1[Y], ld = kClassL2[Y];
+  const int L1 = la + lb + lc + ld + 1;
+  double rf = 0.0;
+  for (int m = 0; m < L1; ++m) rf += 3.0 * (nherm(L1 - m) - 1);
+  double dab = 0.0;
+  for (int x = 0; x < ncart(la); ++x)
+    for (int y = 0; y < ncart(lb); ++y) {
+      int ix, iy, iz, jx, jy, jz;
+      cart_xyz(la, x, ix, iy, iz);
+      cart_xyz(lb, y, jx, jy, jz);
+      const int n[3] = {ix + jx, iy + jy, iz + jz};
+      for (int t = 0; t < 3; ++t)
+        dab += 2.0 * (n[t] + 2) * (n[(t + 1) % 3] + 1) * (n[(t + 2) % 3] + 1) + 4.0 * (n[t] + 2);
+    }
+  const double nab = ncart(la) * ncart(lb), ncd = ncart(lc) * ncart(ld);
+  const double per_pq = 2.0 * (L1 + 1) + 20.0 + rf + 2.0 * nherm(la + lb + 1) * sum_terms(lc, ld);
+  return npq * per_pq + nbp * ncd * dab + nq * 8.0 * nab * ncd;
+}
+
 // Default work-tile length: the thread kernel's lanes already take adjacent
 // items; a warp kernel takes 4 consecutive quartets (mostly one bra) per tile.
 static int default_tile(int X, int Y, int tier) {
@@ -997,6 +1035,7 @@ extern "C" int eri_default_opts(eri_opts_t* o) {
   o->profile = 0;
   o->tune_cache = nullptr;
   o->deterministic = 0;
+  o->density_screen = 0;
   return ERI_OK;
 }
 
@@ -1247,7 +1286,9 @@ static int plan_create(int nmol, const eri_basis_t* const* bases, const double* 
     CKP(dalloc(&P->d_peoff, npair)); CKP(dalloc(&P->d_E, ne_tot)); CKP(dalloc(&P->d_Ef, ne_tot));
     CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_prefmaxp, npair)); CKP(dalloc(&P->d_ea, nprimpair));
     CKP(dalloc(&P->d_dmax, npair));
-    CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3 + 1));  // + range-guard count
+    CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3 + 2));  // + range-guard and screened counts
+    CKP(dalloc(&P->d_counters2, 2 * NPAIRCLASS * NPAIRCLASS * 3));
+    CKP(cudaMemset(P->d_counters2, 0, sizeof(unsigned long long) * 2 * NPAIRCLASS * NPAIRCLASS * 3));
     CKP(dalloc(&P->d_rsteps, st.size()));
     CKP(dalloc(&P->d_Dp, (size_t)P->nmat)); CKP(dalloc(&P->d_Dpf, (size_t)P->nmat));
     CKP(dalloc(&P->d_Kh, (size_t)P->nmat));
@@ -1341,6 +1382,8 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
       CK(cudaEventRecord(P->fork_ev, s));
       for (int b = 0; b < eri_plan_impl::kBranches; ++b) CK(cudaStreamWaitEvent(P->branch[b], P->fork_ev, 0));
     }
+    CK(cudaMemsetAsync(P->d_counters2, 0, sizeof(unsigned long long) * NPAIRCLASS * NPAIRCLASS * 3, s));
+    const bool prof = P->opts.profile && !concurrent;
     int nl = 0;
     for (int X = 0; X < NPAIRCLASS; ++X)
       for (int Y = 0; Y < NPAIRCLASS; ++Y) {
@@ -1348,6 +1391,12 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
         if (ja.wl.total == 0) continue;
         const cudaStream_t ls = concurrent ? P->branch[nl++ % eri_plan_impl::kBranches] : s;
         const int lab = kClassL1[X] + kClassL2[X], lcd = kClassL1[Y] + kClassL2[Y];
+        ja.counter = P->d_counters2 + (X * NPAIRCLASS + Y) * 3;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (prof) {
+          CK(P->prof_event_pair(&e0, &e1));
+          CK(cudaEventRecord(e0, ls));
+        }
         cudaError_t e = cudaErrorInvalidValue;
         switch (lab) {
           case 0: e = launch_j_lab0(lcd, 0, ja, ls, P->nsm); break;
@@ -1359,6 +1408,10 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
           case 6: e = launch_j_lab6(lcd, 0, ja, ls, P->nsm); break;
         }
         CK(e);
+        if (prof) {
+          CK(cudaEventRecord(e1, ls));
+          P->prof_log.push_back({X, Y, 3, P->prof_ev_used - 2});
+        }
       }
     if (concurrent)
       for (int b = 0; b < eri_plan_impl::kBranches; ++b) {
@@ -1375,9 +1428,11 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
     // J and/or K from contracted Cartesian ERIs over canonical quartets
     if (K) CK(cudaMemsetAsync(P->d_Kh, 0, sizeof(double) * nn, s));
     if (J) CK(cudaMemsetAsync(P->d_Jh, 0, sizeof(double) * nn, s));
-    CK(cudaMemsetAsync(P->d_counters, 0, sizeof(unsigned long long) * (NPAIRCLASS * NPAIRCLASS * 6 + 1), s));
+    CK(cudaMemsetAsync(P->d_counters, 0, sizeof(unsigned long long) * (NPAIRCLASS * NPAIRCLASS * 6 + 2), s));
     const bool mixed = precision == ERI_MIXED;
-    if (mixed) {
+    // the device split pass serves the precision tiers and the density screen
+    const bool split = mixed || P->opts.density_screen;
+    if (split) {
       k_dmax<<<grid1(P->npair, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_sh_l, P->d_pao1, P->d_pao2,
                                                   P->d_pmol, P->d_mat_off, P->d_mat_n, P->d_Dp, P->d_dmax);
       CK(cudaGetLastError());
@@ -1388,9 +1443,11 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
     ka.rsteps = P->d_rsteps; ka.Dp = P->d_Dp; ka.Dpf = P->d_Dpf; ka.Kh = K ? P->d_Kh : nullptr;
     ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
     ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
-    ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
+    ka.tau = mixed ? (float)P->opts.mixed_tau : 0.0f; ka.pmax32 = (float)kPmax32; ka.mixed = mixed ? 1 : 0;
     ka.items = nullptr; ka.nitems = nullptr;
     ka.guard = P->d_counters + NPAIRCLASS * NPAIRCLASS * 6;
+    ka.screened = P->d_counters + NPAIRCLASS * NPAIRCLASS * 6 + 1;
+    ka.screen = P->opts.density_screen ? (float)P->thresh : 0.0f;
     ka.omega2 = P->omega * P->omega; ka.omega2f = (float)ka.omega2;
     ka.det = P->opts.deterministic ? 1 : 0;
     ja.Jh = J ? P->d_Jh : nullptr;
@@ -1407,11 +1464,11 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
         order.push_back({X, Y, class_flops(X, Y, (double)tot, (double)P->h_kprim[X * NPAIRCLASS + Y], 0.0,
                                            J != nullptr, K != nullptr)});
       }
-    if (mixed && !concurrent) {
+    if (split && !concurrent) {
       const int rc = P->ensure_tier_bufs(1);
       if (rc != ERI_OK) return rc;
     }
-    if (mixed && P->tier_nb < (concurrent ? eri_plan_impl::kBranches : 1)) return ERI_EINVAL;
+    if (split && P->tier_nb < (concurrent ? eri_plan_impl::kBranches : 1)) return ERI_EINVAL;
     if (concurrent) {
       std::stable_sort(order.begin(), order.end(), [](const L& a, const L& b) { return a.cost > b.cost; });
       CK(cudaEventRecord(P->fork_ev, s));
@@ -1444,7 +1501,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
         ls = P->branch[b];
       }
       ka.same_class = l.X == l.Y;
-      if (!mixed) {
+      if (!split) {
         ka.wl = P->klist(l.X, l.Y);
         ka.items = nullptr;
         ka.nitems = nullptr;
@@ -1452,8 +1509,9 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
         if (rc != ERI_OK) return rc;
         continue;
       }
-      // mixed precision: split each window of the list into its two tiers
-      // (compacted on the device), then run each tier over its own list
+      // mixed precision and/or density screen: split each window of the list
+      // into its two tiers, dropping screened quartets (compacted on the
+      // device), then run each tier over its own list (FP64 builds: tier 0 only)
       const WorkList full = P->klist(l.X, l.Y);
       int2* buf = P->tbuf[b];
       unsigned int* cnt = P->tcnt + 2 * b;
@@ -1467,7 +1525,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
         k_tier_split<<<(int)std::max<int64_t>(1, std::min<int64_t>((nch + 7) / 8, (int64_t)P->nsm * 8)), 256, 0,
                        ls>>>(sa, buf, buf + P->tier_cap, cnt);
         CK(cudaGetLastError());
-        for (int tier = 0; tier < 2; ++tier) {
+        for (int tier = 0; tier < (mixed ? 2 : 1); ++tier) {
           ka.wl = full;
           ka.wl.first = 0;
           ka.wl.total = sa.wl.total - f;  // upper bound of the tier's count (grid sizing)
@@ -1522,7 +1580,7 @@ extern "C" int eri_build_jk_graph(eri_plan_t* plan, const double* D, double* J, 
   if (!P->gexec || P->gkey[0] != D || P->gkey[1] != J || P->gkey[2] != K || P->gprec != precision) {
     int rc = P->ensure_streams();
     if (rc != ERI_OK) return rc;
-    if (precision == ERI_MIXED) {
+    if (precision == ERI_MIXED || P->opts.density_screen) {
       rc = P->ensure_tier_bufs(eri_plan_impl::kBranches);
       if (rc != ERI_OK) return rc;
     }
@@ -1844,11 +1902,23 @@ extern "C" int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int3
   ga.ck = want_k ? 1.0 : 0.0;
   ga.omega2 = P->omega * P->omega;
   ga.det = P->opts.deterministic ? 1 : 0;
+  unsigned long long* gcnt = P->d_counters2 + NPAIRCLASS * NPAIRCLASS * 3;
+  CK(cudaMemsetAsync(gcnt, 0, sizeof(unsigned long long) * NPAIRCLASS * NPAIRCLASS * 3, s));
   for (int X = 0; X < NPAIRCLASS; ++X)
     for (int Y = 0; Y < NPAIRCLASS; ++Y) {
       ga.wl = P->jlist(X, Y);
       if (ga.wl.total == 0) continue;
+      ga.counter = gcnt + (X * NPAIRCLASS + Y) * 3;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (P->opts.profile) {
+        CK(P->prof_event_pair(&e0, &e1));
+        CK(cudaEventRecord(e0, s));
+      }
       CK(launch_grad_class(X, Y, ga, s, P->nsm));
+      if (P->opts.profile) {
+        CK(cudaEventRecord(e1, s));
+        P->prof_log.push_back({X, Y, 2, P->prof_ev_used - 2});
+      }
     }
   if (ga.det) {
     k_fix_to_double<<<grid1(3 * P->natom, 128), 128, 0, s>>>(3 * P->natom, dEdR, P->d_status);
@@ -1901,9 +1971,10 @@ extern "C" int eri_get_stats(eri_plan_t* plan, eri_stats_t* st) {
     }
   }
   {
-    unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6 + 1];
+    unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6 + 2];
     CK(cudaMemcpy(c, P->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
     st->quartets_k_guard = P->last_mixed ? (int64_t)c[NPAIRCLASS * NPAIRCLASS * 6] : 0;
+    st->quartets_k_screened = (int64_t)c[NPAIRCLASS * NPAIRCLASS * 6 + 1];
     double fl = 0.0;
     for (int X = 0; X < NPAIRCLASS; ++X)
       for (int Y = 0; Y <= X; ++Y)
@@ -1926,23 +1997,26 @@ extern "C" int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t
   if (!P || !count || (cap > 0 && !out)) return ERI_EINVAL;
   CK(cudaSetDevice(P->device));
   CK(cudaDeviceSynchronize());
-  unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6];
+  unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6], c2[2 * NPAIRCLASS * NPAIRCLASS * 3];
   CK(cudaMemcpy(c, P->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
-  double ms[NPAIRCLASS * NPAIRCLASS * 2] = {};
-  int nl[NPAIRCLASS * NPAIRCLASS * 2] = {};
+  CK(cudaMemcpy(c2, P->d_counters2, sizeof(c2), cudaMemcpyDeviceToHost));
+  constexpr int NT = 4;  // tiers: 0 FP64 J/K, 1 FP32 J/K, 2 gradient, 3 J-engine
+  double ms[NPAIRCLASS * NPAIRCLASS * NT] = {};
+  int nl[NPAIRCLASS * NPAIRCLASS * NT] = {};
   for (const auto& r : P->prof_log) {
     float t = 0.0f;
     CK(cudaEventElapsedTime(&t, P->prof_events[r.ev], P->prof_events[r.ev + 1]));
-    const int k = (r.X * NPAIRCLASS + r.Y) * 2 + r.tier;
+    const int k = (r.X * NPAIRCLASS + r.Y) * NT + r.tier;
     ms[k] += t;
     nl[k] += 1;
   }
   int n = 0;
-  for (int k = 0; k < NPAIRCLASS * NPAIRCLASS * 2; ++k) {
+  for (int k = 0; k < NPAIRCLASS * NPAIRCLASS * NT; ++k) {
     if (!nl[k]) continue;
     if (n < cap) {
-      const int X = k / (2 * NPAIRCLASS), Y = (k / 2) % NPAIRCLASS, t = k % 2;
-      const unsigned long long* q = c + k * 3;
+      const int X = k / (NT * NPAIRCLASS), Y = (k / NT) % NPAIRCLASS, t = k % NT;
+      const unsigned long long* q = t < 2 ? c + ((X * NPAIRCLASS + Y) * 2 + t) * 3
+                                          : c2 + ((t == 3 ? 0 : 1) * NPAIRCLASS * NPAIRCLASS + X * NPAIRCLASS + Y) * 3;
       eri_launch_prof_t& o = out[n];
       o.bra_class = X;
       o.ket_class = Y;
@@ -1951,7 +2025,9 @@ extern "C" int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t
       o.ms = ms[k];
       o.quartets = (int64_t)q[0];
       o.prim_quartets = (int64_t)q[1];
-      o.flops = class_flops(X, Y, (double)q[0], (double)q[1], (double)q[2], P->last_do_j, P->last_do_k);
+      o.flops = t < 2 ? class_flops(X, Y, (double)q[0], (double)q[1], (double)q[2], P->last_do_j, P->last_do_k)
+                      : t == 2 ? grad_flops(X, Y, (double)q[0], (double)q[1], (double)q[2])
+                               : jengine_flops(X, Y, (double)q[1]);
     }
     ++n;
   }
