@@ -11,10 +11,14 @@ Obara-Saika / Head-Gordon-Pople, energies E_J = 1/2 tr(DJ), E_K = -1/4 tr(DK)
 J and K are symmetric for a symmetric D; the file holds the upper triangles of
 (J + J^T)/2 and (K + K^T)/2 (symmetrising moves an element by rounding only)
 plus the oracle's own energies and Schwarz bounds, keyed by a SHA-256 of the
-inputs (shell table, exponents, raw coefficients, coordinates, D, thresh) so a
-test can tell when the workload generator has changed and the file is stale.
+basis (shell table, exponents, raw coefficients, coordinates: exact draws of
+the seeded generator) and thresh, and by a fingerprint of D (D comes from a QR
+factorisation, whose last bits depend on the BLAS library and its thread
+count, so it is compared to 1e-12, not bit for bit).  A test uses both to tell
+when the workload generator has changed and the file is stale.
 
-Usage:  python tests/golden/make_oracle_jk.py 1      (about 1.5 h on 8 cores)
+Usage:  python tests/golden/make_oracle_jk.py 1          (about 2 h on 6 cores)
+        python tests/golden/make_oracle_jk.py 1 --rekey  (rewrite the keys of an existing file)
 """
 from __future__ import annotations
 
@@ -40,15 +44,21 @@ def golden_path(wl: int) -> str:
     return os.path.join(HERE, f"oracle_jk_w{wl}.npz")
 
 
-def input_hash(basis, D, thresh: float) -> str:
-    """SHA-256 over every input the oracle's J/K depend on."""
+def input_hash(basis, thresh: float) -> str:
+    """SHA-256 over the basis and the threshold the oracle's J/K depend on."""
     h = hashlib.sha256()
     for a in (basis.shell_atom, basis.shell_l, basis.shell_nprim, basis.shell_prim_offset):
         h.update(np.ascontiguousarray(a, np.int32).tobytes())
-    for a in (basis.exps, basis.coefs, basis.coords, D):
+    for a in (basis.exps, basis.coefs, basis.coords):
         h.update(np.ascontiguousarray(a, np.float64).tobytes())
     h.update(np.float64(thresh).tobytes())
     return h.hexdigest()
+
+
+def d_fingerprint(D) -> np.ndarray:
+    """Sum, sum of squares and a seeded weighted sum of D (compared to 1e-12)."""
+    w = np.random.default_rng(99).standard_normal(D.shape)
+    return np.array([D.sum(), (D * D).sum(), (D * w).sum()])
 
 
 def upper(M: np.ndarray) -> np.ndarray:
@@ -65,14 +75,30 @@ def from_upper(u: np.ndarray, n: int) -> np.ndarray:
 
 
 def load(wl: int):
-    """(J, K, E_J, E_K, Q, hash) from the stored file, or None if absent."""
+    """(J, K, E_J, E_K, Q, basis hash, D fingerprint) from the stored file, or None if absent."""
     p = golden_path(wl)
     if not os.path.exists(p):
         return None
     z = np.load(p)
     n = int(z["nbf"])
     return (from_upper(z["J_upper"], n), from_upper(z["K_upper"], n), float(z["E_J"]), float(z["E_K"]),
-            z["Q"], str(z["input_sha256"]))
+            z["Q"], str(z["input_sha256"]), z["d_fingerprint"])
+
+
+def matches(wl: int, basis, D) -> bool:
+    """True if the stored file was made for this basis and (to 1e-12) this D."""
+    r = load(wl)
+    return (r is not None and r[5] == input_hash(basis, THRESH)
+            and np.allclose(r[6], d_fingerprint(D), rtol=1e-12, atol=1e-12))
+
+
+def rekey(wl: int) -> None:
+    """Rewrite the keys of an existing file (J, K, energies and Q are kept as the oracle wrote them)."""
+    basis, D = workloads.workload(wl)
+    z = dict(np.load(golden_path(wl)))
+    z["input_sha256"] = np.str_(input_hash(basis, THRESH))
+    z["d_fingerprint"] = d_fingerprint(D)
+    np.savez_compressed(golden_path(wl), **z)
 
 
 def main(wl: int) -> None:
@@ -86,7 +112,7 @@ def main(wl: int) -> None:
     asym = max(float(np.abs(J - J.T).max()), float(np.abs(K - K.T).max()))
     np.savez_compressed(golden_path(wl), nbf=np.int64(basis.nbf), J_upper=upper(J), K_upper=upper(K),
                         E_J=np.float64(ej), E_K=np.float64(ek), Q=Q, thresh=np.float64(THRESH),
-                        input_sha256=np.str_(input_hash(basis, D, THRESH)),
+                        input_sha256=np.str_(input_hash(basis, THRESH)), d_fingerprint=d_fingerprint(D),
                         oracle_seconds=np.float64(dt), oracle_threads=np.int64(oracle.max_threads()),
                         max_asymmetry=np.float64(asym))
     print(f"workload {wl}: nbf {basis.nbf}, E_J {ej:.15e}, E_K {ek:.15e}, {dt:.0f} s on "
@@ -94,4 +120,8 @@ def main(wl: int) -> None:
 
 
 if __name__ == "__main__":
-    main(int(sys.argv[1]) if len(sys.argv) > 1 else 1)
+    wl_ = int(sys.argv[1]) if len(sys.argv) > 1 else 1
+    if "--rekey" in sys.argv:
+        rekey(wl_)
+    else:
+        main(wl_)
