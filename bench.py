@@ -286,6 +286,7 @@ def run_ours(args, rank, world, local_rank):
     ms_mixed, prof = timed(lambda: plan.build_jk(Dd, J, K, precision=eri.ERI_MIXED), args.steps, args.warmup)
     clk = clocks.stop()
     ms_graph, _ = timed(lambda: plan.build_jk_graph(Dd, J, K, precision=eri.ERI_MIXED), args.steps, 2)
+    graph_branches = plan.stats()["graph_branches"]
     ms64, prof64 = timed(lambda: plan.build_jk(Dd, J, K, precision=eri.ERI_FP64), args.fp64_steps, args.fp64_warmup)
 
     # end to end through the public API: pinned host D in, J and K back to pinned host
@@ -370,7 +371,9 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": (f"{world} GPUs: interleaved work tiles per GPU + sum all-reduce of J and K"
                                    if world > 1 else "1 GPU")},
         "graph": {"ms_per_step": ms_graph / args.steps, "value": nq * args.steps / (ms_graph * 1e-3),
-                  "path": "eri_build_jk_graph (one CUDA graph per build, class launches on 4 branches)"},
+                  "branches": graph_branches,
+                  "path": "eri_build_jk_graph (one CUDA graph per build; serial chain or 4 branches, "
+                          "whichever replayed faster at capture)"},
         "fp64": {"ms_per_step": ms64 / args.fp64_steps, "value": nq * args.fp64_steps / (ms64 * 1e-3),
                  "steps": args.fp64_steps, "warmup": args.fp64_warmup},
         "speedup_mixed_vs_fp64": (ms64 / args.fp64_steps) / (ms_mixed / args.steps),
@@ -570,7 +573,11 @@ def run_batch(args, dev, flush):
     import paper_2406_14920_gb300 as eri
     import workloads as W
     mols = W.workload(4)
-    order = sorted(range(len(mols)), key=lambda i: mols[i][0].nbf)[:args.batch_mols]
+    order = sorted(range(len(mols)), key=lambda i: mols[i][0].nbf)
+    if args.batch_select == "spread":  # every 8th molecule by size: keeps the 100-2000 bf spread
+        order = order[::8]
+    elif args.batch_select == "smallest":
+        order = order[:args.batch_mols]
     sel = [mols[i] for i in order]
     plan = eri.Plan([b for b, _ in sel], thresh=THRESH, precision=eri.ERI_MIXED, mixed_tau=args.tau, device=dev.index)
     Dp = plan.pack([torch.from_numpy(D) for _, D in sel]).to(dev)
@@ -594,10 +601,18 @@ def run_batch(args, dev, flush):
             ms += e0.elapsed_time(e1)
         return ms / steps
 
-    ms_b = tm(lambda: plan.build_jk_graph(Dp, J, K), args.batch_steps, 3)
+    ms_b = tm(lambda: plan.build_jk_graph(Dp, J, K), args.batch_steps, 3 if args.batch_select == "smallest" else 1)
     Eb = plan.energy(Dp, J, K).cpu().numpy().reshape(-1, 2)
-    ms_g = tm(lambda: plan.grad(Dp), 1, 1)
+    ms_g = tm(lambda: plan.grad(Dp), 1, 1) if args.batch_select == "smallest" else None
     plan.close()
+    desc = {"smallest": f"the {len(sel)} smallest of the 64 seeded molecules (workload seed 1004)",
+            "spread": f"every 8th of the 64 seeded molecules by size ({len(sel)} molecules, seed 1004)",
+            "all": "all 64 seeded molecules (workload seed 1004)"}[args.batch_select]
+    if args.batch_select == "all":  # per-molecule FP64 builds of the whole set would take ~1000 s
+        return {"molecules": len(sel), "nbf": [b.nbf for b, _ in sel], "quartets_per_step": nq, "sample": desc,
+                "batched_mixed_graph": {"ms_per_step": ms_b, "value": nq / (ms_b * 1e-3), "unit": UNIT,
+                                        "steps": args.batch_steps},
+                "E_per_molecule": Eb.tolist()}
     ms64, ms_mx, errs = 0.0, 0.0, []
     for m, (b, D) in enumerate(sel):
         p = eri.Plan(b, thresh=THRESH, precision=eri.ERI_FP64, device=dev.index)
@@ -609,7 +624,7 @@ def run_batch(args, dev, flush):
         ms_mx += tm(lambda: p.build_jk(Dt, J1, K1, precision=eri.ERI_MIXED), 1, 1)
         p.close()
     return {"molecules": len(sel), "nbf": [b.nbf for b, _ in sel], "quartets_per_step": nq,
-            "sample": f"the {len(sel)} smallest of the 64 seeded molecules (workload seed 1004)",
+            "sample": desc,
             "batched_mixed_graph": {"ms_per_step": ms_b, "value": nq / (ms_b * 1e-3), "unit": UNIT,
                                     "steps": args.batch_steps},
             "batched_gradient_ms": ms_g,
@@ -686,6 +701,8 @@ def main():
     ap.add_argument("--batch-mols", type=int, default=12,
                     help="molecules of the 64-molecule set in the batched leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batch-select", default="smallest", choices=["smallest", "spread", "all"],
+                    help="molecules of the batched leg: the --batch-mols smallest, every 8th by size, or all 64")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the J-engine, long-range, point-charge and gradient legs")
     ap.add_argument("--aux-steps", type=int, default=2, help="timed steps of the J-engine / long-range / V legs")

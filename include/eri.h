@@ -104,6 +104,7 @@ typedef struct {
                                alone (their bound was below mixed_tau, but an exponent sum above 1e3
                                or a primitive prefactor product above 1e18 would overflow FP32) */
   int64_t quartets_k_screened; /* of quartets_k, dropped by the density screen in the last build */
+  int32_t graph_branches;       /* branches of the current graph build (1 serial, 4 forked; 0: none) */
 } eri_stats_t;
 
 /* Fill opts with the defaults listed above.  Host only. */
@@ -178,8 +179,10 @@ int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double* K, double
  * whole build (density scaling, every class launch of every molecule, the
  * symmetrisation) on a stream of the plan and instantiates it; later calls with
  * the same pointers replay it with one cudaGraphLaunch on `stream` (the contents
- * of D may change between calls).  Inside the graph the class launches fork onto
- * four branches, longest first, so independent classes overlap.  New pointers or
+ * of D may change between calls).  The first call captures two graphs, one with
+ * the class launches in a serial chain and one with them forked onto four
+ * branches (least-loaded first, so independent classes overlap), replays each
+ * twice (host waits) and keeps the faster one.  New pointers or
  * precision re-capture (the old graph is released after a wait on `stream`);
  * a list rebuild (another threshold, new coordinates without frozen lists)
  * drops the graph.  Profiling (opts.profile) does not apply to graph builds.

@@ -51,7 +51,8 @@ class StatsT(C.Structure):
     _fields_ = [("nbf", C.c_int32), ("nshell", C.c_int32), ("npair", C.c_int32), ("nsig_pair", C.c_int32),
                 ("quartets_k", C.c_int64), ("quartets_j", C.c_int64), ("prim_quartets_k", C.c_int64),
                 ("quartets_k_fp32", C.c_int64), ("flops_k", C.c_double), ("flops_j", C.c_double),
-                ("device_status", C.c_int32), ("quartets_k_guard", C.c_int64), ("quartets_k_screened", C.c_int64)]
+                ("device_status", C.c_int32), ("quartets_k_guard", C.c_int64), ("quartets_k_screened", C.c_int64),
+                ("graph_branches", C.c_int32)]
 
 
 def lib():

@@ -31,6 +31,7 @@ constexpr int BOYS_NT = 722;         // covers T < 36 + h/2
 constexpr int BOYS_J64 = 8;          // |dT| <= 0.025: truncation ~ dT^8/8! ~ 4e-18 relative
 constexpr int BOYS_J32 = 4;          // dT^4/4! ~ 1.6e-8 relative
 constexpr int BOYS_MMAX = LMAX_QUARTET;  // 13
+static_assert(BOYS_J32 == 4 && BOYS_J64 == 8, "Boys rows are read as one float4 / four double2");
 
 __host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 // number of Hermite triples (t,u,v) with t+u+v <= n
@@ -177,6 +178,9 @@ struct PairData {
   const double* ea;    // exponent of the s1 (higher-l shell) primitive
   const double* E;     // Hermite coefficients per primitive pair: 3 x (l1+1)(l2+1)(l1+l2+1), x then y then z
   const float* Ef;
+  // FP32 shadows packed for vector loads, 3 per primitive pair i:
+  //   q4[3i] = {P, p}, q4[3i+1] = {P-A, pref}, q4[3i+2] = {P-B, 0}
+  const float4* q4;
   int n;               // number of primitive pairs (row stride of the [3][n] arrays)
 };
 
@@ -229,10 +233,16 @@ __device__ __forceinline__ void boys_f64(double T, const BoysTabs& bt, double* F
   if (T < BOYS_TMAX) {
     const int k = __double2int_rn(T * BOYS_INV_H);
     const double d = k * BOYS_H - T;
-    const double* c = bt.c64 + ((size_t)k * (BOYS_MMAX + 1) + M) * BOYS_J64;
-    double f = __ldg(c + BOYS_J64 - 1);
-#pragma unroll
-    for (int j = BOYS_J64 - 2; j >= 0; --j) f = fma(f, d, __ldg(c + j));
+    // the 8 Taylor coefficients of (k, M) are one 64-byte row: four 16-byte loads
+    const double2* c = reinterpret_cast<const double2*>(bt.c64 + ((size_t)k * (BOYS_MMAX + 1) + M) * BOYS_J64);
+    const double2 c01 = __ldg(c), c23 = __ldg(c + 1), c45 = __ldg(c + 2), c67 = __ldg(c + 3);
+    double f = fma(c67.y, d, c67.x);
+    f = fma(f, d, c45.y);
+    f = fma(f, d, c45.x);
+    f = fma(f, d, c23.y);
+    f = fma(f, d, c23.x);
+    f = fma(f, d, c01.y);
+    f = fma(f, d, c01.x);
     F[M] = f;
     if (M > 0) {
       // exp(d), |d| <= h/2, 8 Taylor terms
@@ -264,10 +274,11 @@ __device__ __forceinline__ void boys_f32(float T, const BoysTabs& bt, float* F) 
   if (T < (float)BOYS_TMAX) {
     const int k = __float2int_rn(T * (float)BOYS_INV_H);
     const float d = k * (float)BOYS_H - T;
-    const float* c = bt.c32 + ((size_t)k * (BOYS_MMAX + 1) + M) * BOYS_J32;
-    float f = __ldg(c + BOYS_J32 - 1);
-#pragma unroll
-    for (int j = BOYS_J32 - 2; j >= 0; --j) f = fmaf(f, d, __ldg(c + j));
+    // the 4 Taylor coefficients of (k, M) are one 16-byte row: one load
+    const float4 c = __ldg(reinterpret_cast<const float4*>(bt.c32) + ((size_t)k * (BOYS_MMAX + 1) + M));
+    float f = fmaf(c.w, d, c.z);
+    f = fmaf(f, d, c.y);
+    f = fmaf(f, d, c.x);
     F[M] = f;
     if (M > 0) {
       float g = 1.0f / 24.0f;

@@ -119,15 +119,26 @@ cudaError_t launch_grad_x(int Y, const GradArgs& a, cudaStream_t s, int nsm) {
 template <int LAB, int LCD, typename T>
 cudaError_t launch_j_t(const JArgs& a, cudaStream_t s, int nsm) {
   if (a.wl.total <= 0) return cudaSuccess;
-  using S = JShape<LAB, LCD, T>;
-  constexpr int WPB = 4;
-  static_assert(WPB * S::smem_per_warp() <= 227 * 1024, "J-engine block exceeds 227 KB");
-  LaunchInfo li;
-  auto kern = j_warp_kernel<LAB, LCD, T>;
-  cudaError_t e = launch_persistent(kern, WPB * S::smem_per_warp(), a.wl.total, WPB, nsm, &li);
-  if (e != cudaSuccess) return e;
-  kern<<<li.grid, li.block, li.smem, s>>>(a);
-  return cudaGetLastError();
+  if constexpr (sizeof(T) == 8 && use_j_thread(LAB, LCD)) {
+    auto kern = j_thread_kernel<LAB, LCD>;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, 0);
+    if (e != cudaSuccess) return e;
+    const int64_t need = (a.wl.total + 127) / 128;
+    const int64_t grid = std::min<int64_t>(need, (int64_t)nsm * std::max(occ, 1));
+    kern<<<(int)std::max<int64_t>(1, grid), 128, 0, s>>>(a);
+    return cudaGetLastError();
+  } else {
+    using S = JShape<LAB, LCD, T>;
+    constexpr int WPB = 4;
+    static_assert(WPB * S::smem_per_warp() <= 227 * 1024, "J-engine block exceeds 227 KB");
+    LaunchInfo li;
+    auto kern = j_warp_kernel<LAB, LCD, T>;
+    cudaError_t e = launch_persistent(kern, WPB * S::smem_per_warp(), a.wl.total, WPB, nsm, &li);
+    if (e != cudaSuccess) return e;
+    kern<<<li.grid, li.block, li.smem, s>>>(a);
+    return cudaGetLastError();
+  }
 }
 
 template <int LAB>

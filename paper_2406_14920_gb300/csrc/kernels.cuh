@@ -156,18 +156,26 @@ template <> __device__ __forceinline__ float ldE<float>(const PairData& pd, int 
 template <> __device__ __forceinline__ double pdv<double>(const double* d, const float*, int i) { return __ldg(d + i); }
 template <> __device__ __forceinline__ float pdv<float>(const double*, const float* f, int i) { return __ldg(f + i); }
 
-// Primitive pair scalars in precision T.
+// Primitive pair scalars in precision T (FP32: three 16-byte vector loads of
+// the packed shadows; unused components are dropped by the compiler).
 template <typename T>
 struct Prim {
   T p, P[3], PA[3], PB[3], pref;
   __device__ __forceinline__ void load(const PairData& pd, int i) {
-    p = pdv<T>(pd.p, pd.pf, i);
-    pref = pdv<T>(pd.pref, pd.preff, i);
+    if constexpr (sizeof(T) == 4) {
+      const float4 a = __ldg(pd.q4 + 3 * i), b = __ldg(pd.q4 + 3 * i + 1), c = __ldg(pd.q4 + 3 * i + 2);
+      P[0] = a.x; P[1] = a.y; P[2] = a.z; p = a.w;
+      PA[0] = b.x; PA[1] = b.y; PA[2] = b.z; pref = b.w;
+      PB[0] = c.x; PB[1] = c.y; PB[2] = c.z;
+    } else {
+      p = pdv<T>(pd.p, pd.pf, i);
+      pref = pdv<T>(pd.pref, pd.preff, i);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      P[d] = pdv<T>(pd.P, pd.Pf, d * pd.n + i);
-      PA[d] = pdv<T>(pd.PA, pd.PAf, d * pd.n + i);
-      PB[d] = pdv<T>(pd.PB, pd.PBf, d * pd.n + i);
+      for (int d = 0; d < 3; ++d) {
+        P[d] = pdv<T>(pd.P, pd.Pf, d * pd.n + i);
+        PA[d] = pdv<T>(pd.PA, pd.PAf, d * pd.n + i);
+        PB[d] = pdv<T>(pd.PB, pd.PBf, d * pd.n + i);
+      }
     }
   }
 };
@@ -309,6 +317,113 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
   }
   }
   if (a.counter && lane == 0 && done) {
+    atomicAdd(a.counter, done);
+    atomicAdd(a.counter + 1, doneq);
+    atomicAdd(a.counter + 2, doneb);
+  }
+}
+
+// Which J-engine classes run one ordered item per thread (R, the item's
+// Hermite J and the ket's Hermite density in registers) instead of one per warp.
+__host__ __device__ constexpr bool use_j_thread(int lab, int lcd) {
+  return nherm(lab + lcd) + nherm(lab) + nherm(lcd) <= 130;
+}
+
+// J-engine (Eq. j_formula), one ordered (bra, ket) shell-pair item per lane:
+// for each bra primitive pair, J_P += sum_{ket prims} sum_Q R_{P+Q} D_Q with
+// every Hermite index a compile-time constant.  The lists are bra-major, so a
+// warp's 32 items usually share one bra pair: then J_P is summed over the warp
+// with shuffles and one lane adds it to the bra primitive's Hermite J (one
+// atomic per element instead of 32); otherwise each lane adds its own.
+template <int LAB, int LCD>
+__global__ void __launch_bounds__(128) j_thread_kernel(JArgs a) {
+  constexpr int L = LAB + LCD, NR = nherm(L), HAB = nherm(LAB), HCD = nherm(LCD);
+  using T = double;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = a.wl.total, first = a.wl.first;
+  const int64_t span = 32 * (int64_t)a.wl.tile, ntiles = (total - first + span - 1) / span;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long done = 0, doneq = 0, doneb = 0;
+  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * a.wl.nshard + a.wl.shard;
+       tl < ntiles; tl += nwarps * a.wl.nshard) {
+    const int64_t t0 = first + tl * span, i1 = t0 + span < total ? t0 + span : total;
+    BraCursor cur(a.wl, t0 + lane < i1 ? t0 + lane : t0);
+    for (int64_t base = t0; base < i1; base += 32) {  // uniform over the warp
+      const int64_t item = base + lane;
+      const bool ok = item < i1;
+      int pb_id = -1, npb = 0, offb = 0, hb = 0, npk = 0, offk = 0, hk = 0;
+      if (ok) {
+        const int ik = cur.at(a.wl, item);
+        pb_id = __ldg(a.wl.bra + cur.ib);
+        const int mol = __ldg(a.sp.pmol + pb_id);
+        const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
+        npb = __ldg(a.sp.np + pb_id);
+        offb = __ldg(a.sp.poff + pb_id);
+        hb = __ldg(a.sp.hoff + pb_id);
+        npk = __ldg(a.sp.np + pk_id);
+        offk = __ldg(a.sp.poff + pk_id);
+        hk = __ldg(a.sp.hoff + pk_id);
+        ++done;
+        doneq += (unsigned long long)npb * npk;
+        doneb += npb;
+      }
+      // lane 0's item is always valid here
+      const int pb0 = __shfl_sync(0xffffffffu, pb_id, 0);
+      const bool uni = __all_sync(0xffffffffu, !ok || pb_id == pb0);
+      const int npb_loop = uni ? __shfl_sync(0xffffffffu, npb, 0) : npb;
+      for (int pb = 0; pb < npb_loop; ++pb) {
+        T acc[HAB];
+#pragma unroll
+        for (int x = 0; x < HAB; ++x) acc[x] = T(0);
+        if (ok) {
+          Prim<T> bp;
+          bp.load(a.pd, offb + pb);
+          for (int pk = 0; pk < npk; ++pk) {
+            Prim<T> kp;
+            kp.load(a.pd, offk + pk);
+            const T ps = bp.p + kp.p;
+            T rho = bp.p * kp.p / ps;
+            T pref = bp.pref * kp.pref * rsqrt_t(ps);
+            attenuate(om2<T>(a), rho, pref);
+            const T X = bp.P[0] - kp.P[0], Y = bp.P[1] - kp.P[1], Z = bp.P[2] - kp.P[2];
+            T F[L + 1];
+            Boys<T>::template eval<L>(rho * (X * X + Y * Y + Z * Z), a.bt, F);
+            T R[NR];
+            r_build_reg<L, T>(F, pref, X, Y, Z, T(-2) * rho, R);
+            const double* dq = a.Dherm + hk + (size_t)pk * HCD;
+            T Dq[HCD];
+#pragma unroll
+            for (int q = 0; q < HCD; ++q) Dq[q] = __ldg(dq + q);
+            for_herm<LAB>([&](auto t, auto u, auto v) {
+              constexpr int P = herm_index(ERI_CI(t), ERI_CI(u), ERI_CI(v));
+              T s = acc[P];
+              for_herm<LCD>([&](auto x, auto y, auto z) {
+                s = fma(R[herm_index(ERI_CI(t) + ERI_CI(x), ERI_CI(u) + ERI_CI(y), ERI_CI(v) + ERI_CI(z))],
+                        Dq[herm_index(ERI_CI(x), ERI_CI(y), ERI_CI(z))], s);
+              });
+              acc[P] = s;
+            });
+          }
+        }
+        if (uni) {
+#pragma unroll
+          for (int x = 0; x < HAB; ++x) {
+            T v = acc[x];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            acc[x] = v;
+          }
+          if (lane == 0)
+#pragma unroll
+            for (int x = 0; x < HAB; ++x) acc_add(a.Jherm + hb + (size_t)pb * HAB + x, acc[x], a.det);
+        } else if (ok) {
+#pragma unroll
+          for (int x = 0; x < HAB; ++x) acc_add(a.Jherm + hb + (size_t)pb * HAB + x, acc[x], a.det);
+        }
+      }
+    }
+  }
+  if (a.counter && done) {
     atomicAdd(a.counter, done);
     atomicAdd(a.counter + 1, doneq);
     atomicAdd(a.counter + 2, doneb);

@@ -52,17 +52,15 @@ __host__ __device__ constexpr bool use_thread_kernel(int la, int lb, int lc, int
 // E tables: FP64 loads them (memory is free next to the FP64 pipe), FP32
 // rebuilds them from P-A, P-B and 1/(2p) (cheaper than scattered loads).
 template <int LI, int LJ, typename T>
-__device__ __forceinline__ void load_or_build_e(const PairData& pd, int e0, int prim, T* e /*[3][NE]*/) {
+__device__ __forceinline__ void load_or_build_e(const PairData& pd, int e0, const Prim<T>& pr, T* e /*[3][NE]*/) {
   constexpr int NE = (LI + 1) * (LJ + 1) * (LI + LJ + 1);
   if constexpr (sizeof(T) == 8) {
 #pragma unroll
     for (int x = 0; x < 3 * NE; ++x) e[x] = ldE<T>(pd, e0 + x);
   } else {
-    const T o2p = T(0.5) / pdv<T>(pd.p, pd.pf, prim);
+    const T o2p = T(0.5) / pr.p;
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
-      md_e_1d<LI, LJ, T>(pdv<T>(pd.PA, pd.PAf, d * pd.n + prim), pdv<T>(pd.PB, pd.PBf, d * pd.n + prim), o2p,
-                         e + d * NE);
+    for (int d = 0; d < 3; ++d) md_e_1d<LI, LJ, T>(pr.PA[d], pr.PB[d], o2p, e + d * NE);
   }
 }
 
@@ -89,12 +87,12 @@ __device__ __forceinline__ void eri_block_reg_pq(const KArgs& a, int offb, int n
     Prim<T> bp;
     bp.load(a.pd, offb + pb);
     T eb[3 * S::NEB];
-    load_or_build_e<LA, LB, T>(a.pd, eb0 + pb * 3 * S::NEB, offb + pb, eb);
+    load_or_build_e<LA, LB, T>(a.pd, eb0 + pb * 3 * S::NEB, bp, eb);
     for (int pk = 0; pk < npk; ++pk) {
       Prim<T> kp;
       kp.load(a.pd, offk + pk);
       T ek[3 * S::NEK];
-      load_or_build_e<LC, LD, T>(a.pd, ek0 + pk * 3 * S::NEK, offk + pk, ek);
+      load_or_build_e<LC, LD, T>(a.pd, ek0 + pk * 3 * S::NEK, kp, ek);
       const T ps = bp.p + kp.p;
       T rho = bp.p * kp.p / ps;
       T pref = bp.pref * kp.pref * rsqrt_t(ps);
@@ -152,7 +150,7 @@ __device__ __forceinline__ void eri_block_reg(const KArgs& a, int offb, int npb,
       Prim<T> kp;
       kp.load(a.pd, offk + pk);
       T ek[3 * S::NEK];
-      load_or_build_e<LC, LD, T>(a.pd, ek0 + pk * 3 * S::NEK, offk + pk, ek);
+      load_or_build_e<LC, LD, T>(a.pd, ek0 + pk * 3 * S::NEK, kp, ek);
       const T ps = bp.p + kp.p;
       T rho = bp.p * kp.p / ps;
       T pref = bp.pref * kp.pref * rsqrt_t(ps);
@@ -178,7 +176,7 @@ __device__ __forceinline__ void eri_block_reg(const KArgs& a, int offb, int npb,
       });
     }
     T eb[3 * S::NEB];
-    load_or_build_e<LA, LB, T>(a.pd, eb0 + pb * 3 * S::NEB, offb + pb, eb);
+    load_or_build_e<LA, LB, T>(a.pd, eb0 + pb * 3 * S::NEB, bp, eb);
     sfor<S::NCD>([&](auto icd_) {
       constexpr int icd = ERI_CI(icd_);
       for_cart<LA>([&](auto ix, auto iy, auto iz) {

@@ -77,6 +77,12 @@ struct BShape {
   // for every ket pair cd in registers, the cd loop unrolled at compile time
   static constexpr int NPS = (HAB + 31) / 32;
   static constexpr bool REGW = CH == NCD && (sizeof(T) == 4 ? NCD * NPS <= 64 : (ERI_REGW64 && NCD * NPS <= 32));
+  // step D with compile-time indices: lane owns ket pair cd = lane + 32 j, the
+  // bra pairs ab are a compile-time loop (E broadcast, W row at a per-lane
+  // base), X[ab][cd] stays in registers over the bra primitives.  Worth it when
+  // most lanes own a cd and the X slice fits in registers.
+  static constexpr int NCS = (NCD + 31) / 32;
+  static constexpr bool REGD = CH == NCD && NCD >= 16 && NAB * NCS <= (sizeof(T) == 4 ? 64 : 48);
   static constexpr int SM_BOX = 0, SM_PING = SM_BOX + G * BOX, SM_SC = SM_PING + G * 2 * NPING,
                        SM_EK = SM_SC + G * NSC, SM_EB = SM_EK + G * 3 * NEK, SM_W = SM_EB + 3 * NEB,
                        SM_X = SM_W + CH * HABP, SM_TOTAL = SM_X + NAB * CH;
@@ -208,6 +214,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 0) jk_warp_kernel(JK
     for (int c0 = 0; c0 < NCD; c0 += CH) {
       const int nci = NCD - c0 < CH ? NCD - c0 : CH;
       for (int x = lane; x < NAB * CH; x += 32) Xs[x] = T(0);
+      T xreg[S::REGD ? S::NCS * NAB : 1];
+      if constexpr (S::REGD) {
+#pragma unroll
+        for (int x = 0; x < S::NCS * NAB; ++x) xreg[x] = T(0);
+      }
       for (int pb = 0; pb < npb; ++pb) {
         for (int x = lane; x < 3 * NEB; x += 32) Eb[x] = ldE<T>(a.pd, eb0 + pb * 3 * NEB + x);
         T wreg[S::REGW ? S::NPS * NCD : 1];
@@ -367,7 +378,31 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 0) jk_warp_kernel(JK
             }
           __syncwarp();
         }
-        // step D: bra transform, items (ab, ci)
+        // step D: bra transform
+        if constexpr (S::REGD) {
+          sfor<S::NCS>([&](auto j_) {
+            constexpr int j = ERI_CI(j_);
+            const int cd = lane + 32 * j;
+            if (j * 32 + 32 <= NCD || cd < NCD) {
+              const T* wc = Ws + cd * HABP;
+              for_cart<LA>([&](auto ix, auto iy, auto iz) {
+                for_cart<LB>([&](auto jx, auto jy, auto jz) {
+                  constexpr int IX = ERI_CI(ix), IY = ERI_CI(iy), IZ = ERI_CI(iz);
+                  constexpr int JX = ERI_CI(jx), JY = ERI_CI(jy), JZ = ERI_CI(jz);
+                  constexpr int iab = cidx(LA, IY, IZ) * NB + cidx(LB, JY, JZ);
+                  const T* fx = Eb + (IX * (LB + 1) + JX) * (LAB + 1);
+                  const T* fy = Eb + NEB + (IY * (LB + 1) + JY) * (LAB + 1);
+                  const T* fz = Eb + 2 * NEB + (IZ * (LB + 1) + JZ) * (LAB + 1);
+                  xreg[j * NAB + iab] += tsum<IX + JX, IY + JY, IZ + JZ, false>(
+                      fx, fy, fz, [&](auto tx, auto ty, auto tz) {
+                        return wc[lex_base(LAB, ERI_CI(tx), ERI_CI(ty)) + ERI_CI(tz)];
+                      });
+                });
+              });
+            }
+          });
+        } else {
+        // items (ab, ci)
         for (int it = lane; it < NAB * nci; it += 32) {
           const int iab = it / nci, ci = it - iab * nci;
           const int a0w = tab_ab[2 * iab], a1w = tab_ab[2 * iab + 1];
@@ -389,6 +424,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 0) jk_warp_kernel(JK
           }
           Xs[iab * CH + ci] += acc;
         }
+        }
+        __syncwarp();
+      }
+      if constexpr (S::REGD) {  // X to shared memory for the contraction
+        sfor<S::NCS>([&](auto j_) {
+          constexpr int j = ERI_CI(j_);
+          const int cd = lane + 32 * j;
+          if (j * 32 + 32 <= NCD || cd < NCD) {
+#pragma unroll
+            for (int iab = 0; iab < NAB; ++iab) Xs[iab * CH + cd] = xreg[j * NAB + iab];
+          }
+        });
         __syncwarp();
       }
       // contraction of the chunk; one lane per output element

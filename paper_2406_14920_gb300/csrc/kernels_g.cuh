@@ -17,6 +17,10 @@
 #pragma once
 #include "kernels_b.cuh"
 
+#ifndef ERI_REGG
+#define ERI_REGG 1
+#endif
+
 namespace eri {
 
 struct GradArgs {
@@ -116,6 +120,12 @@ struct GShape {
   // register ket transform (as in the energy kernel) where W fits
   static constexpr int NPS = (HAB1 + 31) / 32;
   static constexpr bool REGW = ERI_REGW64 && CH == NCD && NCD * NPS <= 32;
+  // derivative contraction with compile-time indices: lane owns ket pair
+  // cd = lane + 32 j, the bra pairs ab are an unrolled loop (coefficients
+  // broadcast from shared memory, the W row at a per-lane base, the lane's
+  // density values in registers); worth it when most lanes own a cd
+  static constexpr int NCS = (NCD + 31) / 32;
+  static constexpr bool REGG = ERI_REGG && CH == NCD && NCD >= 16;
   static constexpr int SM_BOX = 0, SM_PING = SM_BOX + G * BOX, SM_SC = SM_PING + G * 2 * NPING,
                        SM_EK = SM_SC + G * NSC, SM_EB = SM_EK + G * 3 * NEK, SM_W = SM_EB + FIXED,
                        SM_TOTAL = SM_W + CH * HAB1P;
@@ -354,7 +364,88 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
             }
           __syncwarp();
         }
-        // bra derivatives and contraction with G, items (ab, ci)
+        // bra derivatives and contraction with G
+        if constexpr (S::REGG) {
+          sfor<S::NCS>([&](auto j_) {
+            constexpr int j = ERI_CI(j_);
+            const int cd = lane + 32 * j;
+            if (j * 32 + 32 <= NCD || cd < NCD) {
+              constexpr int NA = S::NA;
+              const T* wc = Ws + cd * HABP;
+              const int lam = ao3 + cd / ND, sig = ao4 + cd % ND;
+              const T Dls = __ldg(Dp + (size_t)lam * n + sig);
+              T Dml[NA], Dms[NA], Dnl[NB], Dns[NB];
+#pragma unroll
+              for (int x = 0; x < NA; ++x) {
+                Dml[x] = __ldg(Dp + (size_t)(ao1 + x) * n + lam);
+                Dms[x] = __ldg(Dp + (size_t)(ao1 + x) * n + sig);
+              }
+#pragma unroll
+              for (int x = 0; x < NB; ++x) {
+                Dnl[x] = __ldg(Dp + (size_t)(ao2 + x) * n + lam);
+                Dns[x] = __ldg(Dp + (size_t)(ao2 + x) * n + sig);
+              }
+              for_cart<LA>([&](auto ix, auto iy, auto iz) {
+                for_cart<LB>([&](auto jx, auto jy, auto jz) {
+                  constexpr int IX = ERI_CI(ix), IY = ERI_CI(iy), IZ = ERI_CI(iz);
+                  constexpr int JX = ERI_CI(jx), JY = ERI_CI(jy), JZ = ERI_CI(jz);
+                  constexpr int ia = cidx(LA, IY, IZ), ib = cidx(LB, JY, JZ);
+                  constexpr int NX = IX + JX, NY = IY + JY, NZ = IZ + JZ;
+                  const T* ex = Eb + 0 * 3 * NEB + (IX * (LB + 1) + JX) * NTB;
+                  const T* ey = Eb + 1 * 3 * NEB + (IY * (LB + 1) + JY) * NTB;
+                  const T* ez = Eb + 2 * 3 * NEB + (IZ * (LB + 1) + JZ) * NTB;
+                  const T Gv = a.cj * 4.0 * __ldg(Dp + (size_t)(ao1 + ia) * n + ao2 + ib) * Dls -
+                               a.ck * (Dml[ia] * Dns[ib] + Dms[ia] * Dnl[ib]);
+                  auto w = [&](int tx, int ty, int tz) { return wc[lex_base(LAB + 1, tx, ty) + tz]; };
+                  T dAx = T(0), dBx = T(0), dAy = T(0), dBy = T(0), dAz = T(0), dBz = T(0);
+                  sfor<NX + 2>([&](auto tx_) {  // direction x open to NX + 1
+                    constexpr int tx = ERI_CI(tx_);
+                    T sx = T(0);
+                    sfor<NY + 1>([&](auto ty_) {
+                      constexpr int ty = ERI_CI(ty_);
+                      T sz = T(0);
+                      sfor<NZ + 1>([&](auto tz_) { sz = fma(ez[ERI_CI(tz_)], w(tx, ty, ERI_CI(tz_)), sz); });
+                      sx = fma(ey[ty], sz, sx);
+                    });
+                    dAx = fma(ex[NEB + tx], sx, dAx);
+                    dBx = fma(ex[2 * NEB + tx], sx, dBx);
+                  });
+                  sfor<NY + 2>([&](auto ty_) {  // direction y open
+                    constexpr int ty = ERI_CI(ty_);
+                    T sy = T(0);
+                    sfor<NX + 1>([&](auto tx_) {
+                      constexpr int tx = ERI_CI(tx_);
+                      T sz = T(0);
+                      sfor<NZ + 1>([&](auto tz_) { sz = fma(ez[ERI_CI(tz_)], w(tx, ty, ERI_CI(tz_)), sz); });
+                      sy = fma(ex[tx], sz, sy);
+                    });
+                    dAy = fma(ey[NEB + ty], sy, dAy);
+                    dBy = fma(ey[2 * NEB + ty], sy, dBy);
+                  });
+                  sfor<NZ + 2>([&](auto tz_) {  // direction z open
+                    constexpr int tz = ERI_CI(tz_);
+                    T sz = T(0);
+                    sfor<NX + 1>([&](auto tx_) {
+                      constexpr int tx = ERI_CI(tx_);
+                      T sy = T(0);
+                      sfor<NY + 1>([&](auto ty_) { sy = fma(ey[ERI_CI(ty_)], w(tx, ERI_CI(ty_), tz), sy); });
+                      sz = fma(ex[tx], sy, sz);
+                    });
+                    dAz = fma(ez[NEB + tz], sz, dAz);
+                    dBz = fma(ez[2 * NEB + tz], sz, dBz);
+                  });
+                  gA[0] = fma(Gv, dAx, gA[0]);
+                  gA[1] = fma(Gv, dAy, gA[1]);
+                  gA[2] = fma(Gv, dAz, gA[2]);
+                  gB[0] = fma(Gv, dBx, gB[0]);
+                  gB[1] = fma(Gv, dBy, gB[1]);
+                  gB[2] = fma(Gv, dBz, gB[2]);
+                });
+              });
+            }
+          });
+        } else {
+        // items (ab, ci)
         for (int it = lane; it < NAB * nci; it += 32) {
           const int iab = it / nci, ci = it - iab * nci;
           const int cd = c0 + ci;
@@ -408,6 +499,7 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
             gA[d] = fma(Gv, dA[d], gA[d]);
             gB[d] = fma(Gv, dB[d], gB[d]);
           }
+        }
         }
         __syncwarp();
       }

@@ -116,7 +116,7 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
                         const int* __restrict__ sh_po, const double* __restrict__ ex, const double* __restrict__ cn,
                         const double* __restrict__ coords, int nprimpair, double* p_, double* P_, double* PA_,
                         double* PB_, double* pref_, float* pf, float* Pf, float* PAf, float* PBf, float* preff,
-                        float* pmaxp, float* prefmaxp, double* ea_) {
+                        float* pmaxp, float* prefmaxp, double* ea_, float4* q4) {
   int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= npair) return;
   const int a = s1[ip], b = s2[ip];
@@ -139,15 +139,22 @@ __global__ void k_pairs(int npair, const int* __restrict__ s1, const int* __rest
       pref_[o] = pr;
       pf[o] = (float)p;
       preff[o] = (float)pr;
+      float fP[3], fA[3], fB[3];
       for (int d = 0; d < 3; ++d) {
         const double P = (ea * A[d] + eb * Bc[d]) / p;
         P_[d * nprimpair + o] = P;
         PA_[d * nprimpair + o] = P - A[d];
         PB_[d * nprimpair + o] = P - Bc[d];
-        Pf[d * nprimpair + o] = (float)P;
-        PAf[d * nprimpair + o] = (float)(P - A[d]);
-        PBf[d * nprimpair + o] = (float)(P - Bc[d]);
+        fP[d] = (float)P;
+        fA[d] = (float)(P - A[d]);
+        fB[d] = (float)(P - Bc[d]);
+        Pf[d * nprimpair + o] = fP[d];
+        PAf[d * nprimpair + o] = fA[d];
+        PBf[d * nprimpair + o] = fB[d];
       }
+      q4[3 * (size_t)o] = make_float4(fP[0], fP[1], fP[2], (float)p);
+      q4[3 * (size_t)o + 1] = make_float4(fA[0], fA[1], fA[2], (float)pr);
+      q4[3 * (size_t)o + 2] = make_float4(fB[0], fB[1], fB[2], 0.0f);
     }
   pmaxp[ip] = (float)pmx;
   prefmaxp[ip] = (float)fmin(prmx, 1.0e30);
@@ -698,6 +705,7 @@ int eri_plan_impl::alloc_pairs() {
   CK(dalloc(&d_PB, 3 * (size_t)nprimpair)); CK(dalloc(&d_pref, nprimpair));
   CK(dalloc(&d_pf, nprimpair)); CK(dalloc(&d_Pf, 3 * (size_t)nprimpair)); CK(dalloc(&d_PAf, 3 * (size_t)nprimpair));
   CK(dalloc(&d_PBf, 3 * (size_t)nprimpair)); CK(dalloc(&d_preff, nprimpair));
+  CK(dalloc(&d_q4, 3 * (size_t)nprimpair));
   return ERI_OK;
 }
 
@@ -705,7 +713,7 @@ PairData eri_plan_impl::pairdata() const {
   PairData pd;
   pd.p = d_p; pd.P = d_P; pd.PA = d_PA; pd.PB = d_PB; pd.pref = d_pref;
   pd.pf = d_pf; pd.Pf = d_Pf; pd.PAf = d_PAf; pd.PBf = d_PBf; pd.preff = d_preff;
-  pd.E = d_E; pd.Ef = d_Ef; pd.ea = d_ea;
+  pd.E = d_E; pd.Ef = d_Ef; pd.ea = d_ea; pd.q4 = d_q4;
   pd.n = nprimpair;
   return pd;
 }
@@ -742,7 +750,7 @@ MolMats molmats(const eri_plan_impl* P) {
 int eri_plan_impl::geometry(cudaStream_t s, bool rebuild_q) {
   k_pairs<<<grid1(npair, 128), 128, 0, s>>>(npair, d_ps1, d_ps2, d_ppoff, d_sh_atom, d_sh_np, d_sh_po, d_exps, d_cn,
                                         d_coords, nprimpair, d_p, d_P, d_PA, d_PB, d_pref, d_pf, d_Pf, d_PAf, d_PBf,
-                                        d_preff, d_pmaxp, d_prefmaxp, d_ea);
+                                        d_preff, d_pmaxp, d_prefmaxp, d_ea, d_q4);
   CK(cudaGetLastError());
   k_etab<<<grid1(npair, 64), 64, 0, s>>>(npair, d_ps1, d_ps2, d_pnp, d_ppoff, d_peoff, d_sh_l, pairdata(), d_E, d_Ef);
   CK(cudaGetLastError());
@@ -862,7 +870,7 @@ void eri_plan_impl::release() {
                   d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Jh, d_Dherm,
                   d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp, d_ea,
                   d_mat_off, d_mat_n, d_aobase, d_pbase, d_pmol, d_shloc, d_ccm, d_segloc, d_Dpf,
-                  d_nuc_list, d_nuc_goff, d_nuc_dens, d_counters2};
+                  d_nuc_list, d_nuc_goff, d_nuc_dens, d_counters2, d_q4};
   for (auto& e : prof_events) cudaEventDestroy(e);
   prof_events.clear();
   if (gexec) cudaGraphExecDestroy(gexec);
@@ -1360,7 +1368,10 @@ extern "C" int eri_plan_set_coords(eri_plan_t* plan, const double* coords_dev, i
 // launches are spread over the plan's side streams (fork / join by events) in
 // decreasing order of estimated work; otherwise they run in order on s.
 static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, int precision, cudaStream_t s,
-                      bool concurrent) {
+                      int nbranch) {
+  // nbranch = 0: eager build on s (profiling allowed); >= 1: graph capture,
+  // class launches forked onto nbranch branch streams (least-loaded first)
+  const bool concurrent = nbranch > 0;
   const int64_t nn = P->nmat;
   const MolMats mm = molmats(P);
   k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, P->d_Dp, P->d_Dpf);
@@ -1380,7 +1391,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
     ja.det = P->opts.deterministic ? 1 : 0;
     if (concurrent) {
       CK(cudaEventRecord(P->fork_ev, s));
-      for (int b = 0; b < eri_plan_impl::kBranches; ++b) CK(cudaStreamWaitEvent(P->branch[b], P->fork_ev, 0));
+      for (int b = 0; b < nbranch; ++b) CK(cudaStreamWaitEvent(P->branch[b], P->fork_ev, 0));
     }
     CK(cudaMemsetAsync(P->d_counters2, 0, sizeof(unsigned long long) * NPAIRCLASS * NPAIRCLASS * 3, s));
     const bool prof = P->opts.profile && !concurrent;
@@ -1389,7 +1400,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
       for (int Y = 0; Y < NPAIRCLASS; ++Y) {
         ja.wl = P->jlist(X, Y);
         if (ja.wl.total == 0) continue;
-        const cudaStream_t ls = concurrent ? P->branch[nl++ % eri_plan_impl::kBranches] : s;
+        const cudaStream_t ls = concurrent ? P->branch[nl++ % nbranch] : s;
         const int lab = kClassL1[X] + kClassL2[X], lcd = kClassL1[Y] + kClassL2[Y];
         ja.counter = P->d_counters2 + (X * NPAIRCLASS + Y) * 3;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1414,7 +1425,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
         }
       }
     if (concurrent)
-      for (int b = 0; b < eri_plan_impl::kBranches; ++b) {
+      for (int b = 0; b < nbranch; ++b) {
         CK(cudaEventRecord(P->join_ev[b], P->branch[b]));
         CK(cudaStreamWaitEvent(s, P->join_ev[b], 0));
       }
@@ -1468,11 +1479,11 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
       const int rc = P->ensure_tier_bufs(1);
       if (rc != ERI_OK) return rc;
     }
-    if (split && P->tier_nb < (concurrent ? eri_plan_impl::kBranches : 1)) return ERI_EINVAL;
+    if (split && P->tier_nb < (concurrent ? nbranch : 1)) return ERI_EINVAL;
     if (concurrent) {
       std::stable_sort(order.begin(), order.end(), [](const L& a, const L& b) { return a.cost > b.cost; });
       CK(cudaEventRecord(P->fork_ev, s));
-      for (int b = 0; b < eri_plan_impl::kBranches; ++b) CK(cudaStreamWaitEvent(P->branch[b], P->fork_ev, 0));
+      for (int b = 0; b < nbranch; ++b) CK(cudaStreamWaitEvent(P->branch[b], P->fork_ev, 0));
     }
     const bool prof = P->opts.profile && !concurrent;
     auto launch = [&](int X, int Y, int tier, cudaStream_t ls) -> int {
@@ -1496,7 +1507,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
       cudaStream_t ls = s;
       int b = 0;
       if (concurrent) {  // least-loaded branch
-        b = (int)(std::min_element(load, load + eri_plan_impl::kBranches) - load);
+        b = (int)(std::min_element(load, load + nbranch) - load);
         load[b] += l.cost;
         ls = P->branch[b];
       }
@@ -1539,7 +1550,7 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
       ka.nitems = nullptr;
     }
     if (concurrent)
-      for (int b = 0; b < eri_plan_impl::kBranches; ++b) {
+      for (int b = 0; b < nbranch; ++b) {
         CK(cudaEventRecord(P->join_ev[b], P->branch[b]));
         CK(cudaStreamWaitEvent(s, P->join_ev[b], 0));
       }
@@ -1567,7 +1578,7 @@ extern "C" int eri_build_jk(eri_plan_t* plan, const double* D, double* J, double
     int rc = P->build_lists(thresh, s);
     if (rc != ERI_OK) return rc;
   }
-  return build_impl(P, D, J, K, precision, s, false);
+  return build_impl(P, D, J, K, precision, s, 0);
 }
 
 extern "C" int eri_build_jk_graph(eri_plan_t* plan, const double* D, double* J, double* K, int32_t precision,
@@ -1589,24 +1600,58 @@ extern "C" int eri_build_jk_graph(eri_plan_t* plan, const double* D, double* J, 
       CK(cudaGraphExecDestroy(P->gexec));
       P->gexec = nullptr;
     }
-    // capture one build on the plan's own stream, then instantiate
-    CK(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
-    rc = build_impl(P, D, J, K, precision, P->cap_stream, true);
-    cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &g);
-    if (rc == ERI_OK && ce != cudaSuccess) rc = eri_fail(ce);
-    if (rc == ERI_OK) {
-      const cudaError_t ie = cudaGraphInstantiate(&P->gexec, g, 0);
-      if (ie != cudaSuccess) {
-        P->gexec = nullptr;
-        rc = eri_fail(ie);
+    // Capture the build twice: class launches in one serial chain, and forked
+    // over kBranches branches (least-loaded first).  Long launches that fill
+    // the GPU by themselves run best in order; many short ones (batched
+    // plans, small molecules) gain from overlapping.  Each graph is replayed
+    // twice on `stream` (CUDA events) and the faster one is kept.
+    const int cand[2] = {1, eri_plan_impl::kBranches};
+    cudaGraphExec_t ex[2] = {nullptr, nullptr};
+    for (int c = 0; c < 2 && rc == ERI_OK; ++c) {
+      CK(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+      rc = build_impl(P, D, J, K, precision, P->cap_stream, cand[c]);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &g);
+      if (rc == ERI_OK && ce != cudaSuccess) rc = eri_fail(ce);
+      if (rc == ERI_OK) {
+        const cudaError_t ie = cudaGraphInstantiate(&ex[c], g, 0);
+        if (ie != cudaSuccess) {
+          ex[c] = nullptr;
+          rc = eri_fail(ie);
+        }
       }
+      if (g) cudaGraphDestroy(g);
     }
-    if (g) cudaGraphDestroy(g);
+    float best[2] = {0.0f, 0.0f};
+    if (rc == ERI_OK) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      cudaError_t te = cudaEventCreate(&e0);
+      if (te == cudaSuccess) te = cudaEventCreate(&e1);
+      for (int c = 0; c < 2 && te == cudaSuccess; ++c) {
+        best[c] = 3.4e38f;
+        for (int r = 0; r < 2 && te == cudaSuccess; ++r) {
+          float ms = 0.0f;
+          te = cudaEventRecord(e0, s);
+          if (te == cudaSuccess) te = cudaGraphLaunch(ex[c], s);
+          if (te == cudaSuccess) te = cudaEventRecord(e1, s);
+          if (te == cudaSuccess) te = cudaEventSynchronize(e1);
+          if (te == cudaSuccess) te = cudaEventElapsedTime(&ms, e0, e1);
+          if (te == cudaSuccess && ms < best[c]) best[c] = ms;
+        }
+      }
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (te != cudaSuccess) rc = eri_fail(te);
+    }
+    const int keep = best[1] < best[0] ? 1 : 0;
+    for (int c = 0; c < 2; ++c)
+      if (ex[c] && (rc != ERI_OK || c != keep)) cudaGraphExecDestroy(ex[c]);
     if (rc != ERI_OK) {
       cudaGetLastError();
       return rc;
     }
+    P->gexec = ex[keep];
+    P->gbranches = cand[keep];
     P->gkey[0] = D;
     P->gkey[1] = J;
     P->gkey[2] = K;
@@ -1975,6 +2020,7 @@ extern "C" int eri_get_stats(eri_plan_t* plan, eri_stats_t* st) {
     CK(cudaMemcpy(c, P->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
     st->quartets_k_guard = P->last_mixed ? (int64_t)c[NPAIRCLASS * NPAIRCLASS * 6] : 0;
     st->quartets_k_screened = (int64_t)c[NPAIRCLASS * NPAIRCLASS * 6 + 1];
+    st->graph_branches = P->gexec ? P->gbranches : 0;
     double fl = 0.0;
     for (int X = 0; X < NPAIRCLASS; ++X)
       for (int Y = 0; Y <= X; ++Y)

@@ -34,6 +34,7 @@ struct eri_plan_impl {
   // primitive pairs
   double *d_p = nullptr, *d_P = nullptr, *d_PA = nullptr, *d_PB = nullptr, *d_pref = nullptr;
   float *d_pf = nullptr, *d_Pf = nullptr, *d_PAf = nullptr, *d_PBf = nullptr, *d_preff = nullptr;
+  float4* d_q4 = nullptr;  // packed FP32 shadows, 3 float4 per primitive pair (PairData::q4)
   // screening and lists
   float* d_Q = nullptr;
   unsigned int* d_qmax = nullptr;
@@ -80,6 +81,7 @@ struct eri_plan_impl {
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[3] = {};
   int gprec = -1;
+  int gbranches = 0;  // branches of the kept graph (1: serial chain, kBranches: forked)
   int ensure_streams();
   // compacted tier lists of mixed builds (per branch), see ensure_tier_bufs
   int2* tbuf[kBranches] = {};

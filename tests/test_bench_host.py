@@ -31,3 +31,15 @@ def test_class_rows_rates_and_fractions():
     assert abs(rows[0][3] - 0.625) < 1e-9 and abs(rows[0][4] - 0.5) < 1e-9
     # (fp|ps): 1e12 FLOP in 100 ms -> 10 TFLOP/s of 80.5
     assert abs(rows[1][3] - 10.0) < 1e-9 and abs(rows[1][4] - round(10.0 / 80.5, 5)) < 1e-12
+
+
+def test_class_rows_gradient_and_jengine_tiers_use_fp64_peak():
+    """Profile tiers 2 (gradient) and 3 (J-engine) run in FP64: their fraction is
+    taken against the FP64 peak, nominal or the measured one when given."""
+    prof = [{"bra_class": 9, "ket_class": 9, "tier": 2, "ms": 100.0, "flops": 5e10, "launches": 1},
+            {"bra_class": 0, "ket_class": 0, "tier": 3, "ms": 50.0, "flops": 1e10, "launches": 1}]
+    rows = bench.class_rows(prof, steps=1)
+    assert rows[0][:2] == ["(ff|ff)", "grad-fp64"] and rows[1][:2] == ["(ss|ss)", "jengine-fp64"]
+    assert abs(rows[0][3] - 0.5) < 1e-9 and abs(rows[0][4] - 0.4) < 1e-9
+    rows_m = bench.class_rows(prof, steps=1, peaks={0: 1.0, 1: 80.0})
+    assert abs(rows_m[1][4] - 0.2) < 1e-9
