@@ -6,6 +6,14 @@
 #pragma once
 #include "kernels.cuh"
 
+// FP64 register kernel beyond the tiny classes: largest L and footprint (doubles)
+#ifndef ERI_THREAD64_LMAX
+#define ERI_THREAD64_LMAX 3
+#endif
+#ifndef ERI_THREAD64_FOOT
+#define ERI_THREAD64_FOOT 0
+#endif
+
 namespace eri {
 
 struct JKArgs {
@@ -41,7 +49,7 @@ struct AShape {
 __host__ __device__ constexpr bool use_thread_kernel(int la, int lb, int lc, int ld, bool fp32) {
   const int L = la + lb + lc + ld;
   const int nab = ncart(la) * ncart(lb), ncd = ncart(lc) * ncart(ld);
-  if (!fp32) return L <= 3 && nab * ncd <= 27;
+  if (!fp32) return (L <= 3 && nab * ncd <= 27) || (L <= ERI_THREAD64_LMAX && nherm(la + lb) + nab * ncd + nherm(L) <= ERI_THREAD64_FOOT);
   const int hab = nherm(la + lb), nr = nherm(L);
   return L <= 7 && (hab + nab * ncd + nr) <= 460;
 }

@@ -37,6 +37,14 @@
 #ifndef ERI_WARP_SMEM32_MAX_KB
 #define ERI_WARP_SMEM32_MAX_KB 16
 #endif
+// FP32 compile-time bra transform: largest X slice per lane, and the shared
+// memory per warp a class may take to get there
+#ifndef ERI_REGD32_MAX
+#define ERI_REGD32_MAX 64
+#endif
+#ifndef ERI_WARP_SMEM32_FULL_KB
+#define ERI_WARP_SMEM32_FULL_KB 16
+#endif
 // FP64 also takes the lane-owned-P ket transform where W fits in registers
 #ifndef ERI_REGW64
 #define ERI_REGW64 1
@@ -68,7 +76,14 @@ struct BShape {
   static constexpr int NBATCH = (GTARGET + GMAXB - 1) / GMAXB;
   static constexpr int GWANT = (GTARGET + NBATCH - 1) / NBATCH;
   static constexpr int NEED = FIXED + NCD * PER_C + GWANT * PER_G;
-  static constexpr int BUDGET = NEED <= BASE ? BASE : (NEED <= MAXB ? NEED : MAXB);
+  static constexpr int BUDGET0 = NEED <= BASE ? BASE : (NEED <= MAXB ? NEED : MAXB);
+  // FP32 classes with many ket components take a larger budget when that is
+  // what lets the whole ket range sit in one chunk (one ket primitive per
+  // batch), the condition of the compile-time bra transform below
+  static constexpr int NEED_FULL = FIXED + NCD * PER_C + PER_G;
+  static constexpr bool WANT_FULL = sizeof(T) == 4 && NCD >= 16 && NAB * ((NCD + 31) / 32) <= ERI_REGD32_MAX &&
+                                    NEED_FULL <= (ERI_WARP_SMEM32_FULL_KB * 1024) / 4;
+  static constexpr int BUDGET = (WANT_FULL && BUDGET0 < NEED_FULL) ? NEED_FULL : BUDGET0;
   static constexpr int G0 = (BUDGET - FIXED - NCD * PER_C) / PER_G;
   static constexpr int G = G0 >= 1 ? (G0 > 16 ? 16 : G0) : 1;
   static constexpr int CHMAX = (BUDGET - FIXED - G * PER_G) / PER_C;
@@ -82,7 +97,7 @@ struct BShape {
   // base), X[ab][cd] stays in registers over the bra primitives.  Worth it when
   // most lanes own a cd and the X slice fits in registers.
   static constexpr int NCS = (NCD + 31) / 32;
-  static constexpr bool REGD = CH == NCD && NCD >= 16 && NAB * NCS <= (sizeof(T) == 4 ? 64 : 48);
+  static constexpr bool REGD = CH == NCD && NCD >= 16 && NAB * NCS <= (sizeof(T) == 4 ? ERI_REGD32_MAX : 48);
   static constexpr int SM_BOX = 0, SM_PING = SM_BOX + G * BOX, SM_SC = SM_PING + G * 2 * NPING,
                        SM_EK = SM_SC + G * NSC, SM_EB = SM_EK + G * 3 * NEK, SM_W = SM_EB + 3 * NEB,
                        SM_X = SM_W + CH * HABP, SM_TOTAL = SM_X + NAB * CH;
