@@ -427,7 +427,8 @@ def run_gradient_leg(args, dev, peaks):
     import paper_2406_14920_gb300 as eri
     import workloads as W
     basis, D = W.workload(3)
-    plan = eri.Plan(basis, thresh=THRESH, precision=eri.ERI_FP64, device=dev.index, profile=True)
+    plan = eri.Plan(basis, thresh=THRESH, precision=eri.ERI_FP64, mixed_tau=args.tau, device=dev.index,
+                    profile=True)
     stream = torch.cuda.current_stream(dev)
     R = torch.from_numpy(basis.coords).to(dev)
     Dt = torch.from_numpy(D).to(dev)
@@ -453,6 +454,21 @@ def run_gradient_leg(args, dev, peaks):
         gms += sum(r["ms"] for r in g)
         rows = class_rows(g, 1, peaks)
     net = float(Rg.grad.sum(dim=0).abs().max())
+    # the same gradient with the FP32 tier (eri_jk_grad_prec, ERI_MIXED), at the plan's geometry
+    g64 = Rg.grad.detach().clone()
+    plan.grad(Dt, precision=eri.ERI_MIXED)
+    torch.cuda.synchronize()
+    plan.profile()
+    e0, e1, _ = _events(stream)
+    e0.record(stream)
+    gm = plan.grad(Dt, precision=eri.ERI_MIXED)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_mixed = e0.elapsed_time(e1)
+    pm = plan.profile()
+    mixed_tiers = {"fp64_ms": sum(r["ms"] for r in pm if r["tier"] == 2),
+                   "fp32_ms": sum(r["ms"] for r in pm if r["tier"] == 4)}
+    dmix = float((gm - g64).abs().max())
     plan.close()
     n = len(bwd)
     tf = fl / (gms * 1e-3) / 1e12 if gms > 0 else 0.0
@@ -461,6 +477,8 @@ def run_gradient_leg(args, dev, peaks):
             "backward_over_forward": (sum(bwd) / n) / (sum(fwd) / n),
             "gradient_tflops": round(tf, 4), "frac_fp64_nominal": round(tf / PEAK_TFLOPS[0], 4),
             "frac_fp64_measured": round(tf / peaks[0], 4), "max_abs_net_force": net,
+            "mixed": {"ms": ms_mixed, "tau": args.tau, "max_abs_diff_vs_fp64": dmix,
+                      "speedup_vs_fp64_backward": (sum(bwd) / n) / ms_mixed, "tier_ms": mixed_tiers},
             "class_roofline": {"columns": ["class", "tier", "ms_per_step", "tflops", "frac_of_measured_peak"],
                                "rows": rows[:24]}}
 

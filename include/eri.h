@@ -265,6 +265,17 @@ int eri_energy(eri_plan_t* plan, const double* D, const double* J, const double*
 int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int32_t want_j, int32_t want_k, void* stream);
 
 /*
+ * eri_jk_grad with a precision: ERI_FP64 is eri_jk_grad; ERI_MIXED splits the
+ * ordered items on the device with the energy's tier test (Q_ab Q_cd max|D'|
+ * below the plan's mixed_tau and the FP32 range guard passed: FP32, else FP64)
+ * and evaluates the FP32 tier's derivative integrals and their contraction
+ * with D in FP32, adding each item's sums to the FP64 gradient.  Uses the
+ * plan's tier lists (allocated by the first mixed build or gradient).
+ */
+int eri_jk_grad_prec(eri_plan_t* plan, const double* D, double* dEdR, int32_t want_j, int32_t want_k,
+                     int32_t precision, void* stream);
+
+/*
  * Copy the plan's lists to HOST buffers for inspection (each may be NULL):
  *   Q      float32 [npair]        Schwarz bound per shell pair, pair index a(a+1)/2+b (a >= b)
  *                                 (batched: molecule after molecule, local shell indices)
@@ -282,8 +293,8 @@ int eri_get_lists(eri_plan_t* plan, float* Q, int32_t* sig, int32_t* counts, int
 /* One class launch of the J/K build, as seen by eri_get_profile. */
 typedef struct {
   int32_t bra_class, ket_class; /* pair classes 0..9 = ss ps pp ds dp dd fs fp fd ff */
-  int32_t tier;                 /* 0 = FP64 J/K, 1 = FP32 J/K (mixed precision), 2 = gradient (FP64,
-                                   eri_jk_grad), 3 = J-engine (FP64, J-only builds) */
+  int32_t tier;                 /* 0 = FP64 J/K, 1 = FP32 J/K (mixed precision), 2 = gradient FP64,
+                                   3 = J-engine (FP64, J-only builds), 4 = gradient FP32 tier */
   int32_t launches;             /* profiled launches summed into ms */
   double ms;                    /* total device time of those launches (CUDA events on the build stream) */
   int64_t quartets;             /* canonical shell quartets of the last build's launch */

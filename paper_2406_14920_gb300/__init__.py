@@ -79,6 +79,7 @@ def lib():
         L.eri_set_tiles.argtypes = [vp, C.POINTER(C.c_int32)]
         L.eri_energy.argtypes = [vp, vp, vp, vp, vp, vp]
         L.eri_jk_grad.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.eri_jk_grad_prec.argtypes = [vp, vp, vp, i32, i32, i32, vp]
         L.eri_get_lists.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.eri_get_stats.argtypes = [vp, C.POINTER(StatsT)]
@@ -331,14 +332,15 @@ class Plan:
         if not freeze_lists:
             self.list_version += 1
 
-    def grad(self, D, out=None, want_j=True, want_k=True, stream=None):
+    def grad(self, D, out=None, want_j=True, want_k=True, precision=ERI_FP64, stream=None):
+        """dE/dR (natom x 3): eri_jk_grad, or eri_jk_grad_prec for ERI_MIXED."""
         import torch
         if out is None:
             out = torch.empty((self.natom, 3), dtype=torch.float64, device=D.device)
         _require(D, self.nmat, "D", self.device)
         _require(out, 3 * self.natom, "out", self.device)
-        _check(lib().eri_jk_grad(self.h, _ptr(D), _ptr(out), int(want_j), int(want_k), _stream_ptr(stream)),
-               "eri_jk_grad")
+        _check(lib().eri_jk_grad_prec(self.h, _ptr(D), _ptr(out), int(want_j), int(want_k), int(precision),
+                                      _stream_ptr(stream)), "eri_jk_grad_prec")
         return out
 
     def nuclear(self, q, xyz, V=None, stream=None):

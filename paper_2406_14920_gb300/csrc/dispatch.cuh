@@ -84,36 +84,29 @@ cudaError_t launch_jk_unit(int y, const JKArgs& a, cudaStream_t s, int nsm) {
   }
 }
 
-template <int X, int Y>
-cudaError_t launch_grad_xy(const GradArgs& a, cudaStream_t s, int nsm) {
-  if (a.wl.total <= 0) return cudaSuccess;
-  constexpr int LA = ClassL<X>::l1, LB = ClassL<X>::l2, LC = ClassL<Y>::l1, LD = ClassL<Y>::l2;
-  using S = GShape<LA, LB, LC, LD>;
-  constexpr int WPB = 4;
-  static_assert(S::table_bytes() + WPB * S::smem_per_warp() <= 227 * 1024, "gradient block exceeds 227 KB");
-  LaunchInfo li;
-  auto kern = grad_warp_kernel<LA, LB, LC, LD>;
-  cudaError_t e = launch_persistent(kern, S::table_bytes() + WPB * S::smem_per_warp(), a.wl.total, WPB, nsm, &li);
-  if (e != cudaSuccess) return e;
-  kern<<<li.grid, li.block, li.smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <int X>
-cudaError_t launch_grad_x(int Y, const GradArgs& a, cudaStream_t s, int nsm) {
-  switch (Y) {
-    case 0: return launch_grad_xy<X, 0>(a, s, nsm);
-    case 1: return launch_grad_xy<X, 1>(a, s, nsm);
-    case 2: return launch_grad_xy<X, 2>(a, s, nsm);
-    case 3: return launch_grad_xy<X, 3>(a, s, nsm);
-    case 4: return launch_grad_xy<X, 4>(a, s, nsm);
-    case 5: return launch_grad_xy<X, 5>(a, s, nsm);
-    case 6: return launch_grad_xy<X, 6>(a, s, nsm);
-    case 7: return launch_grad_xy<X, 7>(a, s, nsm);
-    case 8: return launch_grad_xy<X, 8>(a, s, nsm);
-    case 9: return launch_grad_xy<X, 9>(a, s, nsm);
+// Gradient launch of class pair (X, y) in precision P, y in 0..9 (compile-time
+// chain; one compilation unit per (X, P), see units.h)
+template <int X, int P, int Y = 0>
+cudaError_t launch_grad_unit(int y, const GradArgs& a, cudaStream_t s, int nsm) {
+  if constexpr (Y >= NPAIRCLASS) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (y == Y) {
+      if (a.wl.total <= 0) return cudaSuccess;
+      constexpr int LA = ClassL<X>::l1, LB = ClassL<X>::l2, LC = ClassL<Y>::l1, LD = ClassL<Y>::l2;
+      using T = std::conditional_t<P == 1, float, double>;
+      using S = GShape<LA, LB, LC, LD, T>;
+      constexpr int WPB = 4;
+      static_assert(S::table_bytes() + WPB * S::smem_per_warp() <= 227 * 1024, "gradient block exceeds 227 KB");
+      LaunchInfo li;
+      auto kern = grad_warp_kernel<LA, LB, LC, LD, T>;
+      cudaError_t e = launch_persistent(kern, S::table_bytes() + WPB * S::smem_per_warp(), a.wl.total, WPB, nsm, &li);
+      if (e != cudaSuccess) return e;
+      kern<<<li.grid, li.block, li.smem, s>>>(a);
+      return cudaGetLastError();
+    }
+    return launch_grad_unit<X, P, Y + 1>(y, a, s, nsm);
   }
-  return cudaErrorInvalidValue;
 }
 
 template <int LAB, int LCD, typename T>
@@ -164,16 +157,9 @@ cudaError_t launch_j_lab(int LCD, int prec, const JArgs& a, cudaStream_t s, int 
   extern template cudaError_t launch_jk_unit<X, P, YLO, YHI>(int, const JKArgs&, cudaStream_t, int);
 ERI_JK_UNITS(ERI_JK_UNIT_DECL)
 #undef ERI_JK_UNIT_DECL
-cudaError_t launch_grad_bra0(int, const GradArgs&, cudaStream_t, int);
-cudaError_t launch_grad_bra1(int, const GradArgs&, cudaStream_t, int);
-cudaError_t launch_grad_bra2(int, const GradArgs&, cudaStream_t, int);
-cudaError_t launch_grad_bra3(int, const GradArgs&, cudaStream_t, int);
-cudaError_t launch_grad_bra4(int, const GradArgs&, cudaStream_t, int);
-cudaError_t launch_grad_bra5(int, const GradArgs&, cudaStream_t, int);
-cudaError_t launch_grad_bra6(int, const GradArgs&, cudaStream_t, int);
-cudaError_t launch_grad_bra7(int, const GradArgs&, cudaStream_t, int);
-cudaError_t launch_grad_bra8(int, const GradArgs&, cudaStream_t, int);
-cudaError_t launch_grad_bra9(int, const GradArgs&, cudaStream_t, int);
+#define ERI_GRAD_UNIT_DECL(X, P) extern template cudaError_t launch_grad_unit<X, P, 0>(int, const GradArgs&, cudaStream_t, int);
+ERI_GRAD_UNITS(ERI_GRAD_UNIT_DECL)
+#undef ERI_GRAD_UNIT_DECL
 cudaError_t launch_j_lab0(int, int, const JArgs&, cudaStream_t, int);
 cudaError_t launch_j_lab1(int, int, const JArgs&, cudaStream_t, int);
 cudaError_t launch_j_lab2(int, int, const JArgs&, cudaStream_t, int);

@@ -6,12 +6,16 @@
 #pragma once
 #include "kernels.cuh"
 
-// FP64 register kernel beyond the tiny classes: largest L and footprint (doubles)
+// FP64 register kernel beyond the tiny classes: largest L and footprint
+// (doubles).  GB300 issues about 3.4 FP64 FMAs per clock per SM, so every warp
+// instruction with idle lanes is expensive; one quartet per lane keeps all 32
+// lanes busy (measured: (pp|pp) 31 -> 9.8 ms, (ds|pp) 16 -> 5.1 ms, (fp|ps)
+// 12 -> 4.9 ms on workload 1).
 #ifndef ERI_THREAD64_LMAX
-#define ERI_THREAD64_LMAX 3
+#define ERI_THREAD64_LMAX 5
 #endif
 #ifndef ERI_THREAD64_FOOT
-#define ERI_THREAD64_FOOT 0
+#define ERI_THREAD64_FOOT 200
 #endif
 
 namespace eri {
@@ -38,8 +42,8 @@ struct AShape {
 };
 
 // Which classes run one quartet per thread (registers) rather than one per warp.
-// FP64: the tiny classes only (the warp kernel keeps the FP64 pipe busier for the
-// rest).  FP32: every class of L <= 7 whose per-primitive-quartet register
+// FP64: classes with L <= 5 whose per-primitive-quartet footprint is at most
+// 200 doubles.  FP32: every class of L <= 7 whose per-primitive-quartet register
 // footprint is at most 460 values.  Measured on GB300 (workload 1, FP32 tier):
 // the register kernel runs these classes 2.2x to 9.6x faster than the
 // shared-memory warp kernel even where ptxas spills up to ~6 KB per thread

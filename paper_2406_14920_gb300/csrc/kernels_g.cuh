@@ -13,7 +13,9 @@
 // base E^{00,(1)}_0 = 2a (P-A)_tau (the exp(-ab/p |AB|^2) factor of E^{00}_0
 // lives in the pair prefactor).  Hermite indices run one higher than for the
 // energy, so R goes to L+1 (the paper raises one bra angular momentum, SI Sec. 2).
-// One warp per item, FP64 throughout.
+// One warp per item, in FP64 or (mixed precision: quartets whose density-
+// weighted bound is below tau, split on the device as for the energy) in FP32
+// with the per-item sums added to the FP64 gradient.
 #pragma once
 #include "kernels_b.cuh"
 
@@ -30,34 +32,39 @@ struct GradArgs {
   BoysTabs bt;
   const RStep* rsteps;
   const double* Dp;
+  const float* Dpf;    // D' in FP32 for the FP32 tier
   const double* ea;    // exponent of the s1 primitive of each primitive pair
   const int* sh_atom;
   double* grad;        // natom * 3 (all molecules' atoms)
   double cj, ck;       // weights of the Coulomb and exchange parts (1 or 0)
   double omega2;       // erf(omega r)/r: omega^2 (0 = Coulomb)
+  float omega2f;
   int det;             // 1: fixed-point gradient accumulator (deterministic builds)
   unsigned long long* counter;  // items, primitive quartets, bra primitives of this launch (may be null)
+  // mixed precision: this tier's compacted list (bra position, ket position) written
+  // by the tier split, *nitems of them; null: items are positions in wl
+  const int2* items;
+  const unsigned int* nitems;
 };
 
 // E^{ij}_t and E^{ij,(1)}_t for one direction, i <= LI, j <= LJ, t <= i+j,
 // stored with row length LI+LJ+2 (t = i+j+1 left zero).
-template <int LI, int LJ>
-__device__ __forceinline__ void md_e_deriv_1d(double PA, double PB, double o2p, double aop, double bop, double a2,
-                                              double* E, double* E1) {
+template <int LI, int LJ, typename T>
+__device__ __forceinline__ void md_e_deriv_1d(T PA, T PB, T o2p, T aop, T bop, T a2, T* E, T* E1) {
   constexpr int NT = LI + LJ + 2;
   for (int x = 0; x < (LI + 1) * (LJ + 1) * NT; ++x) {
-    E[x] = 0.0;
-    E1[x] = 0.0;
+    E[x] = T(0);
+    E1[x] = T(0);
   }
-  E[0] = 1.0;
+  E[0] = T(1);
   E1[0] = a2 * PA;  // 2a (P-A)
   for (int i = 0; i < LI; ++i) {
-    const double* s0 = E + (i * (LJ + 1)) * NT;
-    const double* s1 = E1 + (i * (LJ + 1)) * NT;
-    double* d0 = E + ((i + 1) * (LJ + 1)) * NT;
-    double* d1 = E1 + ((i + 1) * (LJ + 1)) * NT;
+    const T* s0 = E + (i * (LJ + 1)) * NT;
+    const T* s1 = E1 + (i * (LJ + 1)) * NT;
+    T* d0 = E + ((i + 1) * (LJ + 1)) * NT;
+    T* d1 = E1 + ((i + 1) * (LJ + 1)) * NT;
     for (int t = 0; t <= i + 1; ++t) {
-      double v = PA * s0[t], w = PA * s1[t] - bop * s0[t];
+      T v = PA * s0[t], w = PA * s1[t] - bop * s0[t];
       if (t > 0) {
         v += o2p * s0[t - 1];
         w += o2p * s1[t - 1];
@@ -72,12 +79,12 @@ __device__ __forceinline__ void md_e_deriv_1d(double PA, double PB, double o2p, 
   }
   for (int i = 0; i <= LI; ++i)
     for (int j = 0; j < LJ; ++j) {
-      const double* s0 = E + (i * (LJ + 1) + j) * NT;
-      const double* s1 = E1 + (i * (LJ + 1) + j) * NT;
-      double* d0 = E + (i * (LJ + 1) + j + 1) * NT;
-      double* d1 = E1 + (i * (LJ + 1) + j + 1) * NT;
+      const T* s0 = E + (i * (LJ + 1) + j) * NT;
+      const T* s1 = E1 + (i * (LJ + 1) + j) * NT;
+      T* d0 = E + (i * (LJ + 1) + j + 1) * NT;
+      T* d1 = E1 + (i * (LJ + 1) + j + 1) * NT;
       for (int t = 0; t <= i + j + 1; ++t) {
-        double v = PB * s0[t], w = PB * s1[t] + aop * s0[t];
+        T v = PB * s0[t], w = PB * s1[t] + aop * s0[t];
         if (t > 0) {
           v += o2p * s0[t - 1];
           w += o2p * s1[t - 1];
@@ -92,7 +99,7 @@ __device__ __forceinline__ void md_e_deriv_1d(double PA, double PB, double o2p, 
     }
 }
 
-template <int LA, int LB, int LC, int LD>
+template <int LA, int LB, int LC, int LD, typename T = double>
 struct GShape {
   static constexpr int LAB = LA + LB, LCD = LC + LD, L1 = LAB + LCD + 1;
   static constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
@@ -105,7 +112,8 @@ struct GShape {
   static constexpr int PER_G = BOX + 2 * NPING + NSC + 3 * NEK;
   static constexpr int PER_C = HAB1P;
   // ket-primitive batch sized as for the energy kernel (BShape)
-  static constexpr int BASE = (ERI_WARP_SMEM64_KB * 1024) / 8, MAXB = (ERI_WARP_SMEM64_MAX_KB * 1024) / 8;
+  static constexpr int BASE = sizeof(T) == 8 ? (ERI_WARP_SMEM64_KB * 1024) / 8 : (ERI_WARP_SMEM32_KB * 1024) / 4;
+  static constexpr int MAXB = sizeof(T) == 8 ? (ERI_WARP_SMEM64_MAX_KB * 1024) / 8 : (ERI_WARP_SMEM32_MAX_KB * 1024) / 4;
   static constexpr int GTARGET = (LC <= 1 && LD <= 1) ? 9 : 3;
   static constexpr int fit_g(int budget) { return (budget - FIXED - NCD * PER_C) / PER_G; }
   static constexpr int GMAXB = fit_g(MAXB) < 1 ? 1 : fit_g(MAXB);
@@ -119,7 +127,7 @@ struct GShape {
   static constexpr int CH = CHMAX >= NCD ? NCD : (CHMAX < 1 ? 1 : CHMAX);
   // register ket transform (as in the energy kernel) where W fits
   static constexpr int NPS = (HAB1 + 31) / 32;
-  static constexpr bool REGW = ERI_REGW64 && CH == NCD && NCD * NPS <= 32;
+  static constexpr bool REGW = CH == NCD && (sizeof(T) == 4 ? NCD * NPS <= 64 : (ERI_REGW64 && NCD * NPS <= 32));
   // derivative contraction with compile-time indices: lane owns ket pair
   // cd = lane + 32 j, the bra pairs ab are an unrolled loop (coefficients
   // broadcast from shared memory, the W row at a per-lane base, the lane's
@@ -129,17 +137,16 @@ struct GShape {
   static constexpr int SM_BOX = 0, SM_PING = SM_BOX + G * BOX, SM_SC = SM_PING + G * 2 * NPING,
                        SM_EK = SM_SC + G * NSC, SM_EB = SM_EK + G * 3 * NEK, SM_W = SM_EB + FIXED,
                        SM_TOTAL = SM_W + CH * HAB1P;
-  __host__ __device__ static constexpr size_t smem_per_warp() { return sizeof(double) * SM_TOTAL; }
+  __host__ __device__ static constexpr size_t smem_per_warp() { return sizeof(T) * SM_TOTAL; }
   static constexpr int LEXB = (LAB + 2) * (LAB + 2);
   static constexpr int TAB_INTS = 2 * NCD + 2 * NAB + HAB1 + LEXB;
   static constexpr int TABLE_BYTES = ((4 * TAB_INTS + 15) / 16) * 16;
   __host__ __device__ static constexpr size_t table_bytes() { return TABLE_BYTES; }
 };
 
-template <int LA, int LB, int LC, int LD>
-__global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
-  using S = GShape<LA, LB, LC, LD>;
-  using T = double;
+template <int LA, int LB, int LC, int LD, typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 0) grad_warp_kernel(GradArgs a) {
+  using S = GShape<LA, LB, LC, LD, T>;
   constexpr int LAB = S::LAB, LCD = S::LCD, L = S::L1, B = S::B, BOX = S::BOX, NSC = S::NSC;
   constexpr int NB = S::NB, ND = S::ND, NAB = S::NAB, NCD = S::NCD, HAB = S::HAB1, HABP = S::HAB1P, CH = S::CH,
                 G = S::G, NEB = S::NEB, NEK = S::NEK, NPING = S::NPING, NTB = S::NTB;
@@ -184,16 +191,28 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
   T* Eb = sm + S::SM_EB;  // [d][E | GA | GB][NEB]
   T* Ws = sm + S::SM_W;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t total = a.wl.total;
+  // items: positions in the ordered list, or (mixed precision) this tier's compacted list
+  const bool compact = a.items != nullptr;
+  const int64_t total = compact ? (int64_t)__ldg(a.nitems) : a.wl.total;
+  const int64_t first = compact ? 0 : a.wl.first;
+  const int nshard = compact ? 1 : a.wl.nshard, shard = compact ? 0 : a.wl.shard;
   unsigned long long done = 0, doneq = 0, doneb = 0;
-  const int64_t tile = a.wl.tile, ntiles = (total - a.wl.first + tile - 1) / tile;
-  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * a.wl.nshard + a.wl.shard; tl < ntiles;
-       tl += nwarps * a.wl.nshard) {
-  const int64_t i0 = a.wl.first + tl * tile, i1 = i0 + tile < total ? i0 + tile : total;
-  BraCursor cur(a.wl, i0);
+  const int64_t tile = a.wl.tile, ntiles = (total - first + tile - 1) / tile;
+  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * nshard + shard; tl < ntiles;
+       tl += nwarps * nshard) {
+  const int64_t i0 = first + tl * tile, i1 = i0 + tile < total ? i0 + tile : total;
+  BraCursor cur;
+  if (!compact) cur.seek(a.wl, i0);
   for (int64_t item = i0; item < i1; ++item) {
-    const int ik = cur.at(a.wl, item);
-    const int ib = cur.ib;
+    int ik, ib;
+    if (compact) {
+      const int2 v = __ldg(a.items + item);
+      ib = v.x;
+      ik = v.y;
+    } else {
+      ik = cur.at(a.wl, item);
+      ib = cur.ib;
+    }
     const int pb_id = __ldg(a.wl.bra + ib);
     const int mol = __ldg(a.sp.pmol + pb_id);
     const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
@@ -210,22 +229,24 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
     if (s1 == s2) w *= T(0.5);
     if (s3 == s4) w *= T(0.5);
     const int n = __ldg(a.sp.mat_n + mol);
-    const double* Dp = a.Dp + __ldg(a.sp.mat_off + mol);
-    T gA[3] = {0.0, 0.0, 0.0}, gB[3] = {0.0, 0.0, 0.0};
+    const T* Dp = (sizeof(T) == 8 ? reinterpret_cast<const T*>(a.Dp) : reinterpret_cast<const T*>(a.Dpf)) +
+                  __ldg(a.sp.mat_off + mol);
+    T gA[3] = {T(0), T(0), T(0)}, gB[3] = {T(0), T(0), T(0)};
 
     for (int c0 = 0; c0 < NCD; c0 += CH) {
       const int nci = NCD - c0 < CH ? NCD - c0 : CH;
       for (int pb = 0; pb < npb; ++pb) {
         const int ipb = offb + pb;
-        const T bp_p = __ldg(a.pd.p + ipb), bp_pref = __ldg(a.pd.pref + ipb);
+        const T bp_p = pdv<T>(a.pd.p, a.pd.pf, ipb), bp_pref = pdv<T>(a.pd.pref, a.pd.preff, ipb);
         if (lane < 3) {
-          const T aa = __ldg(a.ea + ipb);
+          const T aa = (T)__ldg(a.ea + ipb);
           const T aop = aa / bp_p, bop = T(1) - aop;
           T* e = Eb + lane * 3 * NEB;
           T* ga = e + NEB;
           T* gb = e + 2 * NEB;
-          md_e_deriv_1d<LA, LB>(__ldg(a.pd.PA + lane * a.pd.n + ipb), __ldg(a.pd.PB + lane * a.pd.n + ipb),
-                                T(0.5) / bp_p, aop, bop, T(2) * aa, e, ga);
+          md_e_deriv_1d<LA, LB, T>(pdv<T>(a.pd.PA, a.pd.PAf, lane * a.pd.n + ipb),
+                                   pdv<T>(a.pd.PB, a.pd.PBf, lane * a.pd.n + ipb), T(0.5) / bp_p, aop, bop,
+                                   T(2) * aa, e, ga);
           // ga currently holds E^(1); form GA, GB in place (t from high to low)
           for (int r = 0; r < (LA + 1) * (LB + 1); ++r) {
             T* er = e + r * NTB;
@@ -246,25 +267,27 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
         } else {
           for (int x = lane; x < CH * HABP; x += 32) Ws[x] = T(0);
         }
-        const T bPx = __ldg(a.pd.P + ipb), bPy = __ldg(a.pd.P + a.pd.n + ipb), bPz = __ldg(a.pd.P + 2 * a.pd.n + ipb);
+        const T bPx = pdv<T>(a.pd.P, a.pd.Pf, ipb), bPy = pdv<T>(a.pd.P, a.pd.Pf, a.pd.n + ipb),
+                bPz = pdv<T>(a.pd.P, a.pd.Pf, 2 * a.pd.n + ipb);
         for (int k0 = 0; k0 < npk; k0 += G) {
           const int ng = npk - k0 < G ? npk - k0 : G;
           for (int x = lane; x < ng * 3 * NEK; x += 32) {
             const int g = x / (3 * NEK), r = x - g * 3 * NEK;
-            const T v = __ldg(a.pd.E + ek0 + (k0 + g) * 3 * NEK + r);
+            const T v = ldE<T>(a.pd, ek0 + (k0 + g) * 3 * NEK + r);
             Ek[x] = ((r % (LCD + 1)) & 1) ? -v : v;
           }
           if (lane < ng) {
             const int ipk = offk + k0 + lane;
-            const T kp = __ldg(a.pd.p + ipk);
+            const T kp = pdv<T>(a.pd.p, a.pd.pf, ipk);
             const T ps = bp_p + kp;
             T rho = bp_p * kp / ps;
-            T pref = bp_pref * __ldg(a.pd.pref + ipk) * rsqrt(ps);
-            attenuate(a.omega2, rho, pref);  // s depends on exponents only: the derivative rules hold as they are
-            const T X = bPx - __ldg(a.pd.P + ipk), Y = bPy - __ldg(a.pd.P + a.pd.n + ipk),
-                    Z = bPz - __ldg(a.pd.P + 2 * a.pd.n + ipk);
+            T pref = bp_pref * pdv<T>(a.pd.pref, a.pd.preff, ipk) * rsqrt_t(ps);
+            // s depends on exponents only: the derivative rules hold as they are
+            attenuate(sizeof(T) == 8 ? T(a.omega2) : T(a.omega2f), rho, pref);
+            const T X = bPx - pdv<T>(a.pd.P, a.pd.Pf, ipk), Y = bPy - pdv<T>(a.pd.P, a.pd.Pf, a.pd.n + ipk),
+                    Z = bPz - pdv<T>(a.pd.P, a.pd.Pf, 2 * a.pd.n + ipk);
             T F[L + 1];
-            boys_f64<L>(rho * (X * X + Y * Y + Z * Z), a.bt, F);
+            Boys<T>::template eval<L>(rho * (X * X + Y * Y + Z * Z), a.bt, F);
             T* sc = scal + lane * NSC;
 #pragma unroll
             for (int m = 0; m <= L; ++m) sc[m] = pref * F[m];
@@ -394,8 +417,8 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
                   const T* ex = Eb + 0 * 3 * NEB + (IX * (LB + 1) + JX) * NTB;
                   const T* ey = Eb + 1 * 3 * NEB + (IY * (LB + 1) + JY) * NTB;
                   const T* ez = Eb + 2 * 3 * NEB + (IZ * (LB + 1) + JZ) * NTB;
-                  const T Gv = a.cj * 4.0 * __ldg(Dp + (size_t)(ao1 + ia) * n + ao2 + ib) * Dls -
-                               a.ck * (Dml[ia] * Dns[ib] + Dms[ia] * Dnl[ib]);
+                  const T Gv = T(4.0 * a.cj) * __ldg(Dp + (size_t)(ao1 + ia) * n + ao2 + ib) * Dls -
+                               T(a.ck) * (Dml[ia] * Dns[ib] + Dms[ia] * Dnl[ib]);
                   auto w = [&](int tx, int ty, int tz) { return wc[lex_base(LAB + 1, tx, ty) + tz]; };
                   T dAx = T(0), dBx = T(0), dAy = T(0), dBy = T(0), dAz = T(0), dBz = T(0);
                   sfor<NX + 2>([&](auto tx_) {  // direction x open to NX + 1
@@ -450,8 +473,8 @@ __global__ void __launch_bounds__(128, 2) grad_warp_kernel(GradArgs a) {
           const int iab = it / nci, ci = it - iab * nci;
           const int cd = c0 + ci;
           const int mu = ao1 + iab / NB, nu = ao2 + iab % NB, la = ao3 + cd / ND, si = ao4 + cd % ND;
-          const T Gv = a.cj * 4.0 * __ldg(Dp + (size_t)mu * n + nu) * __ldg(Dp + (size_t)la * n + si) -
-                       a.ck * (__ldg(Dp + (size_t)mu * n + la) * __ldg(Dp + (size_t)nu * n + si) +
+          const T Gv = T(4.0 * a.cj) * __ldg(Dp + (size_t)mu * n + nu) * __ldg(Dp + (size_t)la * n + si) -
+                       T(a.ck) * (__ldg(Dp + (size_t)mu * n + la) * __ldg(Dp + (size_t)nu * n + si) +
                                __ldg(Dp + (size_t)mu * n + si) * __ldg(Dp + (size_t)nu * n + la));
           const int a0w = tab_ab[2 * iab], a1w = tab_ab[2 * iab + 1];
           const int fxo = a0w & 1023, fyo = (a0w >> 10) & 1023, fzo = a0w >> 20;

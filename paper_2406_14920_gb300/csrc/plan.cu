@@ -1295,8 +1295,8 @@ static int plan_create(int nmol, const eri_basis_t* const* bases, const double* 
     CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_prefmaxp, npair)); CKP(dalloc(&P->d_ea, nprimpair));
     CKP(dalloc(&P->d_dmax, npair));
     CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3 + 2));  // + range-guard and screened counts
-    CKP(dalloc(&P->d_counters2, 2 * NPAIRCLASS * NPAIRCLASS * 3));
-    CKP(cudaMemset(P->d_counters2, 0, sizeof(unsigned long long) * 2 * NPAIRCLASS * NPAIRCLASS * 3));
+    CKP(dalloc(&P->d_counters2, 3 * NPAIRCLASS * NPAIRCLASS * 3));
+    CKP(cudaMemset(P->d_counters2, 0, sizeof(unsigned long long) * 3 * NPAIRCLASS * NPAIRCLASS * 3));
     CKP(dalloc(&P->d_rsteps, st.size()));
     CKP(dalloc(&P->d_Dp, (size_t)P->nmat)); CKP(dalloc(&P->d_Dpf, (size_t)P->nmat));
     CKP(dalloc(&P->d_Kh, (size_t)P->nmat));
@@ -1914,55 +1914,97 @@ extern "C" int eri_energy(eri_plan_t* plan, const double* D, const double* J, co
   return ERI_OK;
 }
 
-static cudaError_t launch_grad_class(int X, int Y, const GradArgs& ga, cudaStream_t s, int nsm) {
-  switch (X) {
-    case 0: return launch_grad_bra0(Y, ga, s, nsm);
-    case 1: return launch_grad_bra1(Y, ga, s, nsm);
-    case 2: return launch_grad_bra2(Y, ga, s, nsm);
-    case 3: return launch_grad_bra3(Y, ga, s, nsm);
-    case 4: return launch_grad_bra4(Y, ga, s, nsm);
-    case 5: return launch_grad_bra5(Y, ga, s, nsm);
-    case 6: return launch_grad_bra6(Y, ga, s, nsm);
-    case 7: return launch_grad_bra7(Y, ga, s, nsm);
-    case 8: return launch_grad_bra8(Y, ga, s, nsm);
-    case 9: return launch_grad_bra9(Y, ga, s, nsm);
-  }
+static cudaError_t launch_grad_class(int X, int Y, int prec, const GradArgs& ga, cudaStream_t s, int nsm) {
+#define ERI_GRAD_UNIT_CALL(UX, UP) \
+  if (X == UX && prec == UP) return launch_grad_unit<UX, UP, 0>(Y, ga, s, nsm);
+  ERI_GRAD_UNITS(ERI_GRAD_UNIT_CALL)
+#undef ERI_GRAD_UNIT_CALL
   return cudaErrorInvalidValue;
 }
 
-extern "C" int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int32_t want_j, int32_t want_k,
-                           void* stream) {
+extern "C" int eri_jk_grad_prec(eri_plan_t* plan, const double* D, double* dEdR, int32_t want_j, int32_t want_k,
+                                int32_t precision, void* stream) {
   eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
   if (!P || !D || !dEdR) return ERI_EINVAL;
+  if (precision != ERI_FP64 && precision != ERI_MIXED) return ERI_EINVAL;
+  const bool mixed = precision == ERI_MIXED;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(P->device));
-  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(molmats(P), D, P->d_f, P->d_Dp, nullptr);
+  const MolMats mm = molmats(P);
+  k_scale_d<<<P->mat_grid(256), 256, 0, s>>>(mm, D, P->d_f, P->d_Dp, mixed ? P->d_Dpf : nullptr);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(dEdR, 0, sizeof(double) * 3 * P->natom, s));
   if (!want_j && !want_k) return ERI_OK;
+  if (mixed) {
+    k_dmax<<<grid1(P->npair, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_sh_l, P->d_pao1, P->d_pao2,
+                                                P->d_pmol, P->d_mat_off, P->d_mat_n, P->d_Dp, P->d_dmax);
+    CK(cudaGetLastError());
+    const int rc = P->ensure_tier_bufs(1);
+    if (rc != ERI_OK) return rc;
+  }
   GradArgs ga{};
   ga.pd = P->pairdata(); ga.sp = P->spinfo(); ga.bt = P->boystabs(); ga.rsteps = P->d_rsteps; ga.Dp = P->d_Dp;
+  ga.Dpf = P->d_Dpf;
   ga.ea = P->d_ea; ga.sh_atom = P->d_sh_atom; ga.grad = dEdR;
   ga.cj = want_j ? 1.0 : 0.0;
   ga.ck = want_k ? 1.0 : 0.0;
   ga.omega2 = P->omega * P->omega;
+  ga.omega2f = (float)ga.omega2;
   ga.det = P->opts.deterministic ? 1 : 0;
-  unsigned long long* gcnt = P->d_counters2 + NPAIRCLASS * NPAIRCLASS * 3;
-  CK(cudaMemsetAsync(gcnt, 0, sizeof(unsigned long long) * NPAIRCLASS * NPAIRCLASS * 3, s));
+  // tier split of the ordered lists: the energy's test (reading 5) on each item
+  KArgs ka{};
+  ka.pd = P->pairdata(); ka.sp = P->spinfo();
+  ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
+  ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
+  ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = 1;
+  unsigned long long* gcnt = P->d_counters2 + NPAIRCLASS * NPAIRCLASS * 3;  // kinds 1 (FP64) and 2 (FP32)
+  CK(cudaMemsetAsync(gcnt, 0, sizeof(unsigned long long) * 2 * NPAIRCLASS * NPAIRCLASS * 3, s));
+  auto launch = [&](int X, int Y, int tier) -> int {
+    ga.counter = gcnt + ((tier * NPAIRCLASS + X) * NPAIRCLASS + Y) * 3;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (P->opts.profile) {
+      CK(P->prof_event_pair(&e0, &e1));
+      CK(cudaEventRecord(e0, s));
+    }
+    CK(launch_grad_class(X, Y, tier, ga, s, P->nsm));
+    if (P->opts.profile) {
+      CK(cudaEventRecord(e1, s));
+      P->prof_log.push_back({X, Y, tier ? 4 : 2, P->prof_ev_used - 2});
+    }
+    return ERI_OK;
+  };
   for (int X = 0; X < NPAIRCLASS; ++X)
     for (int Y = 0; Y < NPAIRCLASS; ++Y) {
-      ga.wl = P->jlist(X, Y);
-      if (ga.wl.total == 0) continue;
-      ga.counter = gcnt + (X * NPAIRCLASS + Y) * 3;
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (P->opts.profile) {
-        CK(P->prof_event_pair(&e0, &e1));
-        CK(cudaEventRecord(e0, s));
+      const WorkList full = P->jlist(X, Y);
+      if (full.total == 0) continue;
+      if (!mixed) {
+        ga.wl = full;
+        ga.items = nullptr;
+        ga.nitems = nullptr;
+        const int rc = launch(X, Y, 0);
+        if (rc != ERI_OK) return rc;
+        continue;
       }
-      CK(launch_grad_class(X, Y, ga, s, P->nsm));
-      if (P->opts.profile) {
-        CK(cudaEventRecord(e1, s));
-        P->prof_log.push_back({X, Y, 2, P->prof_ev_used - 2});
+      int2* buf = P->tbuf[0];
+      unsigned int* cnt = P->tcnt;
+      for (int64_t f = 0; f < full.total; f += P->tier_cap) {
+        ka.wl = full;
+        ka.wl.first = f;
+        ka.wl.total = std::min<int64_t>(full.total, f + P->tier_cap);
+        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned int), s));
+        const int64_t nch = (ka.wl.total - f + 31) / 32;
+        k_tier_split<<<(int)std::max<int64_t>(1, std::min<int64_t>((nch + 7) / 8, (int64_t)P->nsm * 8)), 256, 0,
+                       s>>>(ka, buf, buf + P->tier_cap, cnt);
+        CK(cudaGetLastError());
+        for (int tier = 0; tier < 2; ++tier) {
+          ga.wl = full;
+          ga.wl.first = 0;
+          ga.wl.total = ka.wl.total - f;  // upper bound of the tier's count (grid sizing)
+          ga.items = buf + (tier ? P->tier_cap : 0);
+          ga.nitems = cnt + tier;
+          const int rc = launch(X, Y, tier);
+          if (rc != ERI_OK) return rc;
+        }
       }
     }
   if (ga.det) {
@@ -1970,6 +2012,11 @@ extern "C" int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int3
     CK(cudaGetLastError());
   }
   return ERI_OK;
+}
+
+extern "C" int eri_jk_grad(eri_plan_t* plan, const double* D, double* dEdR, int32_t want_j, int32_t want_k,
+                           void* stream) {
+  return eri_jk_grad_prec(plan, D, dEdR, want_j, want_k, ERI_FP64, stream);
 }
 
 extern "C" int eri_get_lists(eri_plan_t* plan, float* Q, int32_t* sig, int32_t* counts, int32_t* sorted,
@@ -2043,10 +2090,10 @@ extern "C" int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t
   if (!P || !count || (cap > 0 && !out)) return ERI_EINVAL;
   CK(cudaSetDevice(P->device));
   CK(cudaDeviceSynchronize());
-  unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6], c2[2 * NPAIRCLASS * NPAIRCLASS * 3];
+  unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6], c2[3 * NPAIRCLASS * NPAIRCLASS * 3];
   CK(cudaMemcpy(c, P->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(c2, P->d_counters2, sizeof(c2), cudaMemcpyDeviceToHost));
-  constexpr int NT = 4;  // tiers: 0 FP64 J/K, 1 FP32 J/K, 2 gradient, 3 J-engine
+  constexpr int NT = 5;  // tiers: 0 FP64 J/K, 1 FP32 J/K, 2 gradient FP64, 3 J-engine, 4 gradient FP32
   double ms[NPAIRCLASS * NPAIRCLASS * NT] = {};
   int nl[NPAIRCLASS * NPAIRCLASS * NT] = {};
   for (const auto& r : P->prof_log) {
@@ -2061,8 +2108,9 @@ extern "C" int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t
     if (!nl[k]) continue;
     if (n < cap) {
       const int X = k / (NT * NPAIRCLASS), Y = (k / NT) % NPAIRCLASS, t = k % NT;
+      const int kind = t == 3 ? 0 : (t == 2 ? 1 : 2);  // counters2 kinds: J-engine, gradient FP64, gradient FP32
       const unsigned long long* q = t < 2 ? c + ((X * NPAIRCLASS + Y) * 2 + t) * 3
-                                          : c2 + ((t == 3 ? 0 : 1) * NPAIRCLASS * NPAIRCLASS + X * NPAIRCLASS + Y) * 3;
+                                          : c2 + (kind * NPAIRCLASS * NPAIRCLASS + X * NPAIRCLASS + Y) * 3;
       eri_launch_prof_t& o = out[n];
       o.bra_class = X;
       o.ket_class = Y;
@@ -2072,7 +2120,7 @@ extern "C" int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t
       o.quartets = (int64_t)q[0];
       o.prim_quartets = (int64_t)q[1];
       o.flops = t < 2 ? class_flops(X, Y, (double)q[0], (double)q[1], (double)q[2], P->last_do_j, P->last_do_k)
-                      : t == 2 ? grad_flops(X, Y, (double)q[0], (double)q[1], (double)q[2])
+                      : (t == 2 || t == 4) ? grad_flops(X, Y, (double)q[0], (double)q[1], (double)q[2])
                                : jengine_flops(X, Y, (double)q[1]);
     }
     ++n;

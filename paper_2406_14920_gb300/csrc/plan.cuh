@@ -62,7 +62,7 @@ struct eri_plan_impl {
   float *d_pmaxp = nullptr, *d_dmax = nullptr, *d_prefmaxp = nullptr;
   double* d_ea = nullptr;
   unsigned long long* d_counters = nullptr;  // [X*10+Y][tier][items, prim quartets, bra primitives]
-  unsigned long long* d_counters2 = nullptr; // [kind][X*10+Y][same]; kind 0 = J-engine, 1 = gradient
+  unsigned long long* d_counters2 = nullptr; // [kind][X*10+Y][same]; kinds: J-engine, gradient FP64, gradient FP32
   bool last_mixed = false, last_do_j = false, last_do_k = false;
   // optional per-launch profiling (opts.profile): events recorded around each class launch
   struct ProfRec { int X, Y, tier, ev; };

@@ -31,3 +31,9 @@
   U(8, 1, 4, 8)         \
   U(9, 0, 0, 9)         \
   U(9, 1, 0, 9)
+
+// Compilation units of the gradient kernels: ERI_GRAD_UNIT(X, P) is bra pair
+// class X with every ket class, precision P (g_unit.cu, compiled per entry).
+#define ERI_GRAD_UNITS(U) \
+  U(0, 0) U(0, 1) U(1, 0) U(1, 1) U(2, 0) U(2, 1) U(3, 0) U(3, 1) U(4, 0) U(4, 1) \
+  U(5, 0) U(5, 1) U(6, 0) U(6, 1) U(7, 0) U(7, 1) U(8, 0) U(8, 1) U(9, 0) U(9, 1)

@@ -10,12 +10,13 @@ Obara-Saika / Head-Gordon-Pople, energies E_J = 1/2 tr(DJ), E_K = -1/4 tr(DK)
 
 J and K are symmetric for a symmetric D; the file holds the upper triangles of
 (J + J^T)/2 and (K + K^T)/2 (symmetrising moves an element by rounding only)
-plus the oracle's own energies and Schwarz bounds, keyed by a SHA-256 of the
-basis (shell table, exponents, raw coefficients, coordinates: exact draws of
-the seeded generator) and thresh, and by 4096 entries of D at seeded positions (D comes from a QR
+plus the oracle's own energies and Schwarz bounds, keyed by the basis (shell
+table exactly; exponents, raw coefficients and coordinates to 1e-13 relative:
+the exponents come through exp(), whose last bit differs between libm
+builds), thresh, and 4096 entries of D at seeded positions (D comes from a QR
 factorisation, whose last bits depend on the BLAS library and its thread
-count, so they are compared to 1e-12, not bit for bit).  A test uses both to tell
-when the workload generator has changed and the file is stale.
+count, so they are compared to 1e-12).  A test uses the key to tell when the
+workload generator has changed and the file is stale.
 
 Usage:  python tests/golden/make_oracle_jk.py 1          (about 2 h on 6 cores)
         python tests/golden/make_oracle_jk.py 1 --rekey  (rewrite the keys of an existing file)
@@ -44,15 +45,18 @@ def golden_path(wl: int) -> str:
     return os.path.join(HERE, f"oracle_jk_w{wl}.npz")
 
 
-def input_hash(basis, thresh: float) -> str:
-    """SHA-256 over the basis and the threshold the oracle's J/K depend on."""
+def shell_hash(basis, thresh: float) -> str:
+    """SHA-256 over the integer shell table and the threshold (exact on every platform)."""
     h = hashlib.sha256()
     for a in (basis.shell_atom, basis.shell_l, basis.shell_nprim, basis.shell_prim_offset):
         h.update(np.ascontiguousarray(a, np.int32).tobytes())
-    for a in (basis.exps, basis.coefs, basis.coords):
-        h.update(np.ascontiguousarray(a, np.float64).tobytes())
     h.update(np.float64(thresh).tobytes())
     return h.hexdigest()
+
+
+def basis_floats(basis) -> np.ndarray:
+    """Exponents, raw coefficients and coordinates, concatenated."""
+    return np.concatenate([basis.exps, basis.coefs, basis.coords.reshape(-1)]).astype(np.float64)
 
 
 def d_fingerprint(D) -> np.ndarray:
@@ -78,29 +82,38 @@ def from_upper(u: np.ndarray, n: int) -> np.ndarray:
 
 
 def load(wl: int):
-    """(J, K, E_J, E_K, Q, basis hash, D fingerprint) from the stored file, or None if absent."""
+    """(J, K, E_J, E_K, Q) from the stored file, or None if absent."""
     p = golden_path(wl)
     if not os.path.exists(p):
         return None
     z = np.load(p)
     n = int(z["nbf"])
-    return (from_upper(z["J_upper"], n), from_upper(z["K_upper"], n), float(z["E_J"]), float(z["E_K"]),
-            z["Q"], str(z["input_sha256"]), z["d_fingerprint"])
+    return from_upper(z["J_upper"], n), from_upper(z["K_upper"], n), float(z["E_J"]), float(z["E_K"]), z["Q"]
 
 
 def matches(wl: int, basis, D) -> bool:
-    """True if the stored file was made for this basis and (to 1e-12) this D."""
-    r = load(wl)
-    return (r is not None and r[5] == input_hash(basis, THRESH) and r[6].shape == (4096,)
-            and float(np.abs(r[6] - d_fingerprint(D)).max()) < 1e-12)
+    """True if the stored file was made for this basis and (to rounding) this D."""
+    p = golden_path(wl)
+    if not os.path.exists(p):
+        return False
+    z = np.load(p)
+    if "shell_sha256" not in z or str(z["shell_sha256"]) != shell_hash(basis, THRESH):
+        return False
+    bf = basis_floats(basis)
+    return (z["basis_floats"].shape == bf.shape and np.allclose(z["basis_floats"], bf, rtol=1e-13, atol=0.0)
+            and float(np.abs(z["d_fingerprint"] - d_fingerprint(D)).max()) < 1e-12)
+
+
+def keys(basis, D) -> dict:
+    return {"shell_sha256": np.str_(shell_hash(basis, THRESH)), "basis_floats": basis_floats(basis),
+            "d_fingerprint": d_fingerprint(D)}
 
 
 def rekey(wl: int) -> None:
     """Rewrite the keys of an existing file (J, K, energies and Q are kept as the oracle wrote them)."""
     basis, D = workloads.workload(wl)
-    z = dict(np.load(golden_path(wl)))
-    z["input_sha256"] = np.str_(input_hash(basis, THRESH))
-    z["d_fingerprint"] = d_fingerprint(D)
+    z = {k: v for k, v in np.load(golden_path(wl)).items() if k != "input_sha256"}
+    z.update(keys(basis, D))
     np.savez_compressed(golden_path(wl), **z)
 
 
@@ -115,8 +128,7 @@ def main(wl: int) -> None:
     asym = max(float(np.abs(J - J.T).max()), float(np.abs(K - K.T).max()))
     np.savez_compressed(golden_path(wl), nbf=np.int64(basis.nbf), J_upper=upper(J), K_upper=upper(K),
                         E_J=np.float64(ej), E_K=np.float64(ek), Q=Q, thresh=np.float64(THRESH),
-                        input_sha256=np.str_(input_hash(basis, THRESH)), d_fingerprint=d_fingerprint(D),
-                        oracle_seconds=np.float64(dt), oracle_threads=np.int64(oracle.max_threads()),
+                        **keys(basis, D), oracle_seconds=np.float64(dt), oracle_threads=np.int64(oracle.max_threads()),
                         max_asymmetry=np.float64(asym))
     print(f"workload {wl}: nbf {basis.nbf}, E_J {ej:.15e}, E_K {ek:.15e}, {dt:.0f} s on "
           f"{oracle.max_threads()} threads, max |M - M^T| {asym:.2e} -> {golden_path(wl)}")

@@ -17,7 +17,7 @@ import make_oracle_jk as G  # noqa: E402
 def test_w1_fixture_matches_generator_and_energies():
     basis, D = W.workload(1)
     assert G.matches(1, basis, D)
-    J, K, ej, ek, Q, _, _ = G.load(1)
+    J, K, ej, ek, Q = G.load(1)
     assert J.shape == (basis.nbf, basis.nbf) and Q.shape == (basis.nshell * (basis.nshell + 1) // 2,)
     assert abs(0.5 * (D * J).sum() - ej) < 1e-9 * abs(ej)
     assert abs(-0.25 * (D * K).sum() - ek) < 1e-9 * abs(ek)

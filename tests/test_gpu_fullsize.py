@@ -192,7 +192,7 @@ def test_w1_fp64_every_element_vs_oracle(eri, w1):
     """Every element of the FP64 J and K of workload 1 against the oracle's full
     build (stored by tests/golden/make_oracle_jk.py, oracle only), within 1e-10;
     the mixed build's E_J and E_K within 1e-6 Eh of the oracle's energies."""
-    G, (Jo, Ko, ejo, eko, Qo, h, fp) = _golden(1)
+    G, (Jo, Ko, ejo, eko, Qo) = _golden(1)
     assert G.matches(1, w1["basis"], w1["D"]), "stored oracle J/K are for other inputs"
     dj = np.abs(w1["J64"] - Jo).max()
     dk = np.abs(w1["K64"] - Ko).max()
