@@ -6,6 +6,11 @@
 #pragma once
 #include "kernels.cuh"
 
+// 1: the register kernel sums the J_ab contributions of a warp's items over the
+// warp (shuffles) when they share the bra pair, one atomic per element
+#ifndef ERI_JAB_REDUCE
+#define ERI_JAB_REDUCE 0
+#endif
 // FP64 register kernel beyond the tiny classes: largest L and footprint
 // (doubles).  GB300 issues about 3.4 FP64 FMAs per clock per SM, so every warp
 // instruction with idle lanes is expensive; one quartet per lane keeps all 32
@@ -213,7 +218,7 @@ __device__ __forceinline__ void eri_block_reg(const KArgs& a, int offb, int npb,
 // transposes are added by the post kernels).
 template <int LA, int LB, int LC, int LD, typename T>
 __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w, int ao1, int ao2, int ao3, int ao4,
-                                               int64_t base, int n) {
+                                               int64_t base, int n, T* jab_out = nullptr) {
   using S = AShape<LA, LB, LC, LD>;
   const T* Dp = dens<T>(A.k) + base;
   double* Kh = A.k.Kh ? A.k.Kh + base : nullptr;
@@ -274,7 +279,8 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 #pragma unroll
       for (int icd = 0; icd < S::NCD; ++icd)
         s = fma(X[iab * S::NCD + icd], __ldg(Dp + (size_t)(ao3 + icd / S::ND) * n + ao4 + icd % S::ND), s);
-      acc_add(Jh + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB, (double)(w2 * s), A.k.det);
+      if (jab_out) jab_out[iab] = w2 * s;  // reduced over the warp by the caller
+      else acc_add(Jh + (size_t)(ao1 + iab / S::NB) * n + ao2 + iab % S::NB, (double)(w2 * s), A.k.det);
     }
 #pragma unroll
     for (int icd = 0; icd < S::NCD; ++icd) {  // Jh_cd += 2w (ab|cd) D_ab
@@ -288,9 +294,16 @@ __device__ __forceinline__ void contract_block(const JKArgs& A, const T* X, T w,
 }
 
 // One quartet (bra position ib, ket position ik of the work list) of a thread-kernel class.
+// Where an item's J_ab contributions go when the caller reduces them over the warp.
+struct JabTarget {
+  int pb_id, ao1, ao2, n;
+  int64_t base;
+};
+
 template <int LA, int LB, int LC, int LD, typename T>
 __device__ __forceinline__ void thread_item(const JKArgs& A, int ib, int ik, unsigned long long& done,
-                                            unsigned long long& doneq, unsigned long long& doneb) {
+                                            unsigned long long& doneq, unsigned long long& doneb,
+                                            T* jab_out = nullptr, JabTarget* tgt = nullptr) {
   using S = AShape<LA, LB, LC, LD>;
   const KArgs& a = A.k;
   const int pb_id = __ldg(a.wl.bra + ib);
@@ -313,9 +326,12 @@ __device__ __forceinline__ void thread_item(const JKArgs& A, int ib, int ik, uns
   else
     eri_block_reg_pq<LA, LB, LC, LD, T>(a, __ldg(a.sp.poff + pb_id), npb_, __ldg(a.sp.eoff + pb_id),
                                         __ldg(a.sp.poff + pk_id), npk_, __ldg(a.sp.eoff + pk_id), X);
-  contract_block<LA, LB, LC, LD, T>(A, X, w, __ldg(a.sp.ao1 + pb_id), __ldg(a.sp.ao2 + pb_id),
-                                    __ldg(a.sp.ao1 + pk_id), __ldg(a.sp.ao2 + pk_id), __ldg(a.sp.mat_off + mol),
-                                    __ldg(a.sp.mat_n + mol));
+  const int ao1 = __ldg(a.sp.ao1 + pb_id), ao2 = __ldg(a.sp.ao2 + pb_id);
+  const int64_t base = __ldg(a.sp.mat_off + mol);
+  const int n = __ldg(a.sp.mat_n + mol);
+  if (tgt) *tgt = JabTarget{pb_id, ao1, ao2, n, base};
+  contract_block<LA, LB, LC, LD, T>(A, X, w, ao1, ao2, __ldg(a.sp.ao1 + pk_id), __ldg(a.sp.ao2 + pk_id), base, n,
+                                    jab_out);
 }
 
 template <int LA, int LB, int LC, int LD, typename T>
@@ -335,6 +351,52 @@ __global__ void __launch_bounds__(128) jk_thread_kernel(JKArgs A) {
        tl += (stride >> 5) * nshard) {
     const int64_t t0 = first + tl * span;
     const int64_t i1 = t0 + span < total ? t0 + span : total;
+#if ERI_JAB_REDUCE
+    if (A.Jh && !a.det) {
+      // the list is bra-major: a warp's 32 items usually share the bra pair, so
+      // their J_ab contributions are summed with shuffles (in FP64) and added
+      // once; deterministic builds keep one fixed-point add per item, whose sum
+      // does not depend on how items fall into warps
+      using S = AShape<LA, LB, LC, LD>;
+      BraCursor cur;
+      if (!compact) cur.seek(a.wl, t0 + lane < i1 ? t0 + lane : t0);
+      for (int64_t b0 = t0; b0 < i1; b0 += 32) {  // uniform over the warp; lane 0 always has an item
+        const int64_t item = b0 + lane;
+        const bool ok = item < i1;
+        T jab[S::NAB];
+        JabTarget tg{-1, 0, 0, 0, 0};
+#pragma unroll
+        for (int x = 0; x < S::NAB; ++x) jab[x] = T(0);
+        if (ok) {
+          int ib, ik;
+          if (compact) {
+            const int2 v = __ldg(a.items + item);
+            ib = v.x;
+            ik = v.y;
+          } else {
+            ik = cur.at(a.wl, item);
+            ib = cur.ib;
+          }
+          thread_item<LA, LB, LC, LD, T>(A, ib, ik, done, doneq, doneb, jab, &tg);
+        }
+        const int pb0 = __shfl_sync(0xffffffffu, tg.pb_id, 0);
+        if (__all_sync(0xffffffffu, !ok || tg.pb_id == pb0)) {
+#pragma unroll
+          for (int x = 0; x < S::NAB; ++x) {
+            double v = (double)jab[x];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) atomicAdd(A.Jh + tg.base + (size_t)(tg.ao1 + x / S::NB) * tg.n + tg.ao2 + x % S::NB, v);
+          }
+        } else if (ok) {
+#pragma unroll
+          for (int x = 0; x < S::NAB; ++x)
+            acc_add(A.Jh + tg.base + (size_t)(tg.ao1 + x / S::NB) * tg.n + tg.ao2 + x % S::NB, (double)jab[x], a.det);
+        }
+      }
+      continue;
+    }
+#endif
     const int64_t i0 = t0 + lane;
     if (i0 >= i1) continue;
     if (compact) {
