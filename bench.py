@@ -399,6 +399,8 @@ def run_ours(args, rank, world, local_rank):
         out["jengine"] = run_jengine_leg(args, dev, peak_meas)
         out["longrange"] = run_longrange_leg(args, dev)
         out["nuclear"] = run_nuclear_leg(args, dev)
+        if args.shard_balance:
+            out["shard_balance"] = run_shard_leg(args, dev)
         if args.grad_steps > 0:
             out["gradient"] = run_gradient_leg(args, dev, peak_meas)
     if rank == 0 and not args.no_cpu_baseline:
@@ -542,6 +544,51 @@ def run_longrange_leg(args, dev):
     plan.close()
     return {"omega": 0.3, "ms_per_step": ms, "value": nq / (ms * 1e-3), "unit": UNIT, "steps": args.aux_steps,
             "E_J": float(E[0]), "E_K": float(E[1])}
+
+
+def run_shard_leg(args, dev):
+    """Load balance of the work split over N GPUs (eri_plan_set_shard: tiles of
+    every class pair's list dealt round-robin), measured on one GPU by running
+    each share of the mixed workload-1 build in turn: per-share time and
+    quartet count, and the largest share over the mean (the efficiency bound
+    the split leaves for N GPUs).  The shares' J and K summed are compared with
+    the unsplit build."""
+    import torch
+    import paper_2406_14920_gb300 as eri
+    import workloads as W
+    basis, D = W.workload(WORKLOAD_ID)
+    plan = eri.Plan(basis, thresh=THRESH, precision=eri.ERI_MIXED, mixed_tau=args.tau, device=dev.index,
+                    tune_cache=args.tune_cache)
+    stream = torch.cuda.current_stream(dev)
+    Dt = torch.from_numpy(D).to(dev)
+    J, K = torch.empty_like(Dt), torch.empty_like(Dt)
+    plan.build_jk(Dt, J, K)
+    Jf, Kf = J.clone(), K.clone()
+    out = {}
+    for n in args.shard_balance:
+        ms, nq = [], []
+        Js, Ks = torch.zeros_like(Dt), torch.zeros_like(Dt)
+        for r in range(n):
+            plan.set_shard(r, n)
+            plan.build_jk(Dt, J, K)
+            Js += J
+            Ks += K
+            torch.cuda.synchronize()
+            e0, e1, _ = _events(stream)
+            e0.record(stream)
+            for _ in range(args.aux_steps):
+                plan.build_jk(Dt, J, K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1) / args.aux_steps)
+            nq.append(int(plan.stats()["quartets_k"]))
+        diff = max(float((Js - Jf).abs().max()), float((Ks - Kf).abs().max()))
+        out[str(n)] = {"ms": [round(x, 2) for x in ms], "quartets": nq,
+                       "max_over_mean_ms": max(ms) / (sum(ms) / n), "max_over_mean_quartets": max(nq) / (sum(nq) / n),
+                       "sum_ms": sum(ms), "max_abs_diff_vs_unsplit": diff}
+    plan.set_shard(0, 1)
+    plan.close()
+    return out
 
 
 def run_nuclear_leg(args, dev):
@@ -724,6 +771,8 @@ def main():
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the J-engine, long-range, point-charge and gradient legs")
     ap.add_argument("--aux-steps", type=int, default=2, help="timed steps of the J-engine / long-range / V legs")
+    ap.add_argument("--shard-balance", type=lambda v: [int(x) for x in v.split(",") if x], default=[2, 4, 8],
+                    help="share counts of the load-balance leg (comma list; empty to skip)")
     ap.add_argument("--grad-steps", type=int, default=1, help="timed gradient steps (after one warm-up pass)")
     ap.add_argument("--ncu-case", action="store_true",
                     help="small case for ncu section captures: the first 20 atoms of the workload, two mixed "

@@ -15,12 +15,13 @@
 // (doubles).  GB300 issues about 3.4 FP64 FMAs per clock per SM, so every warp
 // instruction with idle lanes is expensive; one quartet per lane keeps all 32
 // lanes busy (measured: (pp|pp) 31 -> 9.8 ms, (ds|pp) 16 -> 5.1 ms, (fp|ps)
-// 12 -> 4.9 ms on workload 1).
+// 12 -> 4.9 ms on workload 1; raising the limits from L 5 / 200 to L 6 / 300
+// took (dp|pp) 16.5 -> 13.6 ms and (fs|fs) 2.5 -> 1.5 ms).
 #ifndef ERI_THREAD64_LMAX
-#define ERI_THREAD64_LMAX 5
+#define ERI_THREAD64_LMAX 6
 #endif
 #ifndef ERI_THREAD64_FOOT
-#define ERI_THREAD64_FOOT 200
+#define ERI_THREAD64_FOOT 300
 #endif
 
 namespace eri {

@@ -82,7 +82,7 @@ struct BShape {
   // what lets the whole ket range sit in one chunk (one ket primitive per
   // batch), the condition of the compile-time bra transform below
   static constexpr int NEED_FULL = FIXED + NCD * PER_C + PER_G;
-  static constexpr bool WANT_FULL = sizeof(T) == 4 && NCD >= 16 && NAB * ((NCD + 31) / 32) <= ERI_REGD32_MAX &&
+  static constexpr bool WANT_FULL = sizeof(T) == 4 && NCD >= 8 && NAB * ((NCD + 31) / 32) <= ERI_REGD32_MAX &&
                                     NEED_FULL <= (ERI_WARP_SMEM32_FULL_KB * 1024) / 4;
   static constexpr int BUDGET = (WANT_FULL && BUDGET0 < NEED_FULL) ? NEED_FULL : BUDGET0;
   static constexpr int G0 = (BUDGET - FIXED - NCD * PER_C) / PER_G;
@@ -95,10 +95,12 @@ struct BShape {
   static constexpr bool REGW = CH == NCD && (sizeof(T) == 4 ? NCD * NPS <= 64 : (ERI_REGW64 && NCD * NPS <= 32));
   // step D with compile-time indices: lane owns ket pair cd = lane + 32 j, the
   // bra pairs ab are a compile-time loop (E broadcast, W row at a per-lane
-  // base), X[ab][cd] stays in registers over the bra primitives.  Worth it when
-  // most lanes own a cd and the X slice fits in registers.
+  // base), X[ab][cd] stays in registers over the bra primitives.  Worth it
+  // from 8 ket components up, when the X slice fits in registers (measured on
+  // workload 1, FP32: (ff|pp) 17.9 -> 9.6 ms, (fd|fs) 15.8 -> 9.4 ms, against
+  // the (ab, cd) item loop).
   static constexpr int NCS = (NCD + 31) / 32;
-  static constexpr bool REGD = CH == NCD && NCD >= 16 && NAB * NCS <= (sizeof(T) == 4 ? ERI_REGD32_MAX : 48);
+  static constexpr bool REGD = CH == NCD && NCD >= 8 && NAB * NCS <= (sizeof(T) == 4 ? ERI_REGD32_MAX : 48);
   static constexpr int SM_BOX = 0, SM_PING = SM_BOX + G * BOX, SM_SC = SM_PING + G * 2 * NPING,
                        SM_EK = SM_SC + G * NSC, SM_EB = SM_EK + G * 3 * NEK, SM_W = SM_EB + 3 * NEB,
                        SM_X = SM_W + CH * HABP, SM_TOTAL = SM_X + NAB * CH;
