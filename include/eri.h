@@ -240,6 +240,19 @@ int eri_plan_set_shard(eri_plan_t* plan, int32_t shard, int32_t nshard);
 int eri_plan_set_omega(eri_plan_t* plan, double omega);
 
 /*
+ * Mixed-precision threshold of this plan's later ERI_MIXED builds, gradients
+ * and allocation-free builds: a quartet runs in FP64 when its density-weighted
+ * Schwarz bound Q_ab Q_cd max|D'| >= mixed_tau (or the FP32 range guard trips),
+ * else in FP32 (Sec. 4.1).  Lowering it between builds is the dynamic-precision
+ * scheme the paper cites: a loose threshold in the first SCF iterations, a
+ * tighter one as the density converges.  The split is taken on the device at
+ * every build, so a change costs nothing; a captured graph build is dropped when
+ * the value changes (after a device wait).  Host only.
+ * Errors: ERI_EINVAL (NULL, mixed_tau < 0 or NaN).
+ */
+int eri_plan_set_tau(eri_plan_t* plan, double mixed_tau);
+
+/*
  * Read or set the plan's tile table (host int32 [10][10][2] indexed
  * [bra class][ket class][tier], entries with ket class > bra class unused;
  * 0 in eri_set_tiles = built-in default, valid values 0..1024).  Use them to

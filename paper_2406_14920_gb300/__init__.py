@@ -76,6 +76,7 @@ def lib():
         L.eri_get_tiles.argtypes = [vp, C.POINTER(C.c_int32)]
         L.eri_plan_set_shard.argtypes = [vp, i32, i32]
         L.eri_plan_set_omega.argtypes = [vp, C.c_double]
+        L.eri_plan_set_tau.argtypes = [vp, C.c_double]
         L.eri_set_tiles.argtypes = [vp, C.POINTER(C.c_int32)]
         L.eri_energy.argtypes = [vp, vp, vp, vp, vp, vp]
         L.eri_jk_grad.argtypes = [vp, vp, vp, i32, i32, vp]
@@ -304,6 +305,11 @@ class Plan:
         """Two-electron operator of later builds and gradients: 0 = 1/r,
         omega > 0 = erf(omega r)/r (eri_plan_set_omega)."""
         _check(lib().eri_plan_set_omega(self.h, float(omega)), "eri_plan_set_omega")
+
+    def set_tau(self, mixed_tau):
+        """Mixed-precision threshold of later ERI_MIXED builds and gradients
+        (eri_plan_set_tau; dynamic precision: tighten it as SCF converges)."""
+        _check(lib().eri_plan_set_tau(self.h, float(mixed_tau)), "eri_plan_set_tau")
 
     def tiles(self):
         t = np.zeros(200, np.int32)

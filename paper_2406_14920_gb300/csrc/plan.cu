@@ -1824,6 +1824,19 @@ extern "C" int eri_plan_set_omega(eri_plan_t* plan, double omega) {
   return ERI_OK;
 }
 
+extern "C" int eri_plan_set_tau(eri_plan_t* plan, double mixed_tau) {
+  eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
+  if (!P || !(mixed_tau >= 0.0)) return ERI_EINVAL;
+  if (P->gexec && mixed_tau != P->opts.mixed_tau) {  // the graph's launches carry the old threshold
+    CK(cudaSetDevice(P->device));
+    CK(cudaDeviceSynchronize());
+    CK(cudaGraphExecDestroy(P->gexec));
+    P->gexec = nullptr;
+  }
+  P->opts.mixed_tau = mixed_tau;
+  return ERI_OK;
+}
+
 extern "C" int eri_get_tiles(eri_plan_t* plan, int32_t* tiles) {
   eri_plan_impl* P = reinterpret_cast<eri_plan_impl*>(plan);
   if (!P || !tiles) return ERI_EINVAL;

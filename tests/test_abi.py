@@ -117,6 +117,7 @@ def test_shard_and_layout_null_arguments(eri):
     assert L.eri_build_jk_noalloc(None, None, None, None, None) == -1
     assert L.eri_peak_probe(0, 0, None, None) == -1
     assert L.eri_plan_set_omega(None, C.c_double(0.5)) == -1
+    assert L.eri_plan_set_tau(None, C.c_double(1e-5)) == -1
     assert L.eri_nuclear(None, 0, None, None, None, None) == -1
     assert L.eri_check(None) == -1
     assert L.eri_jk_grad_prec(None, None, None, 1, 1, 0, None) == -1

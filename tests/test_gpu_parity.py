@@ -140,3 +140,33 @@ def test_mixed_precision_w0(eri, tau, etol, mtol):
         assert st["quartets_k_fp32"] == st["quartets_k"]
     else:  # the paper's default bound still sends part of workload 0 to the FP32 tier
         assert 0 < st["quartets_k_fp32"] < st["quartets_k"], st
+
+
+def test_dynamic_precision_set_tau(eri):
+    """eri_plan_set_tau between builds of one plan (the dynamic-precision scheme
+    of Sec. 4.1's citation): the FP32 share falls as tau falls, tau = 0 is the
+    FP64 build, and a captured graph build follows the new threshold."""
+    import torch
+    basis, D = W.workload(0)
+    plan = eri.Plan(basis, thresh=1e-12, precision=eri.ERI_MIXED, mixed_tau=1e-1)
+    Dt = torch.from_numpy(D).cuda()
+    o = oracle.Oracle(basis)
+    Jr, Kr = o.jk(D, 1e-12, o.schwarz())
+    ej, ek = o.energy(D, Jr, Kr)
+    J, K = torch.empty_like(Dt), torch.empty_like(Dt)
+    plan.build_jk_graph(Dt, J, K)
+    n32, err = [], []
+    for tau in (1e-1, 1e-3, 1e-5, 0.0):
+        plan.set_tau(tau)
+        plan.build_jk(Dt, J, K)
+        E = plan.energy(Dt, J, K).cpu().numpy()
+        n32.append(plan.stats()["quartets_k_fp32"])
+        err.append(max(abs(E[0] - ej), abs(E[1] - ek)))
+    assert n32[0] > n32[1] > n32[2] > n32[3] == 0, n32
+    assert err[1] < 1e-6 and err[2] < 1e-6 and err[3] < 1e-10, err
+    # the graph captured at tau = 0.1 is dropped; the replay now runs all-FP64
+    plan.build_jk_graph(Dt, J, K)
+    assert np.abs(J.cpu().numpy() - Jr).max() < 1e-10 and np.abs(K.cpu().numpy() - Kr).max() < 1e-10
+    with pytest.raises(RuntimeError):
+        plan.set_tau(-1.0)
+
