@@ -64,6 +64,18 @@ def lib():
         L.or_max_threads.restype = C.c_int
         L.or_quartet_batch.argtypes = [C.c_void_p, C.c_int, i]
         L.or_quartet_batch.restype = C.c_double
+        i64 = C.c_int64
+        L.or_xc_grid_size.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.or_xc_grid_size.restype = i64
+        L.or_xc_grid.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, d, d]
+        L.or_xc_ao.argtypes = [C.c_void_p, d, d, d]
+        L.or_xc_density.argtypes = [C.c_void_p, d, i64, d, d, d]
+        L.or_xc_functional.argtypes = [C.c_int, i64, d, d, d, d, d]
+        L.or_xc_functional.restype = C.c_int
+        L.or_xc_energy.argtypes = [i64, d, d]
+        L.or_xc_energy.restype = C.c_double
+        L.or_xc_matrix.argtypes = [C.c_void_p, i64, d, d, d, d, d]
+        L.or_xc_matrix_elements.argtypes = [C.c_void_p, i64, d, d, d, d, C.c_int, i, d]
         _lib = L
     return _lib
 
@@ -118,6 +130,24 @@ def prim_eri_erf(la, lb, lc, ld, a, b, c, d, A, B, Cc, D, omega):
     lib().or_prim_eri_erf(la, lb, lc, ld, a, b, c, d, _d(_v3(A)), _d(_v3(B)), _d(_v3(Cc)), _d(_v3(D)),
                           float(omega), _d(out))
     return out.reshape(ncart(la), ncart(lb), ncart(lc), ncart(ld))
+
+
+def xc_functional(kind, rho, grad):
+    """(eps, v_rho, v_grad[G, 3]) of functional `kind` (1 Slater, 2 Becke-88 exchange) at every point."""
+    rho = np.ascontiguousarray(rho, np.float64).reshape(-1)
+    grad = np.ascontiguousarray(grad, np.float64).reshape(-1, 3)
+    G = rho.shape[0]
+    eps, vrho, vgrad = np.zeros(G), np.zeros(G), np.zeros((G, 3))
+    if lib().or_xc_functional(int(kind), G, _d(rho), _d(grad), _d(eps), _d(vrho), _d(vgrad)) != 0:
+        raise ValueError(f"unknown functional {kind}")
+    return eps, vrho, vgrad
+
+
+def xc_energy(w, eps):
+    """E_xc = sum_g w_g eps_g (compensated sum)."""
+    w = np.ascontiguousarray(w, np.float64).reshape(-1)
+    eps = np.ascontiguousarray(eps, np.float64).reshape(-1)
+    return float(lib().or_xc_energy(w.shape[0], _d(w), _d(eps)))
 
 
 def max_threads() -> int:
@@ -189,6 +219,56 @@ class Oracle:
         lib().or_nuclear_grad(self.h, _d(np.ascontiguousarray(D, np.float64)), int(q.shape[0]), _d(q), _d(Cc),
                               _d(gA), _d(gC))
         return gA, gC
+
+    def xc_grid(self, nrad, ntheta, radius=1.0):
+        """(points [G, 3], weights [G]) of the molecular grid (Sec. 2.6 step 1; readings in oracle.c)."""
+        G = int(lib().or_xc_grid_size(self.h, int(nrad), int(ntheta)))
+        pts, w = np.zeros((G, 3)), np.zeros(G)
+        lib().or_xc_grid(self.h, int(nrad), int(ntheta), float(radius), _d(pts), _d(w))
+        return pts, w
+
+    def xc_ao(self, r):
+        """(phi [nbf], grad phi [3, nbf]) of every basis function at point r."""
+        phi, dphi = np.zeros(self.nbf), np.zeros((3, self.nbf))
+        lib().or_xc_ao(self.h, _d(_v3(r)), _d(phi), _d(dphi))
+        return phi, dphi
+
+    def xc_density(self, D, pts):
+        """(rho [G], grad rho [G, 3]) at points (Eq. xc_density_0, Eq. xc_density_1)."""
+        pts = np.ascontiguousarray(pts, np.float64).reshape(-1, 3)
+        G = pts.shape[0]
+        rho, grad = np.zeros(G), np.zeros((G, 3))
+        lib().or_xc_density(self.h, _d(np.ascontiguousarray(D, np.float64)), G, _d(pts), _d(rho), _d(grad))
+        return rho, grad
+
+    def xc_matrix(self, pts, w, vrho, vgrad):
+        """V_mn of Eq. xc_grid_sum_0 + Eq. xc_grid_sum_1 for given point potentials."""
+        pts = np.ascontiguousarray(pts, np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(w, np.float64).reshape(-1)
+        vrho = np.ascontiguousarray(vrho, np.float64).reshape(-1)
+        vgrad = np.ascontiguousarray(vgrad, np.float64).reshape(-1, 3)
+        V = np.zeros((self.nbf, self.nbf))
+        lib().or_xc_matrix(self.h, pts.shape[0], _d(pts), _d(w), _d(vrho), _d(vgrad), _d(V))
+        return V
+
+    def xc_matrix_elements(self, pts, w, vrho, vgrad, mn):
+        """Selected elements V[m, n] for index pairs mn [k, 2] (each a full sum over the points)."""
+        pts = np.ascontiguousarray(pts, np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(w, np.float64).reshape(-1)
+        vrho = np.ascontiguousarray(vrho, np.float64).reshape(-1)
+        vgrad = np.ascontiguousarray(vgrad, np.float64).reshape(-1, 3)
+        mn = np.ascontiguousarray(mn, np.int32).reshape(-1, 2)
+        out = np.zeros(mn.shape[0])
+        lib().or_xc_matrix_elements(self.h, pts.shape[0], _d(pts), _d(w), _d(vrho), _d(vgrad), mn.shape[0],
+                                    _i(mn), _d(out))
+        return out
+
+    def xc(self, D, nrad, ntheta, kind, radius=1.0):
+        """(E_xc, V_xc) of functional `kind` on the molecular grid: steps (1)-(4) of Sec. 2.6."""
+        pts, w = self.xc_grid(nrad, ntheta, radius)
+        rho, grad = self.xc_density(D, pts)
+        eps, vrho, vgrad = xc_functional(kind, rho, grad)
+        return xc_energy(w, eps), self.xc_matrix(pts, w, vrho, vgrad)
 
     def eri_block(self, a, b, c, d):
         sh = [ncart(self.l[s]) for s in (a, b, c, d)]

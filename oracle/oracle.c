@@ -1181,3 +1181,320 @@ double or_quartet_batch(void* h, int nq, const int32_t* abcd) {
   }
   return total;
 }
+
+/* ======================================================================== */
+/* Exchange-correlation quadrature on a molecular grid (Sec. 2.6)           */
+/* ======================================================================== */
+/*
+ * The paper's four steps (Sec. 2.6): (1) a molecular grid, (2) the density
+ * and its gradient at every grid point (Eq. xc_density_0, Eq. xc_density_1),
+ * (3) the functional at every point, (4) the XC matrix as a weighted sum over
+ * the points (Eq. xc_grid_sum_0, Eq. xc_grid_sum_1).  Everything below is the
+ * plain definition: basis functions evaluated directly from
+ * Eq. contracted_basis, full double sums over (mu, nu), no screening.
+ *
+ * Readings (the paper names atom-centred standard grids with Becke
+ * partitioning, SI Sec. 1.5, but fixes no rule):
+ *   - radial rule: Gauss-Chebyshev nodes of the second kind,
+ *     x_i = cos(i pi/(n+1)), i = 1..n, mapped by Becke's r = R (1+x)/(1-x);
+ *     weight (pi/(n+1)) sin(theta_i) r^2 dr/dx, with dr/dx = 2R/(1-x)^2;
+ *   - angular rule: Gauss-Legendre nodes in cos(theta) (ascending) times the
+ *     trapezoid rule in phi with 2 n_theta points at phi_k = 2 pi (k+1/2)/n_phi;
+ *   - Becke fuzzy cells of equal size: mu_AB = (|r-A| - |r-B|)/|A-B|,
+ *     p(mu) = (3 mu - mu^3)/2 applied three times, s = (1 - p)/2,
+ *     P_A = prod_{B != A} s(mu_AB), w_A = P_A / sum_B P_B;
+ *   - point order g = ((atom * n_rad + (i-1)) * n_theta + j) * n_phi + k;
+ *   - the functional (the paper evaluates it on the CPU and names no
+ *     functional): closed-shell Slater exchange, or Becke-88 exchange with
+ *     beta = 0.0042; points with rho < 1e-14 contribute nothing.
+ */
+
+#define OR_XC_RHO_MIN 1e-14
+
+/* Gauss-Legendre nodes (ascending) and weights on [-1, 1]: Newton on P_n */
+static void gauss_legendre(int n, double* t, double* w) {
+  for (int i = 0; i < n; ++i) {
+    long double x = cosl(OR_PI_L * (i + 0.75L) / (n + 0.5L)), dp = 0.0L;
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1.0L, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        long double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = x; p0 = 1.0L; }
+      dp = n * (x * p1 - p0) / (x * x - 1.0L);
+      long double dx = p1 / dp;
+      x -= dx;
+      if (fabsl(dx) < 1e-19L) break;
+    }
+    {
+      long double p0 = 1.0L, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        long double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = x; p0 = 1.0L; }
+      dp = n * (x * p1 - p0) / (x * x - 1.0L);
+    }
+    /* cos((i+3/4)pi/(n+1/2)) runs from +1 down: store ascending */
+    t[n - 1 - i] = (double)x;
+    w[n - 1 - i] = (double)(2.0L / ((1.0L - x * x) * dp * dp));
+  }
+}
+
+int64_t or_xc_grid_size(void* h, int nrad, int ntheta) {
+  or_ctx* c = (or_ctx*)h;
+  return (int64_t)c->natom * nrad * ntheta * 2 * ntheta;
+}
+
+/* Becke partition weight of atom `own` at point r */
+static double becke_weight(const or_ctx* c, int own, const double r[3]) {
+  int na = c->natom;
+  double sumP = 0.0, Pown = 0.0;
+  for (int A = 0; A < na; ++A) {
+    const double* RA = c->coords + 3 * A;
+    double dA = sqrt((r[0] - RA[0]) * (r[0] - RA[0]) + (r[1] - RA[1]) * (r[1] - RA[1]) +
+                     (r[2] - RA[2]) * (r[2] - RA[2]));
+    double P = 1.0;
+    for (int B = 0; B < na && P != 0.0; ++B) {
+      if (B == A) continue;
+      const double* RB = c->coords + 3 * B;
+      double dB = sqrt((r[0] - RB[0]) * (r[0] - RB[0]) + (r[1] - RB[1]) * (r[1] - RB[1]) +
+                       (r[2] - RB[2]) * (r[2] - RB[2]));
+      double AB = sqrt((RA[0] - RB[0]) * (RA[0] - RB[0]) + (RA[1] - RB[1]) * (RA[1] - RB[1]) +
+                       (RA[2] - RB[2]) * (RA[2] - RB[2]));
+      double mu = (dA - dB) / AB;
+      for (int it = 0; it < 3; ++it) mu = 1.5 * mu - 0.5 * mu * mu * mu;
+      P *= 0.5 * (1.0 - mu);
+    }
+    sumP += P;
+    if (A == own) Pown = P;
+  }
+  return sumP > 0.0 ? Pown / sumP : 0.0;
+}
+
+/* Step (1): points pts[3G] and weights w[G] of the molecular grid */
+void or_xc_grid(void* h, int nrad, int ntheta, double R, double* pts, double* w) {
+  or_ctx* c = (or_ctx*)h;
+  int nphi = 2 * ntheta, nang = ntheta * nphi;
+  double* t = (double*)malloc(sizeof(double) * ntheta);
+  double* wt = (double*)malloc(sizeof(double) * ntheta);
+  gauss_legendre(ntheta, t, wt);
+  int64_t G = or_xc_grid_size(h, nrad, ntheta);
+#pragma omp parallel for schedule(static)
+  for (int64_t g = 0; g < G; ++g) {
+    int64_t q = g;
+    int k = (int)(q % nphi); q /= nphi;
+    int j = (int)(q % ntheta); q /= ntheta;
+    int i = (int)(q % nrad) + 1; q /= nrad;
+    int a = (int)q;
+    double th = i * OR_PI / (nrad + 1), x = cos(th);
+    double r = R * (1.0 + x) / (1.0 - x);
+    double wr = OR_PI / (nrad + 1) * sin(th) * r * r * 2.0 * R / ((1.0 - x) * (1.0 - x));
+    double ph = 2.0 * OR_PI * (k + 0.5) / nphi, st = sqrt(1.0 - t[j] * t[j]);
+    double wa = wt[j] * 2.0 * OR_PI / nphi;
+    const double* A = c->coords + 3 * a;
+    double p[3] = {A[0] + r * st * cos(ph), A[1] + r * st * sin(ph), A[2] + r * t[j]};
+    pts[3 * g] = p[0];
+    pts[3 * g + 1] = p[1];
+    pts[3 * g + 2] = p[2];
+    w[g] = wr * wa * becke_weight(c, a, p);
+  }
+  (void)nang;
+  free(t);
+  free(wt);
+}
+
+static double ipow(double x, int n) {
+  double r = 1.0;
+  for (int k = 0; k < n; ++k) r *= x;
+  return r;
+}
+
+/* values phi[na] (and gradients dphi[3][na] if dphi) of the components of
+ * shell s at point r, Eq. contracted_basis with the component norms */
+static void ao_shell(const or_ctx* c, int s, const double* r, double* phi, double* dphi) {
+  int L = c->l[s], na = ncart(L);
+  const double* A = ctr(c, s);
+  double d[3] = {r[0] - A[0], r[1] - A[1], r[2] - A[2]};
+  double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  double e0 = 0.0, e1 = 0.0; /* sum_k c_k exp(-a r^2) and sum_k c_k a exp(-a r^2) */
+  for (int k = 0; k < c->nprim[s]; ++k) {
+    double a = c->exps[c->poff[s] + k], e = c->cn[c->poff[s] + k] * exp(-a * r2);
+    e0 += e;
+    e1 += a * e;
+  }
+  for (int m = 0; m < na; ++m) {
+    int e[3];
+    cart_comp(L, m, e);
+    double cf = comp_factor(e[0], e[1], e[2]);
+    double pw[3] = {ipow(d[0], e[0]), ipow(d[1], e[1]), ipow(d[2], e[2])};
+    phi[m] = cf * pw[0] * pw[1] * pw[2] * e0;
+    if (dphi) {
+      for (int x = 0; x < 3; ++x) {
+        int y = (x + 1) % 3, z = (x + 2) % 3;
+        /* d/dx [d_x^i exp(-a r^2)] = i d_x^(i-1) exp - 2 a d_x^(i+1) exp */
+        double lower = e[x] > 0 ? e[x] * ipow(d[x], e[x] - 1) * e0 : 0.0;
+        double upper = 2.0 * ipow(d[x], e[x] + 1) * e1;
+        dphi[x * na + m] = cf * (lower - upper) * pw[y] * pw[z];
+      }
+    }
+  }
+}
+
+/* every basis function (and gradient, dphi[3][nbf]) at point r */
+void or_xc_ao(void* h, const double* r, double* phi, double* dphi) {
+  or_ctx* c = (or_ctx*)h;
+  int n = c->nbf;
+  double buf[10], dbuf[30];
+  for (int s = 0; s < c->nshell; ++s) {
+    int na = ncart(c->l[s]), o = c->aoff[s];
+    ao_shell(c, s, r, buf, dphi ? dbuf : NULL);
+    for (int m = 0; m < na; ++m) {
+      phi[o + m] = buf[m];
+      if (dphi)
+        for (int x = 0; x < 3; ++x) dphi[x * n + o + m] = dbuf[x * na + m];
+    }
+  }
+}
+
+/* Step (2): rho(r_g) = sum D_mn phi_m phi_n (Eq. xc_density_0) and
+ * grad rho = sum D_mn grad(phi_m phi_n) (Eq. xc_density_1), grad[3G] or NULL */
+void or_xc_density(void* h, const double* Dm, int64_t G, const double* pts, double* rho, double* grad) {
+  or_ctx* c = (or_ctx*)h;
+  int n = c->nbf;
+#pragma omp parallel
+  {
+    double* phi = (double*)malloc(sizeof(double) * n);
+    double* dphi = (double*)malloc(sizeof(double) * 3 * n);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t g = 0; g < G; ++g) {
+      or_xc_ao(h, pts + 3 * g, phi, dphi);
+      long double r = 0.0L, gx = 0.0L, gy = 0.0L, gz = 0.0L;
+      for (int m = 0; m < n; ++m)
+        for (int v = 0; v < n; ++v) {
+          double dmv = Dm[(size_t)m * n + v];
+          r += dmv * phi[m] * phi[v];
+          gx += dmv * (dphi[m] * phi[v] + phi[m] * dphi[v]);
+          gy += dmv * (dphi[n + m] * phi[v] + phi[m] * dphi[n + v]);
+          gz += dmv * (dphi[2 * n + m] * phi[v] + phi[m] * dphi[2 * n + v]);
+        }
+      rho[g] = (double)r;
+      if (grad) {
+        grad[3 * g] = (double)gx;
+        grad[3 * g + 1] = (double)gy;
+        grad[3 * g + 2] = (double)gz;
+      }
+    }
+    free(phi);
+    free(dphi);
+  }
+}
+
+/* Step (3): energy density eps, v_rho = d eps/d rho and v_grad = d eps/d(grad rho)
+ * (3 per point) of functional `kind`: 1 Slater exchange, 2 Becke-88 exchange.
+ * Returns 0, or -1 for an unknown kind. */
+int or_xc_functional(int kind, int64_t G, const double* rho, const double* grad, double* eps, double* vrho,
+                     double* vgrad) {
+  if (kind != 1 && kind != 2) return -1;
+  const double cx = 0.75 * cbrt(3.0 / OR_PI);        /* closed-shell Slater constant */
+  const double cxs = 1.5 * cbrt(3.0 / (4.0 * OR_PI)); /* per-spin Slater constant */
+  const double beta = 0.0042;
+  for (int64_t g = 0; g < G; ++g) {
+    double r = rho[g];
+    vgrad[3 * g] = vgrad[3 * g + 1] = vgrad[3 * g + 2] = 0.0;
+    if (!(r >= OR_XC_RHO_MIN)) {
+      eps[g] = 0.0;
+      vrho[g] = 0.0;
+      continue;
+    }
+    if (kind == 1) {
+      eps[g] = -cx * pow(r, 4.0 / 3.0);
+      vrho[g] = -4.0 / 3.0 * cx * cbrt(r);
+      continue;
+    }
+    /* B88 on the spin density rho_s = rho/2, |grad rho_s| = |grad rho|/2 */
+    double rs = 0.5 * r, a = pow(rs, 4.0 / 3.0);
+    double gn = sqrt(grad[3 * g] * grad[3 * g] + grad[3 * g + 1] * grad[3 * g + 1] + grad[3 * g + 2] * grad[3 * g + 2]);
+    double x = 0.5 * gn / a, as = asinh(x);
+    double den = 1.0 + 6.0 * beta * x * as;
+    double F = beta * x * x / den;
+    /* F'(x)/x, regular at x = 0 */
+    double Fpx = (2.0 * beta * den - beta * x * (6.0 * beta * as + 6.0 * beta * x / sqrt(1.0 + x * x))) / (den * den);
+    eps[g] = -2.0 * a * (cxs + F);
+    vrho[g] = -4.0 / 3.0 * cbrt(rs) * (cxs + F - x * x * Fpx);
+    for (int k = 0; k < 3; ++k) vgrad[3 * g + k] = -Fpx * grad[3 * g + k] / (2.0 * a);
+  }
+  return 0;
+}
+
+/* E_xc = sum_g w_g eps_g (compensated) */
+double or_xc_energy(int64_t G, const double* w, const double* eps) {
+  long double s = 0.0L;
+  for (int64_t g = 0; g < G; ++g) s += (long double)w[g] * eps[g];
+  return (double)s;
+}
+
+/* Step (4): V_mn = sum_g w_g [v_rho phi_m phi_n + v_grad . grad(phi_m phi_n)]
+ * (Eq. xc_grid_sum_0 + Eq. xc_grid_sum_1), V[nbf*nbf] overwritten */
+void or_xc_matrix(void* h, int64_t G, const double* pts, const double* w, const double* vrho,
+                  const double* vgrad, double* V) {
+  or_ctx* c = (or_ctx*)h;
+  int n = c->nbf;
+  for (size_t i = 0; i < (size_t)n * n; ++i) V[i] = 0.0;
+#pragma omp parallel
+  {
+    double* phi = (double*)malloc(sizeof(double) * n);
+    double* dphi = (double*)malloc(sizeof(double) * 3 * n);
+    double* Vt = (double*)calloc((size_t)n * n, sizeof(double));
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t g = 0; g < G; ++g) {
+      if (w[g] == 0.0) continue;
+      or_xc_ao(h, pts + 3 * g, phi, dphi);
+      const double* vg = vgrad + 3 * g;
+      for (int m = 0; m < n; ++m)
+        for (int v = 0; v < n; ++v) {
+          double pp = phi[m] * phi[v];
+          double gg = vg[0] * (dphi[m] * phi[v] + phi[m] * dphi[v]) +
+                      vg[1] * (dphi[n + m] * phi[v] + phi[m] * dphi[n + v]) +
+                      vg[2] * (dphi[2 * n + m] * phi[v] + phi[m] * dphi[2 * n + v]);
+          Vt[(size_t)m * n + v] += w[g] * (vrho[g] * pp + gg);
+        }
+    }
+#pragma omp critical
+    for (size_t i = 0; i < (size_t)n * n; ++i) V[i] += Vt[i];
+    free(phi);
+    free(dphi);
+    free(Vt);
+  }
+}
+
+/* Selected elements out[e] = V_{mn[2e], mn[2e+1]} of or_xc_matrix, each summed
+ * over every point (shell values of the two shells only): for large grids */
+void or_xc_matrix_elements(void* h, int64_t G, const double* pts, const double* w, const double* vrho,
+                           const double* vgrad, int nel, const int32_t* mn, double* out) {
+  or_ctx* c = (or_ctx*)h;
+  int* shell_of = (int*)malloc(sizeof(int) * c->nbf);
+  for (int s = 0; s < c->nshell; ++s)
+    for (int m = c->aoff[s]; m < c->aoff[s + 1]; ++m) shell_of[m] = s;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int e = 0; e < nel; ++e) {
+    int m = mn[2 * e], v = mn[2 * e + 1], sm = shell_of[m], sv = shell_of[v];
+    int im = m - c->aoff[sm], iv = v - c->aoff[sv], nm = ncart(c->l[sm]), nv = ncart(c->l[sv]);
+    double pm[10], dm[30], pv[10], dv[30];
+    long double acc = 0.0L;
+    for (int64_t g = 0; g < G; ++g) {
+      if (w[g] == 0.0) continue;
+      ao_shell(c, sm, pts + 3 * g, pm, dm);
+      ao_shell(c, sv, pts + 3 * g, pv, dv);
+      const double* vg = vgrad + 3 * g;
+      double gg = 0.0;
+      for (int x = 0; x < 3; ++x) gg += vg[x] * (dm[x * nm + im] * pv[iv] + pm[im] * dv[x * nv + iv]);
+      acc += (long double)w[g] * (vrho[g] * pm[im] * pv[iv] + gg);
+    }
+    out[e] = (double)acc;
+  }
+  free(shell_of);
+}
