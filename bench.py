@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -39,15 +40,17 @@ import numpy as np  # noqa: E402
 METRIC = "J+K build time & ERI quartets/s: mixed vs FP64 on GB300 at ≤1e-6 Eh error"
 UNIT = "quartets/s"
 WORKLOAD_ID = 1
+XC_NRAD, XC_NTHETA = 32, 16  # exchange-correlation grid of the XC leg
 WORKLOAD_DESC = ("60 atoms in a seeded random packing (min distance 2.0 bohr): 40 light 2s1p + 20 heavy "
                  "4s3p2d1f Cartesian shells, 900 basis functions, s/p 3-primitive contractions, D = C C^T "
                  "with C a random orthonormal 900x120, seed 1001")
 THRESH = 1e-12
 # FP32/FP64 tier threshold on the density-weighted Schwarz bound.  The paper's
-# default is 1e-5; 1e-3 keeps the measured energy error near 1e-9 Eh on this
-# workload (1000x inside the 1e-6 Eh budget; a sweep from 1e-5 to all-FP32 put
-# 1e-1 at 5e-7 Eh), and every run reports the measured error against the FP64 path.
-TAU = 1e-3
+# default is 1e-5; on this workload a sweep on GB300 gave |dE_J| 1.4e-9 Eh at
+# 1e-3 (1109 ms), 4.6e-8 at 1e-2 (922 ms) and 5.7e-7 at 1e-1 (850 ms), so 1e-2
+# keeps the error about 20x inside the 1e-6 Eh budget; every run reports the
+# measured error against the FP64 path.
+TAU = 1e-2
 # peaks for the ALU roofline: FP32 = 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz;
 # FP64 = GB300 nominal dense FP64 rate
 PEAK_TFLOPS = {0: 1.25, 1: 80.5}
@@ -170,26 +173,40 @@ def oracle_rate(basis, quartets, target_s):
     return n / dt, n, dt, oracle.max_threads()
 
 
+# sources of the J/K class kernels and their launches: the DRAM traffic figures
+# of profiles/ hold only while these are unchanged
+JK_SOURCES = ["common.cuh", "kernels.cuh", "kernels_a.cuh", "kernels_b.cuh", "dispatch.cuh", "units.h",
+              "k_unit.cu", "plan.cu", "plan.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "jk_dram_traffic_w1.md")
+
+
 def source_hash():
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2406_14920_gb300", "csrc"))):
-        if f.endswith((".cuh", ".cu")):
-            h.update(open(os.path.join(ROOT, "paper_2406_14920_gb300", "csrc", f), "rb").read())
+    for f in JK_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2406_14920_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def traffic_for(X, Y, tier):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
+def traffic_for(X, Y, tier, path=TRAFFIC_FILE):
+    """DRAM bytes per full-size launch of class pair (X, Y) and tier from the
+    committed ncu summary (rows `| (xy|zw) | fp32 | bytes |` under a line
+    `source_hash: <hash>`), if it was taken on the current kernel sources."""
+    if not os.path.exists(path):
         return None
-    try:
-        d = json.load(open(p))
-    except ValueError:
+    txt = open(path).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]{16})", txt)
+    if not m or m.group(1) != source_hash():
         return None
-    if d.get("source_hash") != source_hash():
-        return None
-    return d.get("kernels", {}).get(f"{CLASS_NAMES[X]}|{CLASS_NAMES[Y]}|{tier}")
+    name = f"({CLASS_NAMES[X]}|{CLASS_NAMES[Y]})"
+    tname = {0: "fp64", 1: "fp32"}.get(tier, str(tier))
+    for line in txt.splitlines():
+        cells = [c.strip().replace("\\|", "|") for c in line.strip().strip("|").split(" | ")]
+        if len(cells) >= 3 and cells[0] == name and cells[1] == tname:
+            try:
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
 
 
 TIER_NAMES = {0: "fp64", 1: "fp32", 2: "grad-fp64", 3: "jengine-fp64"}
@@ -399,6 +416,7 @@ def run_ours(args, rank, world, local_rank):
         out["jengine"] = run_jengine_leg(args, dev, peak_meas)
         out["longrange"] = run_longrange_leg(args, dev)
         out["nuclear"] = run_nuclear_leg(args, dev)
+        out["xc"] = run_xc_leg(args, dev, peak_meas)
         if args.shard_balance:
             out["shard_balance"] = run_shard_leg(args, dev)
         if args.grad_steps > 0:
@@ -630,6 +648,59 @@ def run_nuclear_leg(args, dev):
             "max_abs_net_force": float((gR.sum(dim=0) + gC.sum(dim=0)).abs().max())}
 
 
+def run_xc_leg(args, dev, peaks):
+    """Exchange-correlation quadrature (Sec. 2.6) for the bench workload's basis
+    and density: Becke-partitioned grid of 32 radial x 16 x 32 angular points
+    per atom (983,040 points), Becke-88 exchange, FP64.  Times the grid set-up
+    (points, weights, blocks, screening and resident basis values) once, then
+    the density alone and the whole eri_xc (density, functional, matrix) per
+    step; FLOPs are the two block contractions (eri_xc_stats)."""
+    import torch
+    import paper_2406_14920_gb300 as eri
+    import workloads as W
+    basis, D = W.workload(WORKLOAD_ID)
+    plan = eri.Plan(basis, thresh=THRESH, device=dev.index)
+    stream = torch.cuda.current_stream(dev)
+    Dt = torch.from_numpy(D).to(dev)
+    torch.cuda.synchronize()
+    e0, e1, e2 = _events(stream)
+    e0.record(stream)
+    G = plan.xc_grid(XC_NRAD, XC_NTHETA, cap_bytes=float(args.xc_cap_gib) * 2 ** 30)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    setup_ms = e0.elapsed_time(e1)
+    st = plan.xc_stats()
+    E, V = plan.xc(Dt, functional=eri.ERI_XC_B88)
+    rho, _ = plan.xc_density(Dt)
+    torch.cuda.synchronize()
+    e0, e1, e2 = _events(stream)
+    e0.record(stream)
+    for _ in range(args.aux_steps):
+        plan.xc_density(Dt)
+    e1.record(stream)
+    for _ in range(args.aux_steps):
+        E, V = plan.xc(Dt, functional=eri.ERI_XC_B88, V=V)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    ms_d, ms_x = e0.elapsed_time(e1) / args.aux_steps, e1.elapsed_time(e2) / args.aux_steps
+    pts, w = plan.xc_get_grid()
+    nel = float((w * rho).sum())
+    plan.close()
+    fl_d, fl_x = st["flops_density"], st["flops_density"] + st["flops_matrix"]
+    pk = peaks.get(0) if peaks else None
+    out = {"grid": f"{XC_NRAD} radial x {XC_NTHETA} x {2 * XC_NTHETA} angular per atom, Becke cells",
+           "points": G, "blocks": st["nblock"], "mean_block_functions": st["sum_block_functions"] / st["nblock"],
+           "resident_basis_values": bool(st["resident"]), "chunks": st["nchunk"],
+           "workspace_gib": st["workspace_bytes"] / 2 ** 30, "setup_ms": setup_ms, "density_ms": ms_d,
+           "xc_ms": ms_x, "steps": args.aux_steps, "functional": "Becke-88 exchange",
+           "E_xc": float(E.cpu()[0]), "electrons": nel, "density_tflops": fl_d / (ms_d * 1e9),
+           "xc_tflops": fl_x / (ms_x * 1e9)}
+    if pk:
+        out["density_frac_fp64_measured"] = fl_d / (ms_d * 1e9) / pk
+        out["xc_frac_fp64_measured"] = fl_x / (ms_x * 1e9) / pk
+    return out
+
+
 def run_batch(args, dev, flush):
     """Batched leg: molecules of the 64-molecule set in one plan, mixed precision,
     one CUDA-graph build per step, plus one batched gradient; against one FP64
@@ -774,6 +845,9 @@ def main():
     ap.add_argument("--shard-balance", type=lambda v: [int(x) for x in v.split(",") if x], default=[2, 4, 8],
                     help="share counts of the load-balance leg (comma list; empty to skip)")
     ap.add_argument("--grad-steps", type=int, default=1, help="timed gradient steps (after one warm-up pass)")
+    ap.add_argument("--xc-cap-gib", type=float, default=48.0,
+                    help="device memory for resident basis values of the XC leg (GiB)")
+    ap.add_argument("--xc-only", action="store_true", help="run only the exchange-correlation leg")
     ap.add_argument("--ncu-case", action="store_true",
                     help="small case for ncu section captures: the first 20 atoms of the workload, two mixed "
                          "builds and one gradient")
@@ -792,8 +866,22 @@ def main():
         for _ in range(2):
             plan.build_jk(Dt)
         plan.grad(Dt)
+        # exchange-correlation on a small grid of the same atoms (basis values resident)
+        G = plan.xc_grid(16, 8)
+        for _ in range(2):
+            plan.xc(Dt, functional=eri.ERI_XC_B88)
         torch.cuda.synchronize()
-        print(json.dumps({"ncu_case": True, "nbf": b2.nbf, "quartets": plan.stats()["quartets_k"]}))
+        print(json.dumps({"ncu_case": True, "nbf": b2.nbf, "quartets": plan.stats()["quartets_k"],
+                          "xc_points": G}))
+        return
+    if args.xc_only:
+        import torch
+        from paper_2406_14920_gb300.build import build
+        import paper_2406_14920_gb300 as eri
+        build()
+        dev = torch.device("cuda", local_rank)
+        peaks = {0: eri.peak_probe(eri.ERI_FP64, 4000)}
+        print(json.dumps({"xc": run_xc_leg(args, dev, peaks)}))
         return
     if args.impl == "reference":
         if rank == 0:

@@ -396,6 +396,84 @@ int eri_nuclear_grad(eri_plan_t* plan, const double* D, int32_t ncharge, const d
                      double* dEdR, double* dEdC, void* stream);
 
 /*
+ * Exchange-correlation quadrature on a molecular grid (Sec. 2.6; the paper's
+ * four steps: grid, density, functional, matrix).  Plans of one molecule only
+ * (a batched plan gets ERI_EUNSUPPORTED).  All arithmetic is FP64.
+ *
+ * eri_xc_grid builds the plan's grid on the device (step 1): for every atom,
+ * nrad radial nodes (Gauss-Chebyshev of the second kind, x_i = cos(i pi /
+ * (nrad+1)), mapped by Becke's r = radius (1+x)/(1-x), weight
+ * (pi/(nrad+1)) sin(theta_i) r^2 dr/dx) times ntheta Gauss-Legendre nodes in
+ * cos(theta) (ascending) times 2 ntheta azimuths phi_k = 2 pi (k+1/2)/(2 ntheta)
+ * (trapezoid), each weighted by Becke's fuzzy-cell partition (equal cell sizes,
+ * three iterations of p(mu) = (3 mu - mu^3)/2).  Point g = ((atom * nrad + i) *
+ * ntheta + j) * 2 ntheta + k; npoints (host, may be NULL) receives
+ * natom * nrad * 2 ntheta^2.  It also groups the points into blocks of at most
+ * 128 (per atom: adjacent radial shells x one eighth of the sphere), finds the
+ * shells that reach each block, and evaluates the basis functions and their
+ * gradients there; when those values fit in cap_bytes (<= 0: 16 GiB) they stay
+ * resident in device memory for every later call, otherwise each call
+ * recomputes them in chunks of that size.  Waits for the stream (host
+ * bookkeeping of the block sizes).  The grid follows eri_plan_set_coords: it is
+ * rebuilt, with the same parameters, at the next XC call after a change.
+ * Requires 2 <= nrad <= 1000, 2 <= ntheta <= 64 with ntheta even, radius > 0,
+ * and fewer than 2^31 points.
+ * Errors: ERI_EINVAL, ERI_EUNSUPPORTED, ERI_ENOMEM, ERI_ECUDA.
+ */
+int eri_xc_grid(eri_plan_t* plan, int32_t nrad, int32_t ntheta, double radius, double cap_bytes, int64_t* npoints,
+                void* stream);
+
+/* Copy the grid out: points (DEVICE, npoints x 3, bohr) and weights (DEVICE,
+ * npoints); either may be NULL.  Errors: ERI_EINVAL (no grid), ERI_ECUDA. */
+int eri_xc_get_grid(eri_plan_t* plan, double* points, double* weights, void* stream);
+
+/*
+ * Step 2: rho_g = sum_mn D_mn phi_m(r_g) phi_n(r_g) (Eq. xc_density_0) and
+ * grad rho_g = sum_mn D_mn grad(phi_m phi_n)(r_g) (Eq. xc_density_1) at every
+ * grid point.  D: DEVICE, nbf x nbf, symmetric (AO order, unit-normalised
+ * functions as for eri_build_jk); rho: DEVICE, npoints; grad_rho: DEVICE,
+ * npoints x 3 or NULL; both overwritten.  Basis functions beyond their
+ * extent (all components and gradients below 1e-15) are dropped per block.
+ * Errors: ERI_EINVAL (NULL, no grid), ERI_EUNSUPPORTED, ERI_ECUDA.
+ */
+int eri_xc_density(eri_plan_t* plan, const double* D, double* rho, double* grad_rho, void* stream);
+
+/*
+ * Step 4 for given point potentials: V_mn = sum_g w_g [vrho_g phi_m phi_n +
+ * vgrad_g . grad(phi_m phi_n)] (Eq. xc_grid_sum_0 + Eq. xc_grid_sum_1).
+ * vrho: DEVICE, npoints (d eps/d rho); vgrad: DEVICE, npoints x 3
+ * (d eps/d grad rho); V: DEVICE, nbf x nbf, overwritten (symmetric).
+ * Errors: as eri_xc_density.
+ */
+int eri_xc_matrix(eri_plan_t* plan, const double* vrho, const double* vgrad, double* V, void* stream);
+
+#define ERI_XC_SLATER 1 /* closed-shell Slater (Dirac) exchange, eps = -(3/4)(3/pi)^(1/3) rho^(4/3) */
+#define ERI_XC_B88 2    /* Becke-88 exchange (beta = 0.0042) on the spin density rho/2 */
+
+/*
+ * Steps 2-4 with a built-in functional (step 3; the paper evaluates the
+ * functional on the CPU and names none): density and gradient, eps, v_rho and
+ * v_grad per point (points with rho < 1e-14 contribute nothing), then V as in
+ * eri_xc_matrix.  V: DEVICE, nbf x nbf, overwritten; Exc: DEVICE, one double,
+ * overwritten with E_xc = sum_g w_g eps_g (order of the partial sums not fixed).
+ * Errors: ERI_EINVAL (NULL, no grid, unknown functional), ERI_EUNSUPPORTED,
+ * ERI_ECUDA.
+ */
+int eri_xc(eri_plan_t* plan, const double* D, int32_t functional, double* V, double* Exc, void* stream);
+
+/* Shape of the plan's grid and the work of one density / matrix pass. */
+typedef struct {
+  int64_t npoints;
+  int32_t nblock, block_points, resident, nchunk;
+  double sum_block_functions;     /* sum over blocks of the significant functions n_b */
+  double sum_block_functions_sq;  /* sum over blocks of n_b^2 */
+  double workspace_bytes;         /* basis-value workspace */
+  double flops_density;           /* (2 n_b^2 + 8 n_b) * 128 summed over blocks: X = D_b Phi_b and rho, grad rho */
+  double flops_matrix;            /* the same for Z_b Phi_b^T and Z */
+} eri_xc_stats_t;
+int eri_xc_stats(eri_plan_t* plan, eri_xc_stats_t* stats);
+
+/*
  * Measurement utility (not a step of the method): the FP64 (precision =
  * ERI_FP64) or FP32 (ERI_MIXED) fused multiply-add rate of the current device,
  * in TFLOP/s (FMA = 2 FLOP), from one launch of independent FMA chains over

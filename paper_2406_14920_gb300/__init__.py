@@ -19,6 +19,8 @@ _lib = None
 
 ERI_FP64 = 0
 ERI_MIXED = 1
+ERI_XC_SLATER = 1
+ERI_XC_B88 = 2
 
 
 class EriError(RuntimeError):
@@ -53,6 +55,13 @@ class StatsT(C.Structure):
                 ("quartets_k_fp32", C.c_int64), ("flops_k", C.c_double), ("flops_j", C.c_double),
                 ("device_status", C.c_int32), ("quartets_k_guard", C.c_int64), ("quartets_k_screened", C.c_int64),
                 ("graph_branches", C.c_int32)]
+
+
+class XcStatsT(C.Structure):
+    _fields_ = [("npoints", C.c_int64), ("nblock", C.c_int32), ("block_points", C.c_int32),
+                ("resident", C.c_int32), ("nchunk", C.c_int32), ("sum_block_functions", C.c_double),
+                ("sum_block_functions_sq", C.c_double), ("workspace_bytes", C.c_double),
+                ("flops_density", C.c_double), ("flops_matrix", C.c_double)]
 
 
 def lib():
@@ -90,6 +99,12 @@ def lib():
         L.eri_peak_probe.argtypes = [i32, i32, C.POINTER(C.c_double), vp]
         L.eri_nuclear.argtypes = [vp, i32, vp, vp, vp, vp]
         L.eri_nuclear_grad.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
+        L.eri_xc_grid.argtypes = [vp, i32, i32, C.c_double, C.c_double, C.POINTER(C.c_int64), vp]
+        L.eri_xc_get_grid.argtypes = [vp, vp, vp, vp]
+        L.eri_xc_density.argtypes = [vp, vp, vp, vp, vp]
+        L.eri_xc_matrix.argtypes = [vp, vp, vp, vp, vp]
+        L.eri_xc.argtypes = [vp, vp, i32, vp, vp, vp]
+        L.eri_xc_stats.argtypes = [vp, C.POINTER(XcStatsT)]
         L.eri_plan_destroy.argtypes = [vp]
         L.eri_strerror.argtypes = [C.c_int]
         L.eri_strerror.restype = C.c_char_p
@@ -211,6 +226,7 @@ class Plan:
                                  self.atom_off.ctypes.data_as(C.POINTER(C.c_int32))), "eri_plan_layout")
         self.nbf = int(self.mat_n.sum())
         self.nmat = int(self.mat_off[-1])
+        self.xc_npoints = 0
         self.natom = int(self.atom_off[-1])
         self.npair = sum(b.nshell * (b.nshell + 1) // 2 for b in bases)
         # geometry bookkeeping for JKEnergy: geom_version counts set_coords calls,
@@ -374,6 +390,60 @@ class Plan:
         _check(lib().eri_nuclear_grad(self.h, _ptr(D), nc, _ptr(q), _ptr(xyz), _ptr(gR), _ptr(gC),
                                       _stream_ptr(stream)), "eri_nuclear_grad")
         return gR, gC
+
+    def xc_grid(self, nrad, ntheta, radius=1.0, cap_bytes=0.0, stream=None):
+        """Build the plan's exchange-correlation grid on the device (eri_xc_grid);
+        returns the number of points."""
+        n = C.c_int64()
+        _check(lib().eri_xc_grid(self.h, int(nrad), int(ntheta), float(radius), float(cap_bytes), C.byref(n),
+                                 _stream_ptr(stream)), "eri_xc_grid")
+        self.xc_npoints = int(n.value)
+        return self.xc_npoints
+
+    def xc_get_grid(self, stream=None):
+        """(points [G, 3], weights [G]) of the grid, on the plan's device."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        pts = torch.empty((self.xc_npoints, 3), dtype=torch.float64, device=dev)
+        w = torch.empty(self.xc_npoints, dtype=torch.float64, device=dev)
+        _check(lib().eri_xc_get_grid(self.h, _ptr(pts), _ptr(w), _stream_ptr(stream)), "eri_xc_get_grid")
+        return pts, w
+
+    def xc_density(self, D, want_grad=True, stream=None):
+        """(rho [G], grad rho [G, 3] or None) on the grid (eri_xc_density)."""
+        import torch
+        _require(D, self.nmat, "D", self.device)
+        rho = torch.empty(self.xc_npoints, dtype=torch.float64, device=D.device)
+        grad = torch.empty((self.xc_npoints, 3), dtype=torch.float64, device=D.device) if want_grad else None
+        _check(lib().eri_xc_density(self.h, _ptr(D), _ptr(rho), _ptr(grad), _stream_ptr(stream)), "eri_xc_density")
+        return rho, grad
+
+    def xc_matrix(self, vrho, vgrad, V=None, stream=None):
+        """V_mn for given point potentials vrho [G], vgrad [G, 3] (eri_xc_matrix)."""
+        import torch
+        if V is None:
+            V = torch.empty(self._mat_shape(), dtype=torch.float64, device=vrho.device)
+        _require(vrho, self.xc_npoints, "vrho", self.device)
+        _require(vgrad, 3 * self.xc_npoints, "vgrad", self.device)
+        _require(V, self.nmat, "V", self.device)
+        _check(lib().eri_xc_matrix(self.h, _ptr(vrho), _ptr(vgrad), _ptr(V), _stream_ptr(stream)), "eri_xc_matrix")
+        return V
+
+    def xc(self, D, functional=ERI_XC_B88, V=None, stream=None):
+        """(E_xc [1] device tensor, V_xc) with a built-in functional (eri_xc)."""
+        import torch
+        _require(D, self.nmat, "D", self.device)
+        if V is None:
+            V = torch.empty(self._mat_shape(), dtype=torch.float64, device=D.device)
+        _require(V, self.nmat, "V", self.device)
+        E = torch.empty(1, dtype=torch.float64, device=D.device)
+        _check(lib().eri_xc(self.h, _ptr(D), int(functional), _ptr(V), _ptr(E), _stream_ptr(stream)), "eri_xc")
+        return E, V
+
+    def xc_stats(self):
+        s = XcStatsT()
+        _check(lib().eri_xc_stats(self.h, C.byref(s)), "eri_xc_stats")
+        return {k: getattr(s, k) for k, _ in XcStatsT._fields_}
 
     def lists(self):
         Q = np.zeros(self.npair, np.float32)

@@ -871,6 +871,7 @@ void eri_plan_impl::release() {
                   d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp, d_ea,
                   d_mat_off, d_mat_n, d_aobase, d_pbase, d_pmol, d_shloc, d_ccm, d_segloc, d_Dpf,
                   d_nuc_list, d_nuc_goff, d_nuc_dens, d_counters2, d_q4};
+  xc_release();
   for (auto& e : prof_events) cudaEventDestroy(e);
   prof_events.clear();
   if (gexec) cudaGraphExecDestroy(gexec);
@@ -1361,6 +1362,7 @@ extern "C" int eri_plan_set_coords(eri_plan_t* plan, const double* coords_dev, i
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaSetDevice(P->device));
   CK(cudaMemcpyAsync(P->d_coords, coords_dev, sizeof(double) * 3 * P->natom, cudaMemcpyDeviceToDevice, s));
+  ++P->geom_serial;  // an exchange-correlation grid follows the atoms at its next use
   return P->geometry(s, freeze_lists == 0);
 }
 

@@ -127,6 +127,16 @@ def test_shard_and_layout_null_arguments(eri):
     assert L.eri_get_stats(None, None) == -1
 
 
+def test_xc_null_arguments(eri):
+    L = eri.lib()
+    assert L.eri_xc_grid(None, 24, 8, C.c_double(1.0), C.c_double(0.0), None, None) == -1
+    assert L.eri_xc_get_grid(None, None, None, None) == -1
+    assert L.eri_xc_density(None, None, None, None, None) == -1
+    assert L.eri_xc_matrix(None, None, None, None, None) == -1
+    assert L.eri_xc(None, None, 1, None, None, None) == -1
+    assert L.eri_xc_stats(None, None) == -1
+
+
 def test_binding_checks_coordinate_shapes(eri):
     """The binding refuses coordinates that do not match the basis before any
     call into the library (which would read natom x 3 doubles)."""

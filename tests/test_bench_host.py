@@ -43,3 +43,18 @@ def test_class_rows_gradient_and_jengine_tiers_use_fp64_peak():
     assert abs(rows[0][3] - 0.5) < 1e-9 and abs(rows[0][4] - 0.4) < 1e-9
     rows_m = bench.class_rows(prof, steps=1, peaks={0: 1.0, 1: 80.0})
     assert abs(rows_m[1][4] - 0.2) < 1e-9
+
+
+def test_traffic_reader(tmp_path):
+    """roofline.traffic comes from the committed ncu summary only while the J/K
+    kernel sources hash to the value recorded in it."""
+    import bench
+    h = bench.source_hash()
+    p = tmp_path / "t.md"
+    p.write_text(f"source_hash: {h}\n\n| kernel | tier | dram bytes per launch |\n|---|---|---:|\n"
+                 "| (fp\\|dp) | fp32 | 2500000.0 |\n| (ss\\|ss) | fp64 | 10 |\n")
+    assert bench.traffic_for(7, 4, 1, path=str(p)) == 2500000.0
+    assert bench.traffic_for(0, 0, 0, path=str(p)) == 10.0
+    assert bench.traffic_for(7, 4, 0, path=str(p)) is None
+    p.write_text("source_hash: 0000000000000000\n| (fp\\|dp) | fp32 | 2500000.0 |\n")
+    assert bench.traffic_for(7, 4, 1, path=str(p)) is None
