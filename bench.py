@@ -180,6 +180,38 @@ JK_SOURCES = ["common.cuh", "kernels.cuh", "kernels_a.cuh", "kernels_b.cuh", "di
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "jk_dram_traffic_w1.md")
 
 
+def full_build_w0(local_rank):
+    """The whole J/K assembly of the 75-basis-function system (3 atoms 3s2p1d1f,
+    seed 1000) by the oracle on the host cores (Schwarz list, 8-fold scatter,
+    energies) beside the GPU FP64 build of the same system."""
+    import oracle
+    import torch
+    import paper_2406_14920_gb300 as eri
+    import workloads as W
+    basis, D = W.workload(0)
+    t0 = time.perf_counter()
+    o = oracle.Oracle(basis)
+    Q = o.schwarz()
+    Jo, Ko = o.jk(D, THRESH, Q)
+    o.energy(D, Jo, Ko)
+    cpu_s = time.perf_counter() - t0
+    plan = eri.Plan(basis, thresh=THRESH, device=local_rank)
+    Dt = torch.from_numpy(D).cuda(local_rank)
+    J, K = plan.build_jk(Dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        plan.build_jk(Dt, J, K)
+    e1.record()
+    torch.cuda.synchronize()
+    gpu_ms = e0.elapsed_time(e1) / 5
+    diff = max(float(np.abs(J.cpu().numpy() - Jo).max()), float(np.abs(K.cpu().numpy() - Ko).max()))
+    plan.close()
+    return {"workload": "3 atoms 3s2p1d1f, 75 basis functions, seed 1000", "oracle_s": cpu_s,
+            "oracle_cores": oracle.max_threads(), "gpu_fp64_ms": gpu_ms, "max_abs_diff": diff}
+
+
 def source_hash():
     h = hashlib.sha256()
     for f in JK_SOURCES:
@@ -429,6 +461,8 @@ def run_ours(args, rank, world, local_rank):
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{ns} seeded uniformly sampled significant canonical shell quartets of "
                                          f"this workload, contracted ERI blocks in FP64 ({dt:.1f} s)"}
+        if world == 1:
+            out["cpu_baseline"]["full_build_w0"] = full_build_w0(local_rank)
     return out
 
 
