@@ -241,13 +241,13 @@ def traffic_for(X, Y, tier, path=TRAFFIC_FILE):
     return None
 
 
-TIER_NAMES = {0: "fp64", 1: "fp32", 2: "grad-fp64", 3: "jengine-fp64"}
+TIER_NAMES = {0: "fp64", 1: "fp32", 2: "grad-fp64", 3: "jengine-fp64", 4: "grad-fp32", 5: "jengine-fp32"}
 
 
 def tier_peak(tier, peaks=None):
-    """ALU peak of a profile tier: FP32 for tier 1, FP64 for the rest (nominal, or `peaks` if given)."""
+    """ALU peak of a profile tier: FP32 for the FP32 tiers (1, 4, 5), FP64 for the rest (nominal, or `peaks` if given)."""
     p = peaks if peaks is not None else PEAK_TFLOPS
-    return p[1] if tier == 1 else p[0]
+    return p[1] if tier in (1, 4, 5) else p[0]
 
 
 def class_rows(prof, steps, peaks=None):
@@ -559,12 +559,31 @@ def run_jengine_leg(args, dev, peaks):
     ms = e0.elapsed_time(e1) / args.aux_steps
     prof = [r for r in plan.profile() if r["tier"] == 3]
     nq = plan.stats()["quartets_j"]
+    ej64 = 0.5 * float((Dt * J).sum())
+    # the same J-only build in mixed precision (FP32 tier below the bench tier bound)
+    plan.set_tau(args.tau)
+    plan.build_jk(Dt, J, None, want_k=False, precision=eri.ERI_MIXED)
+    torch.cuda.synchronize()
+    plan.profile()
+    e0, e1, _ = _events(stream)
+    e0.record(stream)
+    for _ in range(args.aux_steps):
+        plan.build_jk(Dt, J, None, want_k=False, precision=eri.ERI_MIXED)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_mx = e0.elapsed_time(e1) / args.aux_steps
+    st = plan.stats()
+    dej = 0.5 * float((Dt * J).sum()) - ej64
+    plan.profile()
     plan.close()
     fl = sum(r["flops"] for r in prof) / args.aux_steps
     kms = sum(r["ms"] for r in prof) / args.aux_steps
     tf = fl / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
     return {"ms_per_step": ms, "ordered_pair_pairs_per_s": nq / (ms * 1e-3), "steps": args.aux_steps,
             "tflops": round(tf, 4), "frac_fp64_measured": round(tf / peaks[0], 4),
+            "mixed": {"ms_per_step": ms_mx, "ordered_pair_pairs_per_s": nq / (ms_mx * 1e-3), "tau": args.tau,
+                      "fp32_share": st["quartets_j_fp32"] / max(1, nq), "dE_J_vs_fp64": dej,
+                      "speedup_vs_fp64": ms / ms_mx},
             "class_roofline": {"columns": ["class", "tier", "ms_per_step", "tflops", "frac_of_measured_peak"],
                                "rows": class_rows(prof, args.aux_steps, peaks)[:16]}}
 

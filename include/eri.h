@@ -44,7 +44,7 @@ extern "C" {
 #define ERI_ENOMEM (-2)       /* device or host allocation failed */
 #define ERI_ECUDA (-3)        /* a CUDA runtime call failed */
 #define ERI_EUNSUPPORTED (-4) /* valid request this build cannot serve */
-#define ERI_ETIMEOUT (-5)     /* a bounded device wait gave up */
+#define ERI_ETIMEOUT (-5)     /* reserved: a bounded device wait gave up (no kernel of this build waits on another) */
 #define ERI_EDEVICE (-6)      /* a device-side check failed (status word set) */
 
 #define ERI_FP64 0  /* every quartet in FP64 */
@@ -105,6 +105,7 @@ typedef struct {
                                or a primitive prefactor product above 1e18 would overflow FP32) */
   int64_t quartets_k_screened; /* of quartets_k, dropped by the density screen in the last build */
   int32_t graph_branches;       /* branches of the current graph build (1 serial, 4 forked; 0: none) */
+  int64_t quartets_j_fp32;      /* of quartets_j, evaluated in FP32 by the last J-engine build (mixed) */
 } eri_stats_t;
 
 /* Fill opts with the defaults listed above.  Host only. */
@@ -160,8 +161,10 @@ int eri_plan_set_coords(eri_plan_t* plan, const double* coords_dev, int32_t free
  * whose Schwarz bound Q_ab Q_cd >= thresh (Eq. j_definition, Eq. k_definition,
  * Eq. kernel_upperbound).  D, J, K: device, nbf*nbf (packed per molecule for
  * a batched plan).  D must be symmetric.  J or K may be NULL to
- * skip that matrix (J alone runs only the J-engine, in FP64 whatever the
- * precision argument, unless opts.j_engine = 0).  thresh < 0 keeps the
+ * skip that matrix (J alone runs only the J-engine, Eq. j_formula, unless
+ * opts.j_engine = 0; with ERI_MIXED its ordered (bra, ket) items are split by
+ * the same tier test and the FP32 tier reads an FP32 copy of the Hermite
+ * density, both tiers adding into the FP64 Hermite J).  thresh < 0 keeps the
  * plan's threshold; another value rebuilds the lists first (with a host wait).
  * precision: ERI_FP64 or ERI_MIXED (tier split at the plan's mixed_tau: a device
  * pass writes each class pair's FP64-tier and FP32-tier quartets to two compacted

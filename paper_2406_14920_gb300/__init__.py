@@ -54,7 +54,7 @@ class StatsT(C.Structure):
                 ("quartets_k", C.c_int64), ("quartets_j", C.c_int64), ("prim_quartets_k", C.c_int64),
                 ("quartets_k_fp32", C.c_int64), ("flops_k", C.c_double), ("flops_j", C.c_double),
                 ("device_status", C.c_int32), ("quartets_k_guard", C.c_int64), ("quartets_k_screened", C.c_int64),
-                ("graph_branches", C.c_int32)]
+                ("graph_branches", C.c_int32), ("quartets_j_fp32", C.c_int64)]
 
 
 class XcStatsT(C.Structure):

@@ -112,8 +112,8 @@ cudaError_t launch_grad_unit(int y, const GradArgs& a, cudaStream_t s, int nsm) 
 template <int LAB, int LCD, typename T>
 cudaError_t launch_j_t(const JArgs& a, cudaStream_t s, int nsm) {
   if (a.wl.total <= 0) return cudaSuccess;
-  if constexpr (sizeof(T) == 8 && use_j_thread(LAB, LCD)) {
-    auto kern = j_thread_kernel<LAB, LCD>;
+  if constexpr (use_j_thread(LAB, LCD)) {
+    auto kern = j_thread_kernel<LAB, LCD, T>;
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, 0);
     if (e != cudaSuccess) return e;

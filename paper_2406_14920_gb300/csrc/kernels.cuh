@@ -96,12 +96,23 @@ struct JArgs {
   BoysTabs bt;
   const RStep* rsteps;
   const double* Dherm;  // Hermite density per ket primitive pair (sign (-1)^|Q| folded in)
-  double* Jherm;        // Hermite J per bra primitive pair (accumulated)
+  const float* Dhermf;  // the same in FP32, read by the FP32 tier (no conversions on the FP64 pipe)
+  double* Jherm;        // Hermite J per bra primitive pair (accumulated in FP64 by both tiers)
   double omega2;        // erf(omega r)/r: omega^2 (0 = Coulomb)
   float omega2f;
   int det;              // 1: fixed-point Jherm (deterministic builds)
   unsigned long long* counter;  // items, primitive quartets, bra primitives of this launch (may be null)
+  // mixed precision: the launch runs the compacted list of its tier, item i =
+  // (bra position items[i].x, ket position items[i].y), *nitems of them.
+  // Null: items are positions in wl.
+  const int2* items;
+  const unsigned int* nitems;
 };
+
+// Hermite density of a J-engine launch in its precision
+template <typename T> __device__ __forceinline__ const T* hdens(const JArgs& a);
+template <> __device__ __forceinline__ const double* hdens<double>(const JArgs& a) { return a.Dherm; }
+template <> __device__ __forceinline__ const float* hdens<float>(const JArgs& a) { return a.Dhermf; }
 
 // omega^2 of a launch in its precision
 template <typename T, typename A> __device__ __forceinline__ T om2(const A& a);
@@ -253,16 +264,27 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
     }
   }
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t total = a.wl.total;
+  const bool compact = a.items != nullptr;
+  const int64_t total = compact ? (int64_t)__ldg(a.nitems) : a.wl.total;
+  const int64_t first = compact ? 0 : a.wl.first;
+  const int nshard = compact ? 1 : a.wl.nshard, shard = compact ? 0 : a.wl.shard;
   unsigned long long done = 0, doneq = 0, doneb = 0;
-  const int64_t tile = a.wl.tile, ntiles = (total - a.wl.first + tile - 1) / tile;
-  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * a.wl.nshard + a.wl.shard; tl < ntiles;
-       tl += nwarps * a.wl.nshard) {
-  const int64_t i0 = a.wl.first + tl * tile, i1 = i0 + tile < total ? i0 + tile : total;
-  BraCursor cur(a.wl, i0);
+  const int64_t tile = a.wl.tile, ntiles = (total - first + tile - 1) / tile;
+  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * nshard + shard; tl < ntiles;
+       tl += nwarps * nshard) {
+  const int64_t i0 = first + tl * tile, i1 = i0 + tile < total ? i0 + tile : total;
+  BraCursor cur;
+  if (!compact) cur.seek(a.wl, i0);
   for (int64_t item = i0; item < i1; ++item) {
-    const int ik = cur.at(a.wl, item);
-    const int ib = cur.ib;
+    int ib, ik;
+    if (compact) {
+      const int2 v = __ldg(a.items + item);
+      ib = v.x;
+      ik = v.y;
+    } else {
+      ik = cur.at(a.wl, item);
+      ib = cur.ib;
+    }
     const int pb_id = __ldg(a.wl.bra + ib);
     const int mol = __ldg(a.sp.pmol + pb_id);
     const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
@@ -289,7 +311,7 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
         T F[L + 1];
         Boys<T>::template eval<L>(rho * (X * X + Y * Y + Z * Z), a.bt, F);
         r_build_warp<L, T>(F, pref, X, Y, Z, T(-2) * rho, a.rsteps, ping0, ping1, box, lane);
-        const double* dq = a.Dherm + hk + (size_t)pk * HCD;
+        const T* dq = hdens<T>(a) + hk + (size_t)pk * HCD;
 #pragma unroll
         for (int j = 0; j < S::NPS; ++j) {
           const int P = lane + 32 * j;
@@ -301,7 +323,7 @@ __global__ void __launch_bounds__(128) j_warp_kernel(JArgs a) {
               for (int u = 0; u <= LCD - t; ++u) {
                 const T* r = box + pbase[j] + t * B * B + u * B;
 #pragma unroll
-                for (int v = 0; v <= LCD - t - u; ++v) s = fma(r[v], ldT<T>(dq + herm_index(t, u, v)), s);
+                for (int v = 0; v <= LCD - t - u; ++v) s = fma(r[v], __ldg(dq + herm_index(t, u, v)), s);
               }
             acc[j] += s;
           }
@@ -331,30 +353,43 @@ __host__ __device__ constexpr bool use_j_thread(int lab, int lcd) {
 
 // J-engine (Eq. j_formula), one ordered (bra, ket) shell-pair item per lane:
 // for each bra primitive pair, J_P += sum_{ket prims} sum_Q R_{P+Q} D_Q with
-// every Hermite index a compile-time constant.  The lists are bra-major, so a
-// warp's 32 items usually share one bra pair: then J_P is summed over the warp
-// with shuffles and one lane adds it to the bra primitive's Hermite J (one
-// atomic per element instead of 32); otherwise each lane adds its own.
-template <int LAB, int LCD>
+// every Hermite index a compile-time constant, in the launch's precision (the
+// FP32 tier of a mixed build reads the FP32 pair data and Hermite density).
+// The lists are bra-major, so a warp's 32 items usually share one bra pair:
+// then J_P is summed over the warp with shuffles and one lane adds it to the
+// bra primitive's Hermite J (one FP64 atomic per element instead of 32);
+// otherwise each lane adds its own.
+template <int LAB, int LCD, typename T>
 __global__ void __launch_bounds__(128) j_thread_kernel(JArgs a) {
   constexpr int L = LAB + LCD, NR = nherm(L), HAB = nherm(LAB), HCD = nherm(LCD);
-  using T = double;
   const int lane = threadIdx.x & 31;
-  const int64_t total = a.wl.total, first = a.wl.first;
+  const bool compact = a.items != nullptr;
+  const int64_t total = compact ? (int64_t)__ldg(a.nitems) : a.wl.total;
+  const int64_t first = compact ? 0 : a.wl.first;
+  const int nshard = compact ? 1 : a.wl.nshard, shard = compact ? 0 : a.wl.shard;
   const int64_t span = 32 * (int64_t)a.wl.tile, ntiles = (total - first + span - 1) / span;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long done = 0, doneq = 0, doneb = 0;
-  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * a.wl.nshard + a.wl.shard;
-       tl < ntiles; tl += nwarps * a.wl.nshard) {
+  for (int64_t tl = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * nshard + shard;
+       tl < ntiles; tl += nwarps * nshard) {
     const int64_t t0 = first + tl * span, i1 = t0 + span < total ? t0 + span : total;
-    BraCursor cur(a.wl, t0 + lane < i1 ? t0 + lane : t0);
+    BraCursor cur;
+    if (!compact) cur.seek(a.wl, t0 + lane < i1 ? t0 + lane : t0);
     for (int64_t base = t0; base < i1; base += 32) {  // uniform over the warp
       const int64_t item = base + lane;
       const bool ok = item < i1;
       int pb_id = -1, npb = 0, offb = 0, hb = 0, npk = 0, offk = 0, hk = 0;
       if (ok) {
-        const int ik = cur.at(a.wl, item);
-        pb_id = __ldg(a.wl.bra + cur.ib);
+        int ib, ik;
+        if (compact) {
+          const int2 v = __ldg(a.items + item);
+          ib = v.x;
+          ik = v.y;
+        } else {
+          ik = cur.at(a.wl, item);
+          ib = cur.ib;
+        }
+        pb_id = __ldg(a.wl.bra + ib);
         const int mol = __ldg(a.sp.pmol + pb_id);
         const int pk_id = __ldg(a.wl.ket + __ldg(a.wl.kseg + mol * NPAIRCLASS) + ik);
         npb = __ldg(a.sp.np + pb_id);
@@ -390,7 +425,7 @@ __global__ void __launch_bounds__(128) j_thread_kernel(JArgs a) {
             Boys<T>::template eval<L>(rho * (X * X + Y * Y + Z * Z), a.bt, F);
             T R[NR];
             r_build_reg<L, T>(F, pref, X, Y, Z, T(-2) * rho, R);
-            const double* dq = a.Dherm + hk + (size_t)pk * HCD;
+            const T* dq = hdens<T>(a) + hk + (size_t)pk * HCD;
             T Dq[HCD];
 #pragma unroll
             for (int q = 0; q < HCD; ++q) Dq[q] = __ldg(dq + q);
@@ -415,10 +450,10 @@ __global__ void __launch_bounds__(128) j_thread_kernel(JArgs a) {
           }
           if (lane == 0)
 #pragma unroll
-            for (int x = 0; x < HAB; ++x) acc_add(a.Jherm + hb + (size_t)pb * HAB + x, acc[x], a.det);
+            for (int x = 0; x < HAB; ++x) acc_add(a.Jherm + hb + (size_t)pb * HAB + x, (double)acc[x], a.det);
         } else if (ok) {
 #pragma unroll
-          for (int x = 0; x < HAB; ++x) acc_add(a.Jherm + hb + (size_t)pb * HAB + x, acc[x], a.det);
+          for (int x = 0; x < HAB; ++x) acc_add(a.Jherm + hb + (size_t)pb * HAB + x, (double)acc[x], a.det);
         }
       }
     }

@@ -526,7 +526,7 @@ __global__ void k_hermite_density(int npair, const int* __restrict__ s1, const i
                                   const int* __restrict__ sh_l, const int* __restrict__ pao1,
                                   const int* __restrict__ pao2, const int* __restrict__ pmol, MolMats mm,
                                   const int* __restrict__ sig, PairData pd, const double* __restrict__ Dp,
-                                  double* __restrict__ Dh) {
+                                  double* __restrict__ Dh, float* __restrict__ Dhf) {
   int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= npair || !sig[ip]) return;
   const int a = s1[ip], b = s2[ip], la = sh_l[a], lb = sh_l[b], H = nherm(la + lb);
@@ -555,6 +555,8 @@ __global__ void k_hermite_density(int npair, const int* __restrict__ s1, const i
             }
       }
     }
+    if (Dhf)  // FP32 copy for the FP32 tier of a mixed J-engine build
+      for (int q = 0; q < H; ++q) Dhf[hoff[ip] + (size_t)k * H + q] = (float)out[q];
   }
 }
 
@@ -870,7 +872,7 @@ void eri_plan_impl::release() {
                   d_kpre, d_jpre, d_ktot, d_jtot, d_kprim, d_boys64, d_boys32, d_rsteps, d_Dp, d_Kh, d_Jh, d_Dherm,
                   d_Jherm, d_status, d_bexp64, d_bexp32, d_peoff, d_E, d_Ef, d_pmaxp, d_dmax, d_counters, d_cumnp, d_prefmaxp, d_ea,
                   d_mat_off, d_mat_n, d_aobase, d_pbase, d_pmol, d_shloc, d_ccm, d_segloc, d_Dpf,
-                  d_nuc_list, d_nuc_goff, d_nuc_dens, d_counters2, d_q4};
+                  d_nuc_list, d_nuc_goff, d_nuc_dens, d_counters2, d_q4, d_Dhermf};
   xc_release();
   for (auto& e : prof_events) cudaEventDestroy(e);
   prof_events.clear();
@@ -1296,13 +1298,13 @@ static int plan_create(int nmol, const eri_basis_t* const* bases, const double* 
     CKP(dalloc(&P->d_pmaxp, npair)); CKP(dalloc(&P->d_prefmaxp, npair)); CKP(dalloc(&P->d_ea, nprimpair));
     CKP(dalloc(&P->d_dmax, npair));
     CKP(dalloc(&P->d_counters, NPAIRCLASS * NPAIRCLASS * 2 * 3 + 2));  // + range-guard and screened counts
-    CKP(dalloc(&P->d_counters2, 3 * NPAIRCLASS * NPAIRCLASS * 3));
-    CKP(cudaMemset(P->d_counters2, 0, sizeof(unsigned long long) * 3 * NPAIRCLASS * NPAIRCLASS * 3));
+    CKP(dalloc(&P->d_counters2, 4 * NPAIRCLASS * NPAIRCLASS * 3));
+    CKP(cudaMemset(P->d_counters2, 0, sizeof(unsigned long long) * 4 * NPAIRCLASS * NPAIRCLASS * 3));
     CKP(dalloc(&P->d_rsteps, st.size()));
     CKP(dalloc(&P->d_Dp, (size_t)P->nmat)); CKP(dalloc(&P->d_Dpf, (size_t)P->nmat));
     CKP(dalloc(&P->d_Kh, (size_t)P->nmat));
     CKP(dalloc(&P->d_Jh, (size_t)P->nmat));
-    CKP(dalloc(&P->d_Dherm, nherm_tot)); CKP(dalloc(&P->d_Jherm, nherm_tot));
+    CKP(dalloc(&P->d_Dherm, nherm_tot)); CKP(dalloc(&P->d_Jherm, nherm_tot)); CKP(dalloc(&P->d_Dhermf, nherm_tot));
     CKP(dalloc(&P->d_status, 1));
     if (P->alloc_pairs() != ERI_OK) { rc = ERI_ENOMEM; goto fail; }
     CKP(upload(P->d_sh_l, l)); CKP(upload(P->d_sh_atom, atom)); CKP(upload(P->d_sh_np, np));
@@ -1380,51 +1382,111 @@ static int build_impl(eri_plan_impl* P, const double* D, double* J, double* K, i
   CK(cudaGetLastError());
   const bool jengine = J && !K && P->opts.j_engine;
   if (jengine) {
-    // J alone: Hermite density -> J-engine -> Hermite J to Cartesian (Eq. j_formula)
+    // J alone: Hermite density -> J-engine -> Hermite J to Cartesian (Eq. j_formula).
+    // Mixed precision: each ordered list is split on the device by the energy's
+    // tier test (reading 5) and each tier's kernel runs its own compacted list;
+    // both add into the FP64 Hermite J.
+    const bool jmixed = precision == ERI_MIXED;
     CK(cudaMemsetAsync(P->d_Jherm, 0, sizeof(double) * (size_t)P->nherm_tot, s));
     k_hermite_density<<<grid1(P->npair, 64), 64, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_pnp, P->d_ppoff,
                                                           P->d_phoff, P->d_sh_l, P->d_pao1, P->d_pao2, P->d_pmol, mm,
-                                                          P->d_sig, P->pairdata(), P->d_Dp, P->d_Dherm);
+                                                          P->d_sig, P->pairdata(), P->d_Dp, P->d_Dherm,
+                                                          jmixed ? P->d_Dhermf : nullptr);
     CK(cudaGetLastError());
+    if (jmixed) {
+      k_dmax<<<grid1(P->npair, 128), 128, 0, s>>>(P->npair, P->d_ps1, P->d_ps2, P->d_sh_l, P->d_pao1, P->d_pao2,
+                                                  P->d_pmol, P->d_mat_off, P->d_mat_n, P->d_Dp, P->d_dmax);
+      CK(cudaGetLastError());
+      if (!concurrent) {
+        const int rc = P->ensure_tier_bufs(1);
+        if (rc != ERI_OK) return rc;
+      }
+      if (P->tier_nb < (concurrent ? nbranch : 1)) return ERI_EINVAL;
+    }
     JArgs ja{};
     ja.pd = P->pairdata(); ja.sp = P->spinfo(); ja.bt = P->boystabs();
-    ja.rsteps = P->d_rsteps; ja.Dherm = P->d_Dherm; ja.Jherm = P->d_Jherm;
+    ja.rsteps = P->d_rsteps; ja.Dherm = P->d_Dherm; ja.Dhermf = P->d_Dhermf; ja.Jherm = P->d_Jherm;
     ja.omega2 = P->omega * P->omega; ja.omega2f = (float)ja.omega2;
     ja.det = P->opts.deterministic ? 1 : 0;
+    ja.items = nullptr;
+    ja.nitems = nullptr;
+    KArgs ka{};  // tier split of the ordered lists
+    ka.pd = P->pairdata(); ka.sp = P->spinfo();
+    ka.Q = P->d_Q; ka.dmax = P->d_dmax; ka.pmaxp = P->d_pmaxp; ka.prefmaxp = P->d_prefmaxp;
+    ka.shloc = P->d_shloc; ka.pbase = P->d_pbase;
+    ka.tau = (float)P->opts.mixed_tau; ka.pmax32 = (float)kPmax32; ka.mixed = 1;
     if (concurrent) {
       CK(cudaEventRecord(P->fork_ev, s));
       for (int b = 0; b < nbranch; ++b) CK(cudaStreamWaitEvent(P->branch[b], P->fork_ev, 0));
     }
+    // counters2 kinds 0 (J-engine FP64) and 3 (J-engine FP32)
     CK(cudaMemsetAsync(P->d_counters2, 0, sizeof(unsigned long long) * NPAIRCLASS * NPAIRCLASS * 3, s));
+    CK(cudaMemsetAsync(P->d_counters2 + 3 * NPAIRCLASS * NPAIRCLASS * 3, 0,
+                       sizeof(unsigned long long) * NPAIRCLASS * NPAIRCLASS * 3, s));
+    P->last_jmixed = jmixed;
     const bool prof = P->opts.profile && !concurrent;
     int nl = 0;
+    auto jlaunch = [&](int X, int Y, int tier, cudaStream_t ls) -> int {
+      const int lab = kClassL1[X] + kClassL2[X], lcd = kClassL1[Y] + kClassL2[Y];
+      ja.counter = P->d_counters2 + ((tier ? 3 : 0) * NPAIRCLASS * NPAIRCLASS + X * NPAIRCLASS + Y) * 3;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (prof) {
+        CK(P->prof_event_pair(&e0, &e1));
+        CK(cudaEventRecord(e0, ls));
+      }
+      cudaError_t e = cudaErrorInvalidValue;
+      switch (lab) {
+        case 0: e = launch_j_lab0(lcd, tier, ja, ls, P->nsm); break;
+        case 1: e = launch_j_lab1(lcd, tier, ja, ls, P->nsm); break;
+        case 2: e = launch_j_lab2(lcd, tier, ja, ls, P->nsm); break;
+        case 3: e = launch_j_lab3(lcd, tier, ja, ls, P->nsm); break;
+        case 4: e = launch_j_lab4(lcd, tier, ja, ls, P->nsm); break;
+        case 5: e = launch_j_lab5(lcd, tier, ja, ls, P->nsm); break;
+        case 6: e = launch_j_lab6(lcd, tier, ja, ls, P->nsm); break;
+      }
+      CK(e);
+      if (prof) {
+        CK(cudaEventRecord(e1, ls));
+        P->prof_log.push_back({X, Y, tier ? 5 : 3, P->prof_ev_used - 2});
+      }
+      return ERI_OK;
+    };
     for (int X = 0; X < NPAIRCLASS; ++X)
       for (int Y = 0; Y < NPAIRCLASS; ++Y) {
-        ja.wl = P->jlist(X, Y);
-        if (ja.wl.total == 0) continue;
-        const cudaStream_t ls = concurrent ? P->branch[nl++ % nbranch] : s;
-        const int lab = kClassL1[X] + kClassL2[X], lcd = kClassL1[Y] + kClassL2[Y];
-        ja.counter = P->d_counters2 + (X * NPAIRCLASS + Y) * 3;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (prof) {
-          CK(P->prof_event_pair(&e0, &e1));
-          CK(cudaEventRecord(e0, ls));
+        const WorkList full = P->jlist(X, Y);
+        if (full.total == 0) continue;
+        const int b = concurrent ? nl++ % nbranch : 0;
+        const cudaStream_t ls = concurrent ? P->branch[b] : s;
+        if (!jmixed) {
+          ja.wl = full;
+          const int rc = jlaunch(X, Y, 0, ls);
+          if (rc != ERI_OK) return rc;
+          continue;
         }
-        cudaError_t e = cudaErrorInvalidValue;
-        switch (lab) {
-          case 0: e = launch_j_lab0(lcd, 0, ja, ls, P->nsm); break;
-          case 1: e = launch_j_lab1(lcd, 0, ja, ls, P->nsm); break;
-          case 2: e = launch_j_lab2(lcd, 0, ja, ls, P->nsm); break;
-          case 3: e = launch_j_lab3(lcd, 0, ja, ls, P->nsm); break;
-          case 4: e = launch_j_lab4(lcd, 0, ja, ls, P->nsm); break;
-          case 5: e = launch_j_lab5(lcd, 0, ja, ls, P->nsm); break;
-          case 6: e = launch_j_lab6(lcd, 0, ja, ls, P->nsm); break;
+        int2* buf = P->tbuf[b];
+        unsigned int* cnt = P->tcnt + 2 * b;
+        for (int64_t f = 0; f < full.total; f += P->tier_cap) {
+          KArgs sa = ka;
+          sa.wl = full;
+          sa.wl.first = f;
+          sa.wl.total = std::min<int64_t>(full.total, f + P->tier_cap);
+          CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned int), ls));
+          const int64_t nch = (sa.wl.total - f + 31) / 32;
+          k_tier_split<<<(int)std::max<int64_t>(1, std::min<int64_t>((nch + 7) / 8, (int64_t)P->nsm * 8)), 256, 0,
+                         ls>>>(sa, buf, buf + P->tier_cap, cnt);
+          CK(cudaGetLastError());
+          for (int tier = 0; tier < 2; ++tier) {
+            ja.wl = full;
+            ja.wl.first = 0;
+            ja.wl.total = sa.wl.total - f;  // upper bound of the tier's count (grid sizing)
+            ja.items = buf + (tier ? P->tier_cap : 0);
+            ja.nitems = cnt + tier;
+            const int rc = jlaunch(X, Y, tier, ls);
+            if (rc != ERI_OK) return rc;
+          }
         }
-        CK(e);
-        if (prof) {
-          CK(cudaEventRecord(e1, ls));
-          P->prof_log.push_back({X, Y, 3, P->prof_ev_used - 2});
-        }
+        ja.items = nullptr;
+        ja.nitems = nullptr;
       }
     if (concurrent)
       for (int b = 0; b < nbranch; ++b) {
@@ -2093,6 +2155,9 @@ extern "C" int eri_get_stats(eri_plan_t* plan, eri_stats_t* st) {
         }
     st->flops_k = fl;
     st->flops_j = 0.0;
+    unsigned long long c2[NPAIRCLASS * NPAIRCLASS * 3];
+    CK(cudaMemcpy(c2, P->d_counters2 + 3 * NPAIRCLASS * NPAIRCLASS * 3, sizeof(c2), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < NPAIRCLASS * NPAIRCLASS; ++i) st->quartets_j_fp32 += P->last_jmixed ? (int64_t)c2[3 * i] : 0;
   }
   int status = 0;
   CK(cudaMemcpy(&status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -2105,10 +2170,10 @@ extern "C" int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t
   if (!P || !count || (cap > 0 && !out)) return ERI_EINVAL;
   CK(cudaSetDevice(P->device));
   CK(cudaDeviceSynchronize());
-  unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6], c2[3 * NPAIRCLASS * NPAIRCLASS * 3];
+  unsigned long long c[NPAIRCLASS * NPAIRCLASS * 6], c2[4 * NPAIRCLASS * NPAIRCLASS * 3];
   CK(cudaMemcpy(c, P->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(c2, P->d_counters2, sizeof(c2), cudaMemcpyDeviceToHost));
-  constexpr int NT = 5;  // tiers: 0 FP64 J/K, 1 FP32 J/K, 2 gradient FP64, 3 J-engine, 4 gradient FP32
+  constexpr int NT = 6;  // tiers: 0 FP64 J/K, 1 FP32 J/K, 2 gradient FP64, 3 J-engine, 4 gradient FP32, 5 J-engine FP32
   double ms[NPAIRCLASS * NPAIRCLASS * NT] = {};
   int nl[NPAIRCLASS * NPAIRCLASS * NT] = {};
   for (const auto& r : P->prof_log) {
@@ -2123,7 +2188,8 @@ extern "C" int eri_get_profile(eri_plan_t* plan, eri_launch_prof_t* out, int32_t
     if (!nl[k]) continue;
     if (n < cap) {
       const int X = k / (NT * NPAIRCLASS), Y = (k / NT) % NPAIRCLASS, t = k % NT;
-      const int kind = t == 3 ? 0 : (t == 2 ? 1 : 2);  // counters2 kinds: J-engine, gradient FP64, gradient FP32
+      // counters2 kinds: J-engine FP64, gradient FP64, gradient FP32, J-engine FP32
+      const int kind = t == 3 ? 0 : (t == 2 ? 1 : (t == 4 ? 2 : 3));
       const unsigned long long* q = t < 2 ? c + ((X * NPAIRCLASS + Y) * 2 + t) * 3
                                           : c2 + (kind * NPAIRCLASS * NPAIRCLASS + X * NPAIRCLASS + Y) * 3;
       eri_launch_prof_t& o = out[n];

@@ -83,12 +83,13 @@ struct eri_plan_impl {
   // per-build workspace
   float* d_Dpf = nullptr;  // D' in FP32 for the FP32 tier
   double *d_Dp = nullptr, *d_Kh = nullptr, *d_Jh = nullptr, *d_Dherm = nullptr, *d_Jherm = nullptr;
+  float* d_Dhermf = nullptr;  // Hermite density in FP32 (FP32 tier of a mixed J-engine build)
   int* d_status = nullptr;
   float *d_pmaxp = nullptr, *d_dmax = nullptr, *d_prefmaxp = nullptr;
   double* d_ea = nullptr;
   unsigned long long* d_counters = nullptr;  // [X*10+Y][tier][items, prim quartets, bra primitives]
-  unsigned long long* d_counters2 = nullptr; // [kind][X*10+Y][same]; kinds: J-engine, gradient FP64, gradient FP32
-  bool last_mixed = false, last_do_j = false, last_do_k = false;
+  unsigned long long* d_counters2 = nullptr; // [kind][X*10+Y][same]; kinds: J-engine FP64, gradient FP64, gradient FP32, J-engine FP32
+  bool last_mixed = false, last_do_j = false, last_do_k = false, last_jmixed = false;
   // optional per-launch profiling (opts.profile): events recorded around each class launch
   struct ProfRec { int X, Y, tier, ev; };
   std::vector<cudaEvent_t> prof_events;

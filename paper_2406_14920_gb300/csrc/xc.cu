@@ -693,6 +693,8 @@ static int xc_build(eri_plan_impl* P, cudaStream_t s) {
 static int xc_ready(eri_plan_impl* P, cudaStream_t s) {
   if (P->xc.nrad == 0) return ERI_EINVAL;  // no grid requested
   if (P->xc.built_serial == P->geom_serial) return ERI_OK;
+  // work queued on the old grid's buffers (any stream of this device) must end before they go
+  XCK(cudaDeviceSynchronize());
   XcState keep;
   keep.nrad = P->xc.nrad;
   keep.ntheta = P->xc.ntheta;

@@ -142,6 +142,41 @@ def test_mixed_precision_w0(eri, tau, etol, mtol):
         assert 0 < st["quartets_k_fp32"] < st["quartets_k"], st
 
 
+@pytest.mark.parametrize("tau,etol,mtol", [(1e-5, 1e-6, 1e-6), (1e-2, 1e-6, 1e-5), (1e30, 2e-5, 2e-4)])
+def test_mixed_jengine_w0(eri, tau, etol, mtol):
+    """J-only mixed build through the J-engine (Eq. j_formula): ordered items
+    with Q_ab Q_cd max|D| < tau in FP32 (tau = 1e30: all of them), FP64 Hermite
+    J.  E_J against the oracle within etol, J within mtol; the FP32 share as
+    the tier bound implies; the same build in a CUDA graph agrees."""
+    import torch
+    basis, D = W.workload(0)
+    plan = eri.Plan(basis, thresh=1e-12, precision=eri.ERI_MIXED, mixed_tau=tau)
+    Dt = torch.from_numpy(D).cuda()
+    J, _ = plan.build_jk(Dt, want_k=False)
+    st = plan.stats()
+    o = oracle.Oracle(basis)
+    Jr, Kr = o.jk(D, 1e-12, o.schwarz())
+    ej, _ = o.energy(D, Jr, Kr)
+    Jn = J.cpu().numpy()
+    e = 0.5 * float((D * Jn).sum())
+    assert abs(e - ej) < etol, e - ej
+    assert np.abs(Jn - Jr).max() < mtol
+    assert np.abs(Jn - Jn.T).max() < 1e-12
+    if tau > 1:
+        assert st["quartets_j_fp32"] == st["quartets_j"]
+    else:
+        assert 0 < st["quartets_j_fp32"] < st["quartets_j"], st
+    # the graph replay runs the same tiers; the FP32 tier's sums depend on how
+    # the items fall into warps (the compacted lists are appended with atomics),
+    # so the two builds agree to FP32 rounding of that tier, not bit for bit
+    Jg = torch.empty_like(J)
+    plan.build_jk_graph(Dt, Jg, None)
+    assert np.abs(Jg.cpu().numpy() - Jn).max() < 0.1 * mtol
+    J64, _ = plan.build_jk(Dt, want_k=False, precision=eri.ERI_FP64)
+    assert plan.stats()["quartets_j_fp32"] == 0
+    assert np.abs(J64.cpu().numpy() - Jr).max() < TOL
+
+
 def test_dynamic_precision_set_tau(eri):
     """eri_plan_set_tau between builds of one plan (the dynamic-precision scheme
     of Sec. 4.1's citation): the FP32 share falls as tau falls, tau = 0 is the
