@@ -770,7 +770,7 @@ extern "C" int eri_xc_grid(eri_plan_t* plan, int32_t nrad, int32_t ntheta, doubl
   if (G >= (int64_t)1 << 31) return ERI_EUNSUPPORTED;  // point indices are int32
   cudaStream_t s = (cudaStream_t)stream;
   XCK(cudaSetDevice(P->device));
-  XCK(cudaStreamSynchronize(s));  // the old grid's buffers may still be read by queued work
+  XCK(cudaDeviceSynchronize());  // the old grid's buffers may still be read by queued work on any stream
   P->xc_release();
   P->xc.nrad = nrad;
   P->xc.ntheta = ntheta;
