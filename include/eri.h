@@ -412,7 +412,7 @@ int eri_nuclear_grad(eri_plan_t* plan, const double* D, int32_t ncharge, const d
  * three iterations of p(mu) = (3 mu - mu^3)/2).  Point g = ((atom * nrad + i) *
  * ntheta + j) * 2 ntheta + k; npoints (host, may be NULL) receives
  * natom * nrad * 2 ntheta^2.  It also groups the points into blocks of at most
- * 128 (per atom: adjacent radial shells x one eighth of the sphere), finds the
+ * 64 (per atom: adjacent radial shells x one sixteenth of the sphere), finds the
  * shells that reach each block, and evaluates the basis functions and their
  * gradients there; when those values fit in cap_bytes (<= 0: 16 GiB) they stay
  * resident in device memory for every later call, otherwise each call
@@ -471,7 +471,7 @@ typedef struct {
   double sum_block_functions;     /* sum over blocks of the significant functions n_b */
   double sum_block_functions_sq;  /* sum over blocks of n_b^2 */
   double workspace_bytes;         /* basis-value workspace */
-  double flops_density;           /* (2 n_b^2 + 8 n_b) * 128 summed over blocks: X = D_b Phi_b and rho, grad rho */
+  double flops_density;           /* (2 n_b^2 + 8 n_b) x points, summed over blocks: X = D_b Phi_b and rho, grad rho */
   double flops_matrix;            /* the same for Z_b Phi_b^T and Z */
 } eri_xc_stats_t;
 int eri_xc_stats(eri_plan_t* plan, eri_xc_stats_t* stats);

@@ -8,7 +8,7 @@
 #include "../../include/eri.h"
 
 // exchange-correlation grid of a plan (xc.cu): points and weights in natural
-// order, blocks of at most 128 points (perm: natural index of each block slot,
+// order, blocks of at most 64 points (perm: natural index of each block slot,
 // -1 for padding), per-block bounding spheres, significant shells and
 // functions, and the workspace of basis values (resident when it fits the cap)
 struct alignas(32) XcSphere {
@@ -30,6 +30,7 @@ struct XcState {
   std::vector<int> chunk;  // block boundaries of the workspace chunks
   double *d_rho = nullptr, *d_grad = nullptr, *d_vrho = nullptr, *d_vgrad = nullptr, *d_exc = nullptr;
   double sum_nb = 0.0, sum_nb2 = 0.0;  // sum over blocks of n_b and n_b^2 (significant functions)
+  double sum_nbp = 0.0, sum_nb2p = 0.0;  // the same weighted by each block's number of points
 };
 
 struct eri_plan_impl {

@@ -12,9 +12,9 @@
 //  (4) matrix      V_mn = sum_g w_g [v_rho phi_m phi_n + v_grad . grad(phi_m phi_n)]
 //                  (Eq. xc_grid_sum_0 + Eq. xc_grid_sum_1): k_xc_vmat.
 //
-// Layout.  Points are grouped into blocks of at most 128 that are close in
-// space: one atom, a group of adjacent radial shells and one eighth of the
-// sphere (half of the theta nodes x a quarter of the azimuths).  A block keeps
+// Layout.  Points are grouped into blocks of at most 64 that are close in
+// space: one atom, a group of adjacent radial shells and one sixteenth of the
+// sphere (a quarter of the theta nodes x a quarter of the azimuths).  A block keeps
 // the shells whose extent (the radius beyond which every component and its
 // gradient stays below 1e-15) reaches its bounding sphere: the paper's grid
 // boxes with pair cutoffs (Sec. 3.5), per shell instead of per pair.  The
@@ -40,7 +40,8 @@ using namespace eri;
 
 namespace {
 
-constexpr int kBP = 128;          // points per block (at most)
+constexpr int kBP = 64;           // points per block (at most) = threads of the per-block kernels
+constexpr int kWarps = kBP / 32;
 constexpr int kRT = 16;           // rows of D_b per register tile (k_xc_rho)
 constexpr int kNC = 64;           // columns of D_b per staged chunk (k_xc_rho)
 constexpr int kVT = 64;           // V tile edge (basis functions), k_xc_vmat
@@ -172,7 +173,7 @@ __global__ void k_xc_points(int64_t G, int na, int nrad, int ntheta, const doubl
 // bounding sphere (centre, radius) of every block
 __global__ void __launch_bounds__(kBP) k_xc_bsph(const int* __restrict__ perm, const double* __restrict__ pts,
                                                  XcSphere* __restrict__ bsph) {
-  __shared__ double red[4][4];
+  __shared__ double red[kWarps][4];
   const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, wp = t >> 5;
   const int g = perm[(int64_t)b * kBP + t];
   double x = 0.0, y = 0.0, z = 0.0, c = 0.0;
@@ -185,16 +186,28 @@ __global__ void __launch_bounds__(kBP) k_xc_bsph(const int* __restrict__ perm, c
   double sx = warp_sum(x), sy = warp_sum(y), sz = warp_sum(z), sc = warp_sum(c);
   if (lane == 0) { red[wp][0] = sx; red[wp][1] = sy; red[wp][2] = sz; red[wp][3] = sc; }
   __syncthreads();
-  const double n = red[0][3] + red[1][3] + red[2][3] + red[3][3];
-  const double cx = (red[0][0] + red[1][0] + red[2][0] + red[3][0]) / n;
-  const double cy = (red[0][1] + red[1][1] + red[2][1] + red[3][1]) / n;
-  const double cz = (red[0][2] + red[1][2] + red[2][2] + red[3][2]) / n;
+  double n = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+#pragma unroll
+  for (int x = 0; x < kWarps; ++x) {
+    n += red[x][3];
+    cx += red[x][0];
+    cy += red[x][1];
+    cz += red[x][2];
+  }
+  cx /= n;
+  cy /= n;
+  cz /= n;
   __syncthreads();
   double d = g >= 0 ? sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz)) : 0.0;
   d = warp_max(d);
   if (lane == 0) red[wp][0] = d;
   __syncthreads();
-  if (t == 0) bsph[b] = XcSphere{cx, cy, cz, fmax(fmax(red[0][0], red[1][0]), fmax(red[2][0], red[3][0]))};
+  if (t == 0) {
+    double rmax = 0.0;
+#pragma unroll
+    for (int x = 0; x < kWarps; ++x) rmax = fmax(rmax, red[x][0]);
+    bsph[b] = XcSphere{cx, cy, cz, rmax};
+  }
 }
 
 // extent of every shell: largest r (step 0.02 bohr, up to 80) where
@@ -236,7 +249,7 @@ __global__ void __launch_bounds__(kBP) k_xc_sig(int nshell, int nbf, const XcSph
                                                 const double* __restrict__ ext, int* __restrict__ nsh,
                                                 int* __restrict__ shl, int* __restrict__ shoff,
                                                 int* __restrict__ nbfb, int* __restrict__ bfl) {
-  __shared__ int wcnt[4];
+  __shared__ int wcnt[kWarps];
   __shared__ int base;
   const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, wp = t >> 5;
   const XcSphere sp = bsph[b];
@@ -259,7 +272,8 @@ __global__ void __launch_bounds__(kBP) k_xc_sig(int nshell, int nbf, const XcSph
     for (int x = 0; x < wp; ++x) pre += wcnt[x];
     if (sig) myshl[pre + __popc(m & ((1u << lane) - 1u))] = s;
     __syncthreads();
-    if (t == 0) base += wcnt[0] + wcnt[1] + wcnt[2] + wcnt[3];
+    if (t == 0)
+      for (int x = 0; x < kWarps; ++x) base += wcnt[x];
     __syncthreads();
   }
   const int n = base;
@@ -597,8 +611,10 @@ void eri_plan_impl::xc_release() {
 static int xc_build(eri_plan_impl* P, cudaStream_t s) {
   XcState& X = P->xc;
   const int na = P->natom, nrad = X.nrad, nth = X.ntheta, nphi = 2 * nth;
-  // block table: (atom, group of nrb radial shells, theta half, phi quarter), chunks of <= 128
-  const int ph = nth / 2, pq = nphi / 4, patch = ph * pq;
+  // block table: (atom, group of nrb radial shells, one of kTP theta ranges, one
+  // of kPP azimuth ranges), chunks of <= kBP points
+  constexpr int kTP = 4, kPP = 4;
+  const int patch = ((nth + kTP - 1) / kTP) * ((nphi + kPP - 1) / kPP);
   const int nrb = std::max(1, kBP / patch);
   std::vector<int> perm;
   perm.reserve((size_t)X.npts + kBP);
@@ -611,11 +627,11 @@ static int xc_build(eri_plan_impl* P, cudaStream_t s) {
   };
   for (int a = 0; a < na; ++a)
     for (int i0 = 0; i0 < nrad; i0 += nrb)
-      for (int h = 0; h < 2; ++h)
-        for (int q = 0; q < 4; ++q) {
+      for (int h = 0; h < kTP; ++h)
+        for (int q = 0; q < kPP; ++q) {
           for (int i = i0; i < std::min(nrad, i0 + nrb); ++i)
-            for (int j = h * ph; j < (h + 1) * ph; ++j)
-              for (int k = q * pq; k < (q + 1) * pq; ++k)
+            for (int j = h * nth / kTP; j < (h + 1) * nth / kTP; ++j)
+              for (int k = q * nphi / kPP; k < (q + 1) * nphi / kPP; ++k)
                 cur.push_back((int)(((int64_t)(a * nrad + i) * nth + j) * nphi + k));
           flush();
         }
@@ -652,14 +668,14 @@ static int xc_build(eri_plan_impl* P, cudaStream_t s) {
   k_xc_sig<<<nb, kBP, 0, s>>>(ns, nbf, X.d_bsph, P->d_sh_atom, P->d_sh_l, P->d_sh_ao, P->d_coords, X.d_ext,
                               X.d_nsh, X.d_shl, X.d_shoff, X.d_nbfb, X.d_bfl);
   XCK(cudaGetLastError());
-  // workspace plan: per block 4 x n_b x 128 doubles; chunks under the cap
+  // workspace plan: per block kSlots x n_b x kBP doubles; chunks under the cap
   std::vector<int> nbfb(nb);
   XCK(cudaMemcpyAsync(nbfb.data(), X.d_nbfb, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
   XCK(cudaStreamSynchronize(s));
   const size_t cap = std::max<size_t>(X.cap_bytes / sizeof(double), (size_t)kSlots * nbf * kBP);
   std::vector<int64_t> woff(nb + 1);
   X.chunk.assign(1, 0);
-  X.sum_nb = X.sum_nb2 = 0.0;
+  X.sum_nb = X.sum_nb2 = X.sum_nbp = X.sum_nb2p = 0.0;
   size_t used = 0, peak = 0;
   for (int b = 0; b < nb; ++b) {
     const size_t need = (size_t)kSlots * nbfb[b] * kBP;
@@ -670,8 +686,12 @@ static int xc_build(eri_plan_impl* P, cudaStream_t s) {
     woff[b] = (int64_t)used;
     used += need;
     peak = std::max(peak, used);
+    int np = 0;
+    for (int t = 0; t < kBP; ++t) np += perm[(size_t)b * kBP + t] >= 0;
     X.sum_nb += nbfb[b];
     X.sum_nb2 += (double)nbfb[b] * nbfb[b];
+    X.sum_nbp += (double)nbfb[b] * np;
+    X.sum_nb2p += (double)nbfb[b] * nbfb[b] * np;
   }
   X.chunk.push_back(nb);
   woff[nb] = 0;
@@ -863,7 +883,7 @@ extern "C" int eri_xc_stats(eri_plan_t* plan, eri_xc_stats_t* st) {
   // density X = D_b Phi_b (2 n_b^2 per point) and the rho / grad rho
   // epilogue (8 n_b); matrix Z_b Phi_b^T + Phi_b Z_b^T on the lower triangle
   // (2 n_b^2 per point) and Z (8 n_b); FMA = 2 FLOP
-  st->flops_density = (2.0 * X.sum_nb2 + 8.0 * X.sum_nb) * kBP;
-  st->flops_matrix = (2.0 * X.sum_nb2 + 8.0 * X.sum_nb) * kBP;
+  st->flops_density = 2.0 * X.sum_nb2p + 8.0 * X.sum_nbp;
+  st->flops_matrix = 2.0 * X.sum_nb2p + 8.0 * X.sum_nbp;
   return ERI_OK;
 }
