@@ -412,7 +412,7 @@ int eri_nuclear_grad(eri_plan_t* plan, const double* D, int32_t ncharge, const d
  * three iterations of p(mu) = (3 mu - mu^3)/2).  Point g = ((atom * nrad + i) *
  * ntheta + j) * 2 ntheta + k; npoints (host, may be NULL) receives
  * natom * nrad * 2 ntheta^2.  It also groups the points into blocks of at most
- * 64 (per atom: adjacent radial shells x one sixteenth of the sphere), finds the
+ * 32 (per atom: adjacent radial shells x one thirty-second of the sphere), finds the
  * shells that reach each block, and evaluates the basis functions and their
  * gradients there; when those values fit in cap_bytes (<= 0: 16 GiB) they stay
  * resident in device memory for every later call, otherwise each call

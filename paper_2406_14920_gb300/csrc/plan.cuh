@@ -8,7 +8,7 @@
 #include "../../include/eri.h"
 
 // exchange-correlation grid of a plan (xc.cu): points and weights in natural
-// order, blocks of at most 64 points (perm: natural index of each block slot,
+// order, blocks of at most 32 points (perm: natural index of each block slot,
 // -1 for padding), per-block bounding spheres, significant shells and
 // functions, and the workspace of basis values (resident when it fits the cap)
 struct alignas(32) XcSphere {

@@ -12,9 +12,9 @@
 //  (4) matrix      V_mn = sum_g w_g [v_rho phi_m phi_n + v_grad . grad(phi_m phi_n)]
 //                  (Eq. xc_grid_sum_0 + Eq. xc_grid_sum_1): k_xc_vmat.
 //
-// Layout.  Points are grouped into blocks of at most 64 that are close in
-// space: one atom, a group of adjacent radial shells and one sixteenth of the
-// sphere (a quarter of the theta nodes x a quarter of the azimuths).  A block keeps
+// Layout.  Points are grouped into blocks of at most 32 that are close in
+// space: one atom, a group of adjacent radial shells and one thirty-second of
+// the sphere (a quarter of the theta nodes x an eighth of the azimuths).  A block keeps
 // the shells whose extent (the radius beyond which every component and its
 // gradient stays below 1e-15) reaches its bounding sphere: the paper's grid
 // boxes with pair cutoffs (Sec. 3.5), per shell instead of per pair.  The
@@ -40,7 +40,7 @@ using namespace eri;
 
 namespace {
 
-constexpr int kBP = 64;           // points per block (at most) = threads of the per-block kernels
+constexpr int kBP = 32;           // points per block (at most) = threads of the per-block kernels
 constexpr int kWarps = kBP / 32;
 constexpr int kRT = 16;           // rows of D_b per register tile (k_xc_rho)
 constexpr int kNC = 64;           // columns of D_b per staged chunk (k_xc_rho)
@@ -613,7 +613,7 @@ static int xc_build(eri_plan_impl* P, cudaStream_t s) {
   const int na = P->natom, nrad = X.nrad, nth = X.ntheta, nphi = 2 * nth;
   // block table: (atom, group of nrb radial shells, one of kTP theta ranges, one
   // of kPP azimuth ranges), chunks of <= kBP points
-  constexpr int kTP = 4, kPP = 4;
+  constexpr int kTP = 4, kPP = 8;
   const int patch = ((nth + kTP - 1) / kTP) * ((nphi + kPP - 1) / kPP);
   const int nrb = std::max(1, kBP / patch);
   std::vector<int> perm;
