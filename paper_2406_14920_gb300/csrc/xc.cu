@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(kBP) k_xc_bsph(const int* __restrict__ perm, c
 
 // extent of every shell: largest r (step 0.02 bohr, up to 80) where
 // sum_k |c_k| f_max (r^l + l r^(l-1) + 2 a_k r^(l+1)) exp(-a_k r^2) >= kAoEps,
-// a bound on every component and its gradient
+// a bound on every component and its gradient; a shell above the bound at
+// 80 bohr (exponents below about 0.005) gets an unlimited extent
 __global__ void k_xc_extent(int nshell, const int* __restrict__ sh_l, const int* __restrict__ sh_np,
                             const int* __restrict__ sh_po, const int* __restrict__ sh_ao,
                             const double* __restrict__ ex, const double* __restrict__ cn, const double* __restrict__ f,
@@ -234,7 +235,7 @@ __global__ void k_xc_extent(int nshell, const int* __restrict__ sh_l, const int*
       b += fabs(cn[o + k]) * fm * (rl + L * rlm + 2.0 * a * rl * r) * exp(-a * r * r);
     }
     if (b >= kAoEps) {
-      e = r + 0.02;
+      e = st == 4000 ? 1e300 : r + 0.02;  // still significant at 80 bohr: never screened
       break;
     }
   }
@@ -795,7 +796,7 @@ extern "C" int eri_xc_grid(eri_plan_t* plan, int32_t nrad, int32_t ntheta, doubl
   P->xc.nrad = nrad;
   P->xc.ntheta = ntheta;
   P->xc.radius = radius;
-  P->xc.cap_bytes = cap_bytes > 0.0 ? (size_t)cap_bytes : kDefaultCap;
+  P->xc.cap_bytes = cap_bytes > 0.0 ? (size_t)std::min(cap_bytes, 1e18) : kDefaultCap;
   P->xc.npts = G;
   P->xc.built_serial = -1;
   rc = xc_ready(P, s);
