@@ -603,7 +603,7 @@ constexpr size_t kVmatSmem = sizeof(double) * (kVT * (kVT + 1) + 4 * kVT * (kVP 
 void eri_plan_impl::xc_release() {
   void* ptrs[] = {xc.d_pts, xc.d_w, xc.d_rad, xc.d_ang, xc.d_invab, xc.d_perm, xc.d_bsph, xc.d_ext, xc.d_nsh,
                   xc.d_shl, xc.d_shoff, xc.d_nbfb, xc.d_bfl, xc.d_woff, xc.d_work, xc.d_rho, xc.d_grad,
-                  xc.d_vrho, xc.d_vgrad, xc.d_exc};
+                  xc.d_vrho, xc.d_vgrad};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   xc = XcState{};
@@ -656,7 +656,6 @@ static int xc_build(eri_plan_impl* P, cudaStream_t s) {
   XCK(xalloc(&X.d_grad, 3 * (size_t)X.npts));
   XCK(xalloc(&X.d_vrho, (size_t)X.npts));
   XCK(xalloc(&X.d_vgrad, 3 * (size_t)X.npts));
-  XCK(xalloc(&X.d_exc, 1));
   XCK(cudaMemcpyAsync(X.d_perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice, s));
   const int nt = std::max(nrad, nth);
   k_xc_nodes<<<(nt + 127) / 128, 128, 0, s>>>(nrad, nth, X.radius, X.d_rad, X.d_ang);
