@@ -4,8 +4,9 @@ Eq. xc_density_0, Eq. xc_density_1, Eq. xc_grid_sum_0, Eq. xc_grid_sum_1).
 Each pin rests on something other than the oracle's own formulas:
 
 - the angular rule integrates monomials of the unit vector exactly
-  (textbook moments 4 pi/(k+1) of u_x^k, 4 pi/15 of u_x^2 u_y^2) and the radial rule of a one-atom
-  grid integrates a normalised Gaussian to 1 (closed form);
+  (textbook moments 4 pi/(k+1) of u_x^k, 4 pi/15 of u_x^2 u_y^2), its theta
+  nodes and weights are numpy's Gauss-Legendre ones, and the radial rule of a
+  one-atom grid integrates a normalised Gaussian to 1 (closed form);
 - the Becke cells are a partition of unity: a normalised Gaussian placed
   anywhere in a molecule integrates to 1 over the whole molecular grid;
 - the grid integral of phi_m phi_n is the overlap S_mn of the oracle's
@@ -195,3 +196,20 @@ def test_matrix_elements_match_full_matrix():
     mn = rng.integers(0, basis.nbf, (20, 2))
     el = o.xc_matrix_elements(pts, w, vrho, vgrad, mn)
     assert np.allclose(el, V[mn[:, 0], mn[:, 1]], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("nt", [4, 8, 16, 24])
+def test_angular_nodes_are_gauss_legendre(nt):
+    """cos(theta) of the grid points are numpy's Gauss-Legendre nodes and the
+    theta weights (summed over azimuths, normalised) its weights."""
+    b = _one_atom([0], [1.0])
+    pts, w = oracle.Oracle(b).xc_grid(2, nt)
+    nang = nt * 2 * nt
+    sl = slice(0, nang)
+    r = np.linalg.norm(pts[sl], axis=1)
+    ct = (pts[sl, 2] / r).reshape(nt, 2 * nt)
+    wt = w[sl].reshape(nt, 2 * nt).sum(axis=1)
+    x, wx = np.polynomial.legendre.leggauss(nt)
+    assert np.allclose(ct, ct[:, :1], atol=1e-15)
+    assert np.abs(ct[:, 0] - x).max() < 1e-14
+    assert np.abs(wt / wt.sum() * 2.0 - wx).max() < 1e-14
