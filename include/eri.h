@@ -416,9 +416,10 @@ int eri_nuclear_grad(eri_plan_t* plan, const double* D, int32_t ncharge, const d
  * shells that reach each block, and evaluates the basis functions and their
  * gradients there; when those values fit in cap_bytes (<= 0: 16 GiB) they stay
  * resident in device memory for every later call, otherwise each call
- * recomputes them in chunks of that size.  Waits for the stream (host
- * bookkeeping of the block sizes).  The grid follows eri_plan_set_coords: it is
- * rebuilt, with the same parameters, at the next XC call after a change.
+ * recomputes them in chunks of that size.  Waits for the device (a previous
+ * grid's buffers are released; host bookkeeping of the block sizes).  The grid
+ * follows eri_plan_set_coords: it is rebuilt, with the same parameters, at the
+ * next XC call after a change (that call waits for the device too).
  * Requires 2 <= nrad <= 1000, 2 <= ntheta <= 64 with ntheta even, radius > 0,
  * and fewer than 2^31 points.
  * Errors: ERI_EINVAL, ERI_EUNSUPPORTED, ERI_ENOMEM, ERI_ECUDA.
