@@ -537,6 +537,25 @@ def _autograd_function():
     return JKEnergy
 
 
+_JKENERGY = None
+
+
+def __getattr__(name):
+    """``JKEnergy`` (the autograd Function) is created on first access, so that
+    importing this module does not import torch."""
+    global _JKENERGY
+    if name == "JKEnergy":
+        if _JKENERGY is None:
+            _JKENERGY = _autograd_function()
+        return _JKENERGY
+    raise AttributeError(name)
+
+
 def jk_energy(coords, D, plan, freeze_lists=False):
     """Differentiable E_J + E_K; see JKEnergy."""
-    return _autograd_function().apply(coords, D, plan, freeze_lists)
+    return __getattr__("JKEnergy").apply(coords, D, plan, freeze_lists)
+
+
+def build_jk(plan, D, **kw):
+    """(J, K) of density D on `plan` (Plan.build_jk; keyword arguments as there)."""
+    return plan.build_jk(D, **kw)

@@ -156,3 +156,14 @@ def test_binding_requires_device_float64_tensors(eri):
     with pytest.raises(ValueError):
         eri._require(np.zeros(4), 4, "D")                               # not a tensor
     eri._require(None, 4, "K")                                          # optional output
+
+
+def test_module_level_api(eri):
+    """eri.JKEnergy (the autograd Function, created on first access and then
+    reused) and eri.build_jk(plan, D) exist; unknown names still raise."""
+    import torch
+    assert issubclass(eri.JKEnergy, torch.autograd.Function)
+    assert eri.JKEnergy is eri.JKEnergy
+    assert callable(eri.build_jk) and callable(eri.jk_energy)
+    with pytest.raises(AttributeError):
+        eri.no_such_name
