@@ -58,3 +58,12 @@ def test_traffic_reader(tmp_path):
     assert bench.traffic_for(7, 4, 0, path=str(p)) is None
     p.write_text("source_hash: 0000000000000000\n| (fp\\|dp) | fp32 | 2500000.0 |\n")
     assert bench.traffic_for(7, 4, 1, path=str(p)) is None
+
+
+def test_tier_peaks_and_names():
+    """FP32 tiers (J/K FP32, gradient FP32, J-engine FP32) take the FP32 ALU
+    peak, the others the FP64 one; every profile tier has a name."""
+    import bench
+    peaks = {0: 1.0, 1: 64.0}
+    assert [bench.tier_peak(t, peaks) for t in range(6)] == [1.0, 64.0, 1.0, 1.0, 64.0, 64.0]
+    assert set(bench.TIER_NAMES) == set(range(6))
